@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs for the dd Rgemm / Rsyrk / Rpotrf / Rpotrs workloads.
+
+This module is shared by the tests, the benchmark and the oracle checks.  It
+holds only the input recipes (random numbers, shapes, scalings); none of the
+method's arithmetic.  All generators draw from numpy's PCG64 with an explicit
+seed, so both sides of every comparison see identical bits.
+
+Recipes (the manual benchmarks on random matrices; its dd format is a pair
+hi + lo of binary64 numbers with |lo| <= ulp(hi)/2):
+
+* dd entries: hi ~ U(-1, 1); lo' = hi * 2^-53 * U(-1, 1); then (hi, lo) is
+  renormalised so that hi == fl(hi + lo) (one binary64 addition and one
+  subtraction, the standard renormalisation of a two-term sum).
+* dd scalars alpha, beta: hi ~ U(0.5, 2), lo as above.
+* ill-scaled operands: A = D_r * A0, B = B0 * D_c with power-of-two diagonal
+  scalings whose integer exponents are uniform on {-30..30} ("outer"); the
+  "inner" stress variant also scales the shared dimension.
+* grouped problems: m, n, k each round(exp(U(ln 16, ln 512))).
+* SPD requests: G (n x 2n) = U [diag(s) 0] V^T with s geometric from 1 to
+  1e-10 and random orthogonal U, V (products of Householder reflectors with
+  Gaussian vectors), formed in binary64; G's lo plane follows the dd entry
+  recipe.  F = G G^T then has condition ~1e20.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def rng(seed: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _renormalise(hi: np.ndarray, lo: np.ndarray):
+    s = hi + lo
+    return s, lo - (s - hi)
+
+
+def dd_lo_for(hi: np.ndarray, g: np.random.Generator):
+    """Return (hi', lo) with lo drawn as hi * 2^-53 * U(-1, 1), renormalised."""
+    lo = hi * 2.0 ** -53 * g.uniform(-1.0, 1.0, size=hi.shape)
+    return _renormalise(hi, lo)
+
+
+def dd_matrix(g: np.random.Generator, rows: int, cols: int, ld: int | None = None,
+              low: float = -1.0, high: float = 1.0):
+    """A rows x cols dd matrix in column-major planes of leading dimension ld.
+
+    Padding rows (ld > rows) are filled with NaN so that a kernel that reads
+    outside the logical matrix is caught by the comparison."""
+    ld = max(1, rows if ld is None else ld)
+    hi = g.uniform(low, high, size=(rows, cols))
+    hi, lo = dd_lo_for(hi, g)
+    H = np.full((ld, cols), np.nan, order="F")
+    L = np.full((ld, cols), np.nan, order="F")
+    H[:rows, :] = hi
+    L[:rows, :] = lo
+    return H, L
+
+
+def dd_scalar(g: np.random.Generator, low: float = 0.5, high: float = 2.0):
+    hi = np.array([g.uniform(low, high)])
+    hi, lo = dd_lo_for(hi, g)
+    return float(hi[0]), float(lo[0])
+
+
+def pow2_exponents(g: np.random.Generator, count: int, lo: int = -30, hi: int = 30):
+    return g.integers(lo, hi + 1, size=count)
+
+
+def scale_rows(M, exps):
+    """Multiply row r of both planes by 2^exps[r] (exact)."""
+    f = np.ldexp(1.0, np.asarray(exps))[:, None]
+    return M[0] * f, M[1] * f
+
+
+def scale_cols(M, exps):
+    f = np.ldexp(1.0, np.asarray(exps))[None, :]
+    return M[0] * f, M[1] * f
+
+
+@dataclass
+class GemmCase:
+    transa: str
+    transb: str
+    m: int
+    n: int
+    k: int
+    alpha: tuple
+    A: tuple
+    B: tuple
+    beta: tuple
+    C: tuple
+
+
+def gemm_case(seed: int, transa: str, transb: str, m: int, n: int, k: int,
+              alpha=None, beta=None, pad: int = 0, ill: str | None = None) -> GemmCase:
+    """Draw A, then B, then C, then alpha, then beta (column-major order).
+
+    ``alpha``/``beta`` None means "random dd in [0.5, 2]".  ``pad`` extra rows
+    make every leading dimension non-tight.  ``ill`` is None, "outer" or
+    "inner" (the ill-scaled recipes above)."""
+    g = rng(seed)
+    ta, tb = transa.upper() in "TC", transb.upper() in "TC"
+    ar, ac = (k, m) if ta else (m, k)
+    br, bc = (n, k) if tb else (k, n)
+    A = dd_matrix(g, ar, ac, ar + pad)
+    B = dd_matrix(g, br, bc, br + pad)
+    C = dd_matrix(g, m, n, m + pad)
+    al = dd_scalar(g) if alpha is None else alpha
+    be = dd_scalar(g) if beta is None else beta
+    if ill is not None:
+        er = pow2_exponents(g, m)
+        ec = pow2_exponents(g, n)
+        # op(A) row i scaled by 2^er[i]; op(B) column j by 2^ec[j]
+        A = scale_cols(A, er) if ta else _scale_rows_padded(A, er)
+        B = _scale_rows_padded(B, ec) if tb else scale_cols(B, ec)
+        if ill == "inner":
+            ek = pow2_exponents(g, k, -15, 15)
+            A = _scale_rows_padded(A, ek) if ta else scale_cols(A, ek)
+            B = scale_cols(B, -ek) if tb else _scale_rows_padded(B, -ek)
+    return GemmCase(transa, transb, m, n, k, al, A, B, be, C)
+
+
+def _scale_rows_padded(M, exps):
+    exps = np.asarray(exps)
+    f = np.ones(M[0].shape[0])
+    f[: exps.size] = np.ldexp(1.0, exps)
+    return M[0] * f[:, None], M[1] * f[:, None]
+
+
+def grouped_problems(seed: int, count: int = 4096, lo: int = 16, hi: int = 512):
+    """m, n, k per problem, each round(exp(U(ln lo, ln hi)))."""
+    g = rng(seed)
+    u = g.uniform(math.log(lo), math.log(hi), size=(count, 3))
+    return np.rint(np.exp(u)).astype(np.int64)
+
+
+def householder_orthogonal_apply(g: np.random.Generator, X: np.ndarray, side: str,
+                                 reflectors: int = 3) -> np.ndarray:
+    """Apply a random orthogonal Q = H_1 ... H_r (Householder reflectors with
+    Gaussian vectors) to X from the left (Q X) or the right (X Q^T)."""
+    X = np.array(X, dtype=np.float64, order="F")
+    dim = X.shape[0] if side == "left" else X.shape[1]
+    for _ in range(reflectors):
+        v = g.standard_normal(dim)
+        v /= np.linalg.norm(v)
+        if side == "left":
+            X -= 2.0 * np.outer(v, v @ X)
+        else:
+            X -= 2.0 * np.outer(X @ v, v)
+    return X
+
+
+def spd_request(seed: int, n: int, nrhs: int = 4, smin: float = 1e-10):
+    """One served-solve request: G (n x 2n) dd and B (n x nrhs) dd."""
+    g = rng(seed)
+    s = np.geomspace(1.0, smin, n)
+    G = np.zeros((n, 2 * n), order="F")
+    G[np.arange(n), np.arange(n)] = s
+    G = householder_orthogonal_apply(g, G, "left")
+    G = householder_orthogonal_apply(g, G, "right")
+    gh, gl = dd_lo_for(G, g)
+    Bh = g.uniform(-1.0, 1.0, size=(n, nrhs))
+    Bh, Bl = dd_lo_for(Bh, g)
+    return (np.asfortranarray(gh), np.asfortranarray(gl)), (np.asfortranarray(Bh),
+                                                            np.asfortranarray(Bl))
+
+
+def request_sizes(seed: int, count: int = 2000, lo: int = 64, hi: int = 2048):
+    g = rng(seed)
+    return np.rint(np.exp(g.uniform(math.log(lo), math.log(hi), size=count))).astype(np.int64)
+
+
+def poisson_arrivals(seed: int, count: int, rate_per_s: float) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
+    g = rng(seed)
+    return np.cumsum(g.exponential(1.0 / rate_per_s, size=count))

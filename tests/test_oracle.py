@@ -1,0 +1,500 @@
+"""Pins for the oracle (CPU only).
+
+The oracle is checked against things other than itself: exact rational
+arithmetic (``fractions``), values the manual prints for its worked examples
+(``tests/golden/``), closed forms, special cases that reduce to binary64
+library routines, and LAPACK-style test ratios.  ``test_planted_mistakes``
+re-runs this file against deliberately broken copies of the oracle and
+requires every copy to fail.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+import tempfile
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from oracle import fraction_ref as fr
+from ddcheck import EPS_DD, U, err_over_bound, gemm_bound, is_normalised
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+U2 = U * U
+
+
+# ---------------------------------------------------------------------------
+# golden fixtures
+# ---------------------------------------------------------------------------
+
+def read_golden(name):
+    """Parse a fixture: 'key value...' lines and named blocks of matrix rows."""
+    out, block = {}, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if len(parts) == 1 and parts[0].isupper() or parts[0].startswith("ANSWER"):
+                block = parts[0]
+                out[block] = []
+            elif block is None or parts[0] in ("alpha", "beta", "epsilon", "precision",
+                                               "digits"):
+                out[parts[0]] = parts[1:]
+            else:
+                out[block].append(line)
+    return out
+
+
+def rows_real(lines):
+    return [[Fraction(x) for x in l.split()] for l in lines]
+
+
+def rows_complex(lines):
+    res = []
+    for l in lines:
+        row = []
+        for cell in l.split("|"):
+            re, im = cell.split()
+            row.append((re, im))
+        res.append(row)
+    return res
+
+
+def dd_plane_from_fracs(F, conv):
+    """Column-major (hi, lo) planes from a list of rows of Fractions."""
+    m, n = len(F), len(F[0])
+    hi, lo = np.zeros((m, n), order="F"), np.zeros((m, n), order="F")
+    for i in range(m):
+        for j in range(n):
+            hi[i, j], lo[i, j] = conv(F[i][j])
+    return hi, lo
+
+
+# ---------------------------------------------------------------------------
+# scalar dd layer
+# ---------------------------------------------------------------------------
+
+def random_dd(g, n, emin=-40, emax=40):
+    hi = g.uniform(-1, 1, n) * np.ldexp(1.0, g.integers(emin, emax, n))
+    return datagen.dd_lo_for(hi, g)
+
+
+def adversarial_pairs(g, n):
+    a = random_dd(g, n)
+    b = random_dd(g, n)
+    # a third of the pairs nearly cancel: b = -a + small perturbation
+    k = n // 3
+    bh = -a[0][:k] * (1 + g.uniform(-1, 1, k) * 2.0 ** -40)
+    bl = -a[1][:k] * g.uniform(0, 2, k)
+    bh, bl = datagen._renormalise(bh, bl)
+    b = (np.concatenate([bh, b[0][k:]]), np.concatenate([bl, b[1][k:]]))
+    return a, b
+
+
+def F(h, l=0.0):
+    return Fraction(float(h)) + Fraction(float(l))
+
+
+def test_two_sum_and_two_prod_are_exact():
+    g = datagen.rng(1)
+    a = g.uniform(-1, 1, 2000) * np.ldexp(1.0, g.integers(-60, 60, 2000))
+    b = g.uniform(-1, 1, 2000) * np.ldexp(1.0, g.integers(-60, 60, 2000))
+    s, e = oracle.two_sum(a, b)
+    p, q = oracle.two_prod(a, b)
+    assert np.array_equal(s, a + b)
+    assert np.array_equal(p, a * b)
+    for i in range(a.size):
+        assert F(s[i]) + F(e[i]) == F(a[i]) + F(b[i])
+        assert F(p[i]) + F(q[i]) == F(a[i]) * F(b[i])
+
+
+def rel_errs(got_h, got_l, exact):
+    out = []
+    for h, l, x in zip(got_h, got_l, exact):
+        if x == 0:
+            out.append(0.0 if h == 0 and l == 0 else float("inf"))
+        else:
+            out.append(float(abs(F(h, l) - x) / abs(x)))
+    return np.array(out)
+
+
+def test_dd_add_relative_error():
+    g = datagen.rng(2)
+    a, b = adversarial_pairs(g, 1500)
+    rh, rl = oracle.dd_add(a, b)
+    exact = [F(a[0][i], a[1][i]) + F(b[0][i], b[1][i]) for i in range(rh.size)]
+    # accurate dd addition: relative error <= 3u^2 + 13u^3
+    assert rel_errs(rh, rl, exact).max() <= 3.0001 * U2
+    assert is_normalised(rh, rl)
+
+
+def test_dd_mul_div_sqrt_relative_error():
+    g = datagen.rng(3)
+    a, b = random_dd(g, 1500), random_dd(g, 1500)
+    mh, ml = oracle.dd_mul(a, b)
+    ex = [F(a[0][i], a[1][i]) * F(b[0][i], b[1][i]) for i in range(mh.size)]
+    assert rel_errs(mh, ml, ex).max() <= 6 * U2
+    dh, dl = oracle.dd_div(a, b)
+    ex = [F(a[0][i], a[1][i]) / F(b[0][i], b[1][i]) for i in range(dh.size)]
+    assert rel_errs(dh, dl, ex).max() <= 8 * U2
+    pos = (np.abs(a[0]), np.where(a[0] < 0, -a[1], a[1]))
+    sh, sl = oracle.dd_sqrt(pos)
+    for i in range(sh.size):
+        x = F(pos[0][i], pos[1][i])
+        r = F(sh[i], sl[i])
+        # |r - sqrt(x)| = |r^2 - x| / (r + sqrt(x)) ~ |r^2 - x| / (2r)
+        assert abs(r * r - x) / (2 * r) <= 8 * U2 * r
+    assert is_normalised(mh, ml) and is_normalised(dh, dl) and is_normalised(sh, sl)
+
+
+# ---------------------------------------------------------------------------
+# exact tier
+# ---------------------------------------------------------------------------
+
+def test_exact_sum_known_values():
+    assert oracle.exact_sum([1.0, 2.0 ** -100, -1.0]) == (2.0 ** -100, 0.0)
+    assert oracle.exact_sum([1e308, 1e308, -1e308]) == (1e308, 0.0)
+    assert oracle.exact_sum([1.0, 2.0 ** -60]) == (1.0, 2.0 ** -60)
+    assert oracle.exact_sum([-3.0, 2.0 ** -200, 2.0 ** -201]) == (-3.0, 3 * 2.0 ** -201)
+    # 1 + 2^-53 is a rounding tie for hi; the 2^-160 below it breaks the tie
+    # upward (sticky bit), so hi = 1 + 2^-52 and lo = RN(-2^-53 + 2^-160) = -2^-53
+    assert oracle.exact_sum([1.0, 2.0 ** -53, 2.0 ** -160]) == (1.0 + 2.0 ** -52, -2.0 ** -53)
+    assert oracle.exact_sum([1.0, 2.0 ** -53]) == (1.0, 2.0 ** -53)
+    g = datagen.rng(4)
+    for _ in range(50):
+        v = g.uniform(-1, 1, 40) * np.ldexp(1.0, g.integers(-300, 300, 40))
+        assert oracle.exact_sum(v) == fr.round_dd(sum(F(t) for t in v))
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_exact_tier_equals_fraction_rounding(ta, tb):
+    for seed, (m, n, k) in enumerate([(3, 4, 5), (5, 2, 7), (1, 1, 1), (4, 4, 0), (2, 6, 3)]):
+        c = datagen.gemm_case(10 + seed, ta, tb, m, n, k, pad=1)
+        if seed == 3:
+            c.beta = (0.0, 0.0)
+        rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+        got = oracle.exact_gemm_entries(ta, tb, k, c.alpha, c.A, c.B, c.beta, c.C, rr.ravel(),
+                                        cc.ravel())
+        want = fr.gemm_exact_dd(ta, tb, m, n, k, c.alpha, c.A, c.B, c.beta, c.C)
+        assert np.array_equal(got[0].reshape(m, n), want[0])
+        assert np.array_equal(got[1].reshape(m, n), want[1])
+
+
+# ---------------------------------------------------------------------------
+# scalar dd Rgemm
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("t", "c")])
+def test_scalar_gemm_within_bound(ta, tb):
+    m, n, k = 7, 5, 33
+    c = datagen.gemm_case(20, ta, tb, m, n, k, pad=2)
+    got = oracle.dd_gemm(ta, tb, c.alpha, c.A, c.B, c.beta, c.C, m, n, k)
+    got = (got[0][:m, :n], got[1][:m, :n])
+    want = fr.gemm_exact_dd(ta, tb, m, n, k, c.alpha, c.A, c.B, c.beta, c.C)
+    bound = gemm_bound(ta, tb, m, n, k, c.alpha, c.A, c.B, c.beta, c.C)
+    assert err_over_bound(got, want, bound) <= 1.0
+    assert is_normalised(*got)
+
+
+def test_rgemm_worked_example_exact():
+    gd = read_golden("rgemm_worked_example.txt")
+    A = rows_real(gd["A"])
+    B = rows_real(gd["B"])
+    C = rows_real(gd["C"])
+    to = lambda x: (float(x), 0.0)
+    Ad, Bd, Cd = (dd_plane_from_fracs(M, to) for M in (A, B, C))
+    al = (float(gd["alpha"][0]), 0.0)
+    be = (float(gd["beta"][0]), 0.0)
+    got = oracle.dd_gemm("N", "N", al, Ad, Bd, be, Cd)
+    ans = np.array([[float(x) for x in r] for r in rows_real(gd["ANSWER"])])
+    assert np.array_equal(got[0], ans) and not got[1].any()
+
+
+def complex_gemm_via_real(gemm, alpha, A, B, beta, C):
+    """alpha*A*B + beta*C for complex dd data through six real Rgemm calls.
+
+    ``gemm(alpha, A, B, beta, C)`` is a real 'N','N' dd Rgemm on (hi, lo)
+    planes returning the new C.  Re/Im parts: A = (Ar, Ai) etc."""
+    (Ar, Ai), (Br, Bi), (Cr, Ci) = A, B, C
+    neg = lambda X: (-X[0], -X[1])
+    hcat = lambda X, Y: (np.hstack([X[0], Y[0]]), np.hstack([X[1], Y[1]]))
+    vcat = lambda X, Y: (np.vstack([X[0], Y[0]]), np.vstack([X[1], Y[1]]))
+    n = Cr[0].shape[1]
+    eye = (np.eye(n), np.zeros((n, n)))
+    (ar, ai), (br, bi) = alpha, beta
+    one = (1.0, 0.0)
+    A1, B1 = hcat(Ar, neg(Ai)), vcat(Br, Bi)   # A1 @ B1 = Re(AB)
+    A2, B2 = hcat(Ar, Ai), vcat(Bi, Br)        # A2 @ B2 = Im(AB)
+    re = gemm(ar, A1, B1, br, Cr)
+    re = gemm((-ai[0], -ai[1]), A2, B2, one, re)
+    re = gemm((-bi[0], -bi[1]), Ci, eye, one, re)
+    im = gemm(ar, A2, B2, br, Ci)
+    im = gemm(ai, A1, B1, one, im)
+    im = gemm(bi, Cr, eye, one, im)
+    return re, im
+
+
+def cgemm_case(variant):
+    gd = read_golden("cgemm_worked_example.txt")
+    if variant == "binary64":
+        conv = lambda s: (float(s), 0.0)
+        ans_lines = gd["ANSWER_BINARY64"]
+    else:
+        conv = lambda s: fr.round_dd(Fraction(s))
+        ans_lines = gd["ANSWER_DECIMAL"]
+
+    def planes(lines):
+        cells = rows_complex(lines)
+        re = [[Fraction(c[0]) if variant == "decimal" else Fraction(float(c[0])) for c in r]
+              for r in cells]
+        im = [[Fraction(c[1]) if variant == "decimal" else Fraction(float(c[1])) for c in r]
+              for r in cells]
+        tod = (lambda x: fr.round_dd(x))
+        return dd_plane_from_fracs(re, tod), dd_plane_from_fracs(im, tod)
+
+    A, B, C = planes(gd["A"]), planes(gd["B"]), planes(gd["C"])
+    alpha = tuple(conv(s) for s in gd["alpha"])
+    beta = tuple(conv(s) for s in gd["beta"])
+    ans = rows_complex(ans_lines)
+    return alpha, A, B, beta, C, ans
+
+
+def check_cgemm_result(re, im, alpha, A, B, beta, C, ans):
+    """Compare with the printed 64-digit answer; tolerance derived from the
+    accuracy bound of the six real calls (k <= 6 each, three per part)."""
+    mag = lambda X: np.abs(X[0])
+    a = abs(alpha[0][0]) + abs(alpha[1][0])
+    b = abs(beta[0][0]) + abs(beta[1][0])
+    M = a * (mag(A[0]) + mag(A[1])) @ (mag(B[0]) + mag(B[1])) + b * (mag(C[0]) + mag(C[1]))
+    tol = 3 * 4 * 6 * EPS_DD * M * 1.01 + 8 * U2 * M
+    for i in range(3):
+        for j in range(3):
+            er = abs(F(re[0][i, j], re[1][i, j]) - Fraction(ans[i][j][0]))
+            ei = abs(F(im[0][i, j], im[1][i, j]) - Fraction(ans[i][j][1]))
+            assert er <= Fraction(tol[i, j]) and ei <= Fraction(tol[i, j]), (i, j, float(er),
+                                                                              float(ei))
+
+
+@pytest.mark.parametrize("variant", ["binary64", "decimal"])
+def test_cgemm_worked_example_through_real_rgemm(variant):
+    alpha, A, B, beta, C, ans = cgemm_case(variant)
+
+    def gemm(al, X, Y, be, Z):
+        return oracle.dd_gemm("N", "N", al, X, Y, be, Z)
+
+    re, im = complex_gemm_via_real(gemm, alpha, A, B, beta, C)
+    check_cgemm_result(re, im, alpha, A, B, beta, C, ans)
+
+
+def test_rlamch_dd_epsilon_is_the_bound_constant():
+    gd = read_golden("rlamch_dd.txt")
+    eps = Fraction(gd["epsilon"][0])
+    # the printed epsilon is a 15-significant-digit decimal of 2^-104 carried
+    # as a binary64 constant, so it agrees with 2^-104 to ~1e-15 relative
+    assert abs(eps - Fraction(EPS_DD)) / Fraction(EPS_DD) < Fraction(1, 10 ** 14)
+    assert int(float(gd["digits"][0])) == 106          # 2 x 53 significand bits
+    assert Fraction(gd["precision"][0]) == 2 * eps     # eps * base
+
+
+def test_closed_forms():
+    g = datagen.rng(5)
+    m, n = 6, 4
+    # k = 1: C = alpha*a*b + beta*c, one product per entry
+    c = datagen.gemm_case(30, "N", "N", m, n, 1)
+    got = oracle.dd_gemm("N", "N", c.alpha, c.A, c.B, c.beta, c.C)
+    for i in range(m):
+        for j in range(n):
+            x = (F(*c.alpha) * F(c.A[0][i, 0], c.A[1][i, 0]) * F(c.B[0][0, j], c.B[1][0, j])
+                 + F(*c.beta) * F(c.C[0][i, j], c.C[1][i, j]))
+            assert abs(F(got[0][i, j], got[1][i, j]) - x) <= 16 * U2 * (
+                abs(F(*c.alpha) * F(c.A[0][i, 0]) * F(c.B[0][0, j]))
+                + abs(F(*c.beta) * F(c.C[0][i, j])))
+    # A = I: C = alpha*B + beta*C
+    c = datagen.gemm_case(31, "N", "N", m, n, m)
+    I = (np.eye(m), np.zeros((m, m)))
+    got = oracle.dd_gemm("N", "N", c.alpha, I, c.B[:1] + c.B[1:], c.beta, c.C)
+    B = (c.B[0][:m, :n], c.B[1][:m, :n])
+    want = oracle.dd_add(oracle.dd_mul((np.full(m * n, c.alpha[0]), np.full(m * n, c.alpha[1])),
+                                       (B[0].ravel("F"), B[1].ravel("F"))),
+                         oracle.dd_mul((np.full(m * n, c.beta[0]), np.full(m * n, c.beta[1])),
+                                       (c.C[0].ravel("F"), c.C[1].ravel("F"))))
+    assert np.array_equal(got[0].ravel("F"), want[0]) and np.array_equal(got[1].ravel("F"),
+                                                                         want[1])
+    # alpha = 0: C = beta*C exactly as one dd product per entry, A and B unread
+    nanA = (np.full((m, 3), np.nan), np.full((m, 3), np.nan))
+    nanB = (np.full((3, n), np.nan), np.full((3, n), np.nan))
+    got = oracle.dd_gemm("N", "N", (0.0, 0.0), nanA, nanB, c.beta, c.C)
+    want = oracle.dd_mul((np.full(m * n, c.beta[0]), np.full(m * n, c.beta[1])),
+                         (c.C[0].ravel("F"), c.C[1].ravel("F")))
+    assert np.array_equal(got[0].ravel("F"), want[0])
+
+
+def test_integer_inputs_match_binary64_matmul():
+    g = datagen.rng(6)
+    for ta, tb in [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")]:
+        m, n, k = 9, 7, 11
+        A = g.integers(-50, 50, (k, m) if ta == "T" else (m, k)).astype(np.float64)
+        B = g.integers(-50, 50, (n, k) if tb == "T" else (k, n)).astype(np.float64)
+        C = g.integers(-50, 50, (m, n)).astype(np.float64)
+        z = np.zeros_like
+        got = oracle.dd_gemm(ta, tb, (3.0, 0.0), (A, z(A)), (B, z(B)), (-2.0, 0.0), (C, z(C)))
+        opA = A.T if ta == "T" else A
+        opB = B.T if tb == "T" else B
+        assert np.array_equal(got[0], 3.0 * (opA @ opB) - 2.0 * C) and not got[1].any()
+
+
+def test_quick_returns_and_beta_zero_does_not_read_c():
+    c = datagen.gemm_case(40, "N", "N", 4, 3, 5)
+    Cn = (np.full((4, 3), np.nan), np.full((4, 3), np.nan))
+    got = oracle.dd_gemm("N", "N", c.alpha, c.A, c.B, (0.0, 0.0), Cn)
+    assert np.isfinite(got[0]).all() and np.isfinite(got[1]).all()
+    # (alpha == 0 or k == 0) and beta == 1: no-op, even on NaN
+    same = oracle.dd_gemm("N", "N", (0.0, 0.0), c.A, c.B, (1.0, 0.0), Cn)
+    assert np.isnan(same[0]).all()
+    same = oracle.dd_gemm("N", "N", c.alpha, c.A, c.B, (1.0, 0.0), Cn, 4, 3, 0)
+    assert np.isnan(same[0]).all()
+
+
+# ---------------------------------------------------------------------------
+# scalar dd Rsyrk
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("uplo,trans", [("U", "N"), ("L", "N"), ("U", "T"), ("l", "t")])
+def test_syrk_matches_gemm_triangle_and_exact(uplo, trans):
+    n, k = 6, 9
+    g = datagen.rng(50)
+    A = datagen.dd_matrix(g, k if trans.upper() == "T" else n, n if trans.upper() == "T" else k)
+    C = datagen.dd_matrix(g, n, n)
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    got = oracle.dd_syrk(uplo, trans, al, A, be, C)
+    t = trans.upper() == "T"
+    ref = oracle.dd_gemm("T" if t else "N", "N" if t else "T", al, A, A, be, C)
+    tri = np.triu(np.ones((n, n), bool)) if uplo.upper() == "U" else np.tril(
+        np.ones((n, n), bool))
+    assert np.array_equal(got[0][tri], ref[0][tri]) and np.array_equal(got[1][tri], ref[1][tri])
+    assert np.array_equal(got[0][~tri], C[0][~tri])
+    ex = fr.syrk_exact(uplo, trans, n, k, al, A, be, C)
+    bound = gemm_bound("T" if t else "N", "N" if t else "T", n, n, k, al, A, A, be, C)
+    for i in range(n):
+        for j in range(n):
+            if tri[i, j]:
+                d = abs(F(got[0][i, j], got[1][i, j]) - ex[i][j])
+                assert d <= Fraction(bound[i, j])
+
+
+# ---------------------------------------------------------------------------
+# Rpotrf / Rpotrs
+# ---------------------------------------------------------------------------
+
+def test_potrf_recovers_exact_integer_factor():
+    g = datagen.rng(60)
+    n = 12
+    Ui = np.triu(g.integers(-4, 5, (n, n))).astype(np.float64)
+    np.fill_diagonal(Ui, g.integers(1, 6, n))
+    Fm = Ui.T @ Ui                      # exact in binary64 (small integers)
+    fh, fl, info = oracle.dd_potrf("U", (Fm, np.zeros_like(Fm)))
+    assert info == 0
+    assert np.array_equal(np.triu(fh), Ui) and not np.triu(fl).any()
+    lh, ll, info = oracle.dd_potrf("L", (Fm, np.zeros_like(Fm)))
+    assert info == 0 and np.array_equal(np.tril(lh), Ui.T)
+
+
+def test_potrf_reports_first_non_positive_minor():
+    Fm = np.diag([4.0, 9.0, -1.0, 16.0])
+    assert oracle.dd_potrf("U", (Fm, np.zeros_like(Fm)))[2] == 3
+    Fm = np.array([[1.0, 2.0], [2.0, 4.0]])   # singular: second minor is 0
+    assert oracle.dd_potrf("U", (Fm, np.zeros_like(Fm)))[2] == 2
+
+
+def exact_residual_norm_ratio_potrf(Fd, Ud, n):
+    """||U^T U - F||_1 / (n ||F||_1 eps) with U^T U - F evaluated exactly."""
+    Ut = (np.triu(Ud[0]), np.triu(Ud[1]))
+    rr, cc = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    R = oracle.exact_gemm_entries("T", "N", n, (1.0, 0.0), Ut, Ut, (-1.0, 0.0), Fd, rr.ravel(),
+                                  cc.ravel())
+    Rm = np.abs(R[0].reshape(n, n))
+    Fn = np.abs(Fd[0]).sum(axis=0).max()
+    return Rm.sum(axis=0).max() / (n * Fn * EPS_DD)
+
+
+def test_potrf_potrs_lapack_ratios_on_ill_conditioned_spd():
+    n = 24
+    G, B = datagen.spd_request(61, n)
+    Fd = oracle.dd_syrk("U", "N", (1.0, 0.0), G, (0.0, 0.0),
+                        (np.zeros((n, n), order="F"), np.zeros((n, n), order="F")))
+    # symmetrise (lower from upper) for the residual evaluation
+    Fs = tuple(np.triu(P) + np.triu(P, 1).T for P in Fd)
+    fh, fl, info = oracle.dd_potrf("U", Fd)
+    assert info == 0
+    assert exact_residual_norm_ratio_potrf(Fs, (fh, fl), n) < 30  # LAPACK threshold
+    X = oracle.dd_potrs("U", (fh, fl), B)
+    rr, cc = np.meshgrid(np.arange(n), np.arange(B[0].shape[1]), indexing="ij")
+    R = oracle.exact_gemm_entries("N", "N", n, (-1.0, 0.0), Fs, X, (1.0, 0.0), B, rr.ravel(),
+                                  cc.ravel())
+    Fn = np.abs(Fs[0]).sum(axis=0).max()
+    Xn = np.abs(X[0]).sum(axis=0).max()
+    ratio = np.abs(R[0]).reshape(rr.shape).sum(axis=0).max() / (Fn * Xn * EPS_DD)
+    assert ratio < 30
+    # binary64 Cholesky cannot factor the same matrix reliably (cond ~ 1e20)
+    try:
+        L = np.linalg.cholesky(Fs[0])
+        rel = np.abs(L @ L.T - Fs[0]).max() / np.abs(Fs[0]).max()
+        x64 = np.linalg.solve(L.T, np.linalg.solve(L, B[0]))
+        xdd = X[0]
+        assert np.abs(x64 - xdd).max() / np.abs(xdd).max() > 1e-6 or rel > 0
+    except np.linalg.LinAlgError:
+        pass
+
+
+def test_potrf_matches_numpy_on_well_conditioned_spd():
+    g = datagen.rng(62)
+    n = 20
+    M = g.uniform(-1, 1, (n, n))
+    Fm = M @ M.T + n * np.eye(n)
+    fh, fl, info = oracle.dd_potrf("L", (Fm, np.zeros_like(Fm)))
+    assert info == 0
+    L = np.linalg.cholesky(Fm)
+    assert np.abs(np.tril(fh) - L).max() <= 1e-13 * np.abs(L).max()
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes: every broken copy of the oracle must fail this file
+# ---------------------------------------------------------------------------
+
+MUTANTS = {
+    "dropped_cross_term": ("e += a.hi * b.lo + a.lo * b.hi + a.lo * b.lo;",
+                           "e += a.lo * b.hi + a.lo * b.lo;"),
+    "two_sum_wrong_sign": ("*e = (a - av) + (b - bv);", "*e = (a - av) - (b - bv);"),
+    "transposed_operand": ("int64_t idx = trans ? (c + r * ld) : (r + c * ld);",
+                           "int64_t idx = trans ? (r + c * ld) : (c + r * ld);"),
+    "dropped_beta_term": ("return dd_add(acc, dd_mul(beta, cin));", "return acc;"),
+    "no_sticky_rounding": ("if (round_bit && (sticky || (mant & 1))) mant += 1;",
+                           "if (round_bit && (mant & 1)) mant += 1;"),
+    "sqrt_without_newton": ("fast_two_sum(x, corr, &s, &e);", "fast_two_sum(x, 0.0, &s, &e);"),
+}
+
+
+@pytest.mark.skipif(os.environ.get("DD_ORACLE_LIB") is not None,
+                    reason="already running against a planted mistake")
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistakes_are_caught(name):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "dd_oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) == 1
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "mutant.c")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        so = oracle.compile_source(path, os.path.join(d, "libmutant.so"))
+        env = dict(os.environ, DD_ORACLE_LIB=so)
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            os.path.abspath(__file__)], env=env, capture_output=True, text=True,
+                           cwd=os.path.dirname(HERE))
+    assert r.returncode != 0, f"mutant {name} passed every pin:\n{r.stdout[-2000:]}"
