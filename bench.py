@@ -1,0 +1,371 @@
+"""Benchmark of the dd Rgemm / Rsyrk hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload plain] [--size S]
+
+Default workload ("plain"): one step is dd Rgemm NN, dd Rgemm TN and dd Rsyrk
+(uplo U, trans N) at m = n = k = 4096 on the plain FP64 path, random dd
+inputs with alpha, beta random dd in [0.5, 2] (seeded synthetic data).  The
+metric is dd-GFlops (LAPACK operation counts, one dd add or multiply = one
+flop: Rgemm 2mnk, Rsyrk k n (n+1)).  The inputs (805 MB per problem set) are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line.  With N > 1 (torchrun, one process per GPU) every rank
+runs an independent replica of the step (weak scaling, no collective on the
+data path); value = total flops of all ranks / the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (the plain scalar dd loops) on
+this host's cores on a bounded sample of the same workload, and prints the
+same metric with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import datagen  # noqa: E402
+
+METRIC = "dd-Rgemm/Rsyrk GFlops vs roofline; sliced vs plain at bound; p50/p99 solve ms"
+UNIT = "dd-GFlop/s"
+# nominal FP64 rate of GB300 (1.25 TFLOP/s counting an FMA as two flops) ->
+# 625 G FP64 instructions per second; a dd multiply-add costs 15 of them
+NOMINAL_FP64_INSTR = 1.25e12 / 2
+FP64_OPS_PER_MAC = 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain", choices=["plain"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# workload: plain dd Rgemm NN + Rgemm TN + Rsyrk UN
+# ----------------------------------------------------------------------------
+
+def plain_problems(size: int):
+    """The step's three problems as host (numpy) data."""
+    nn = datagen.gemm_case(1, "N", "N", size, size, size)
+    tn = datagen.gemm_case(2, "T", "N", size, size, size)
+    g = datagen.rng(3)
+    A = datagen.dd_matrix(g, size, size)
+    C = datagen.dd_matrix(g, size, size)
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    syrk = dict(uplo="U", trans="N", n=size, k=size, alpha=al, A=A, beta=be, C=C)
+    return nn, tn, syrk
+
+
+def plain_flops(size: int):
+    g = 2.0 * size ** 3
+    return {"Rgemm_NN": g, "Rgemm_TN": g, "Rsyrk_UN": float(size) * size * (size + 1)}
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mpdd_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_2109_13406_gb300 as mp
+
+    size = args.size
+    nn, tn, syrk = plain_problems(size)
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    dnn = (dev(nn.A), dev(nn.B), dev(nn.C))
+    dtn = (dev(tn.A), dev(tn.B), dev(tn.C))
+    dsy = (dev(syrk["A"]), dev(syrk["C"]))
+    stream = torch.cuda.current_stream()
+    # per-kernel events on the launching stream
+    names = ["Rgemm_NN", "Rgemm_TN", "Rsyrk_UN"]
+    ev = {n: [] for n in names}
+
+    def step(record=False):
+        for nm, c, (A, B, C) in (("Rgemm_NN", nn, dnn), ("Rgemm_TN", tn, dtn)):
+            if record:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            mp.mp_dd_Rgemm(c.transa, c.transb, size, size, size, c.alpha, A, size, B, size,
+                           c.beta, C, size)
+            if record:
+                e1.record(stream)
+                ev[nm].append((e0, e1))
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        mp.mp_dd_Rsyrk("U", "N", size, size, syrk["alpha"], dsy[0], size, syrk["beta"], dsy[1],
+                       size)
+        if record:
+            e1.record(stream)
+            ev["Rsyrk_UN"].append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    peak_fp64 = mp.mp_dd_peak_fp64() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(tt.item())
+        if world > 1 and rank == 0:
+            pass
+    flops = plain_flops(size)
+    step_flops = sum(flops.values())
+    value = world * step_flops * args.steps / (ms * 1e-3) / 1e9
+    per = {}
+    for nm in names:
+        t = [a.elapsed_time(b) for a, b in ev[nm]]
+        avg = sum(t) / len(t)
+        per[nm] = {"ms": avg, "GFlops": flops[nm] / (avg * 1e-3) / 1e9}
+    # dominant kernel: the Rgemm NN launch; algorithmic FP64 instructions
+    nn_ms = per["Rgemm_NN"]["ms"]
+    achieved = FP64_OPS_PER_MAC * float(size) ** 3 / (nn_ms * 1e-3) / 1e9
+    roofline = {
+        "bound": "alu", "kernel": "dd_gemm_plain_kernel<0,0> (Rgemm NN)",
+        "achieved": achieved, "peak": NOMINAL_FP64_INSTR / 1e9, "unit": "GFP64instr/s",
+        "frac": achieved / (NOMINAL_FP64_INSTR / 1e9),
+        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FP64 instr/s (derived)",
+        "peak_measured_fp64_microbench": (peak_fp64 / 1e9) if peak_fp64 else None,
+        "frac_of_measured": (achieved / (peak_fp64 / 1e9)) if peak_fp64 else None,
+        "traffic": None,
+        "fp64_instr_per_dd_mac": FP64_OPS_PER_MAC,
+    }
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, mp, torch, nn, tn, syrk, world)
+    if rank == 0:
+        cpu = None if args.no_cpu or world > 1 else cpu_baseline(size, budget_s=15.0)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PCG64; dd entries hi~U(-1,1), lo=hi*2^-53*U(-1,1) "
+                    "renormalised; alpha,beta random dd in [0.5,2])",
+            "config": {"workload": f"plain dd path: Rgemm NN + Rgemm TN + Rsyrk U/N, "
+                                   f"m=n=k={size}", "m": size, "n": size, "k": size,
+                       "l2": f"inputs {3 * 3 * 2 * 8 * size * size / 1e6:.0f} MB > 129 MB L2, "
+                             "no flush", "parallelism": f"replicas x{world}"},
+            "per_call": per,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, mp, torch, nn, tn, syrk, world):
+    """The same step through the host-buffer entry points (pinned host
+    memory), host<->device copies inside the timed region."""
+    size = args.size
+
+    def pin(pair):
+        out = []
+        for x in pair:
+            t = torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T)).pin_memory()
+            out.append(t)
+        return out
+
+    hnn = [pin(nn.A), pin(nn.B), pin(nn.C)]
+    htn = [pin(tn.A), pin(tn.B), pin(tn.C)]
+    hsy = [pin(syrk["A"]), pin(syrk["C"])]
+    steps = max(1, min(args.steps, 3))
+
+    def step():
+        for c, (A, B, C) in ((nn, hnn), (tn, htn)):
+            mp.mp_dd_Rgemm_host(c.transa, c.transb, size, size, size, c.alpha, A, size, B, size,
+                                c.beta, C, size)
+        mp.mp_dd_Rsyrk_host("U", "N", size, size, syrk["alpha"], hsy[0], size, syrk["beta"],
+                            hsy[1], size)
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    per_mat = 16 * size * size
+    h2d = 2 * 3 * per_mat + 2 * per_mat      # two GEMMs (A, B, C) + Rsyrk (A, C)
+    d2h = 3 * per_mat
+    flops = sum(plain_flops(size).values())
+    return {"value": world * flops * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "api": "mp_dd_Rgemm_host / mp_dd_Rsyrk_host (pinned host buffers)"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def cpu_sample(size: int, cols: int):
+    """A column panel of the Rgemm NN problem: C[:, :cols] with full k."""
+    c = datagen.gemm_case(1, "N", "N", size, size, size)
+    B = (c.B[0][:, :cols], c.B[1][:, :cols])
+    C = (c.C[0][:, :cols], c.C[1][:, :cols])
+    return c, B, C
+
+
+def cpu_baseline(size: int, budget_s: float = 15.0):
+    import oracle
+
+    threads = oracle.num_threads()
+    # calibrate on a narrow panel (one column per thread), then size the
+    # sample to the time budget in whole multiples of the thread count
+    cols = max(1, threads)
+    c, B, C = cpu_sample(size, cols)
+    t0 = time.perf_counter()
+    oracle.dd_gemm("N", "N", c.alpha, c.A, B, c.beta, C, size, cols, size)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    cols = int(min(size, cols * reps))
+    c, B, C = cpu_sample(size, cols)
+    t0 = time.perf_counter()
+    oracle.dd_gemm("N", "N", c.alpha, c.A, B, c.beta, C, size, cols, size)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * size * cols * size / dt / 1e9, "unit": UNIT, "cores": threads,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"scalar dd Rgemm NN, C[:, :{cols}] of the {size}^3 problem (full k)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    size = args.size
+    threads = oracle.num_threads()
+    cols = max(1, threads)          # one output column per host thread per step
+    c, B, C = cpu_sample(size, cols)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.dd_gemm("N", "N", c.alpha, c.A, B, c.beta, C, size, cols, size)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    value = 2.0 * size * cols * size / per / 1e9
+    sample = f"scalar dd Rgemm NN, C[:, :{cols}] of the {size}^3 problem (full k) per step"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"plain dd path: Rgemm NN + Rgemm TN + Rsyrk U/N, m=n=k={size}",
+                   "m": size, "n": size, "k": size},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": threads,
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * mpdd -- double-double (dd) Rgemm / Rsyrk for one GB300 GPU (sm_103a).
+ *
+ * C ABI of libmpdd.so.  Semantics follow MPBLAS as described in the
+ * MPLAPACK 2.0.1 user manual (arXiv 2109.13406):
+ *
+ *  - A dd number is the unevaluated sum hi + lo of two binary64 numbers with
+ *    |lo| <= ulp(hi)/2 (Sec. 5, "Supported Floating point formats"; the dd
+ *    arithmetic is built from Knuth's TwoSum and Dekker's exact product).
+ *  - Matrices are one-dimensional column-major arrays with a leading
+ *    dimension, element (i, j) at index i + j*ld (Sec. 7.3, "How to use
+ *    MPBLAS").  A dd matrix is two such arrays, the hi plane and the lo
+ *    plane, which share the leading dimension.
+ *  - Argument lists are those of the BLAS/LAPACK routine each call mirrors
+ *    (Sec. 7.3 gives the Rgemm prototype and its one-to-one correspondence
+ *    with DGEMM: CHARACTER -> const char*, INTEGER -> 64-bit integer, arrays
+ *    -> pointers).  Flags are case-insensitive first characters, as with the
+ *    BLAS lsame ('N', 'T', 'C'; 'U', 'L'); 'C' means 'T' for real data.
+ *
+ * Ownership and execution: unless a call says otherwise, every matrix
+ * pointer is DEVICE memory owned by the caller, and every call is
+ * asynchronous on the calling thread's current stream (mp_dd_set_stream).
+ * The library allocates nothing that outlives a call except what a call
+ * documents.
+ *
+ * Return codes (all int-returning calls):
+ *    0            success
+ *   -i            argument i (1-based, numbered as in the mirrored BLAS or
+ *                 LAPACK routine) is illegal -- the xerbla convention the
+ *                 manual's MPBLAS tests compare (Sec. 8.1)
+ *   1000 + e      CUDA runtime error e while launching or copying
+ *   2001          a device-side wait ran out of time (the kernel stopped
+ *                 early; the output is undefined)
+ *   2002          requested size beyond a documented limit
+ *   2003          workspace too small
+ *   2004          the CUDA extension cannot run (no device / wrong arch)
+ * mp_dd_last_error() describes the last non-zero return on this thread.
+ */
+#ifndef MPDD_H
+#define MPDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* dd scalar: value = hi + lo (passed by value). */
+typedef struct {
+    double hi, lo;
+} mp_dd;
+
+/* Read-only dd matrix: device hi and lo planes sharing one leading dimension. */
+typedef struct {
+    const double *hi, *lo;
+} mp_dd_cmat;
+
+/* Writable dd matrix planes. */
+typedef struct {
+    double *hi, *lo;
+} mp_dd_mat;
+
+#define MP_DD_OK 0
+#define MP_DD_ERR_CUDA_BASE 1000
+#define MP_DD_ERR_TIMEOUT 2001
+#define MP_DD_ERR_TOO_LARGE 2002
+#define MP_DD_ERR_WORKSPACE 2003
+#define MP_DD_ERR_NO_DEVICE 2004
+
+/* ------------------------------------------------------------------------ */
+/* Streams and errors                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Set the CUDA stream (a cudaStream_t, or NULL for the legacy default
+ * stream) used by later calls made from the calling thread.  Returns 0. */
+int mp_dd_set_stream(void *stream);
+
+/* The calling thread's current stream. */
+void *mp_dd_get_stream(void);
+
+/* Human-readable description of the calling thread's last error ("" if none).
+ * The string is owned by the library and valid until the next call. */
+const char *mp_dd_last_error(void);
+
+/* Library ABI version (increments when a declaration here changes). */
+int mp_dd_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Level-3 MPBLAS: plain double-double path (FP64 DFMA arithmetic)           */
+/* ------------------------------------------------------------------------ */
+
+/* Rgemm (manual Sec. 7.3 prototype; Sec. 6 table of MPBLAS routines;
+ * CUDA dd Rgemm in Sec. 7.3 "CUDA accelerated MPBLAS"):
+ *
+ *     C := alpha * op(A) * op(B) + beta * C,   op(X) = X or X^T,
+ *
+ * op(A) is m x k, op(B) is k x n, C is m x n.  A is stored m x k (transa N)
+ * or k x m (T/C) with leading dimension lda >= max(1, rows stored); same
+ * for B (k x n or n x k, ldb) and C (m x n, ldc >= max(1, m)).
+ * Arithmetic: every multiply-add is dd arithmetic -- the exact product of
+ * the hi parts by FMA plus the two cross products, accumulated with TwoSum
+ * and renormalised after every step; the summation order over k is fixed
+ * (l = 0, 1, ..., k-1), so results are bitwise reproducible run to run and
+ * independent of the launch configuration.  Accuracy: componentwise
+ * |C - C_exact| <= 4 k 2^-104 (|alpha| |op(A)| |op(B)| + |beta| |C|).
+ * BLAS semantics: m == 0, n == 0, or ((alpha == 0 or k == 0) and
+ * beta == 1) returns at once; beta == 0 means C is write-only (NaNs in C
+ * are not propagated); alpha == 0 means A and B are not read.
+ * Errors: -1 transa, -2 transb, -3 m < 0, -4 n < 0, -5 k < 0,
+ * -7 A.hi/A.lo NULL, -8 lda, -9 B planes NULL, -10 ldb, -12 C planes NULL,
+ * -13 ldc (DGEMM's numbering). */
+int mp_dd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
+                mp_dd_mat C, int64_t ldc);
+
+/* Rsyrk (Sec. 6 table; CUDA dd Rsyrk in Sec. 7.3):
+ *
+ *     C := alpha * A * A^T + beta * C   (trans N, A is n x k), or
+ *     C := alpha * A^T * A + beta * C   (trans T/C, A is k x n),
+ *
+ * updating only the uplo ('U' upper, 'L' lower) triangle of the n x n C;
+ * the other triangle is neither read nor written.  Arithmetic and accuracy
+ * as mp_dd_Rgemm; every entry of the triangle is bitwise equal to the same
+ * entry of mp_dd_Rgemm(N, T) (trans N) or (T, N) (trans T) on A, A.
+ * Errors: -1 uplo, -2 trans, -3 n < 0, -4 k < 0, -6 A planes NULL,
+ * -7 lda < max(1, n (N) or k (T)), -9 C planes NULL, -10 ldc < max(1, n)
+ * (DSYRK's numbering). */
+int mp_dd_Rsyrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
+
+/* Host-buffer forms of the two calls above, as the manual's CUDA MPBLAS is
+ * used (Sec. 7.3: the caller passes host arrays; the library moves them to
+ * the GPU and back -- the "with host-GPU transfer" figures of Sec. 10).
+ * All matrix pointers are HOST memory (pinned memory gives the fastest
+ * copies).  The call allocates device buffers for the operands with
+ * cudaMallocAsync on the current stream, copies in, computes, copies C
+ * back, frees the buffers and synchronises the stream before returning.
+ * Same arguments, accuracy and error codes as the device forms. */
+int mp_dd_Rgemm_host(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                     mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
+                     mp_dd beta, mp_dd_mat C, int64_t ldc);
+int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                     mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
+
+/* ------------------------------------------------------------------------ */
+/* Measured roofline denominators (no counterpart in the manual)             */
+/* ------------------------------------------------------------------------ */
+
+/* Time a kernel of independent FP64 fused multiply-add chains filling every
+ * SM and report the issue rate in FP64 instructions per second in *rate.
+ * Synchronous (synchronises the current stream).  Returns 0 or an error. */
+int mp_dd_peak_fp64(double *rate);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDD_H */

@@ -1,0 +1,200 @@
+"""GB300-native double-double (dd) Rgemm / Rsyrk: the MPBLAS hot path.
+
+A thin Python binding over the C ABI of ``libmpdd.so`` (``include/mpdd.h``).
+Each ``mp_dd_*`` function here has the C name and argument list and only
+marshals arguments: device pointers from torch tensors, dd scalars as
+``(hi, lo)`` tuples, the current torch stream.  Every step of the
+computation runs in the library's CUDA kernels; if the library is missing
+the import fails.
+
+Matrices follow the manual's convention (MPLAPACK 2.0.1, Sec. 7.3): column
+major with a leading dimension.  A dd matrix is a pair ``(hi, lo)`` of
+float64 tensors with strides ``(1, ld)`` (a column-major view); see
+``dd_empty`` and ``to_device``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import MpDD, MpDDCMat, MpDDMat
+
+__all__ = [
+    "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
+    "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "Rgemm", "Rsyrk", "dd_empty",
+    "to_device", "to_numpy", "lib",
+]
+
+_LIB = _abi.load()
+
+
+class MpddError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def lib():
+    return _LIB
+
+
+def mp_dd_last_error() -> str:
+    return (_LIB.mp_dd_last_error() or b"").decode()
+
+
+def _check(rc: int, name: str) -> int:
+    if rc != 0:
+        raise MpddError(rc, f"{name}: {mp_dd_last_error()}")
+    return rc
+
+
+def mp_dd_set_stream(stream=None) -> None:
+    """Use ``stream`` (a torch.cuda.Stream, a raw handle, or None for torch's
+    current stream) for later calls from this thread."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
+    _LIB.mp_dd_set_stream(ctypes.c_void_p(handle))
+
+
+def _sync_stream():
+    # calls run on torch's current stream; without a CUDA device (argument
+    # checks only) the legacy default stream handle is passed
+    if torch.cuda.is_available():
+        mp_dd_set_stream(torch.cuda.current_stream())
+    else:
+        _LIB.mp_dd_set_stream(None)
+
+
+def _flag(c: str) -> bytes:
+    return c.encode()[:1]
+
+
+def _dd(x) -> MpDD:
+    if isinstance(x, MpDD):
+        return x
+    if isinstance(x, (int, float)):
+        return MpDD(float(x), 0.0)
+    return MpDD(float(x[0]), float(x[1]))
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _cm(pair) -> MpDDCMat:
+    return MpDDCMat(_ptr(pair[0]), _ptr(pair[1]))
+
+
+def _m(pair) -> MpDDMat:
+    return MpDDMat(_ptr(pair[0]), _ptr(pair[1]))
+
+
+# ----------------------------------------------------------------------------
+# raw entry points: same names and argument lists as include/mpdd.h
+# (matrix arguments are (hi, lo) pairs of tensors, arrays or raw addresses)
+# ----------------------------------------------------------------------------
+
+def mp_dd_Rgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgemm(_flag(transa), _flag(transb), m, n, k, _dd(alpha), _cm(A), lda,
+                          _cm(B), ldb, _dd(beta), _m(C), ldc)
+    return _check(rc, "mp_dd_Rgemm") if check else rc
+
+
+def mp_dd_Rsyrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rsyrk(_flag(uplo), _flag(trans), n, k, _dd(alpha), _cm(A), lda, _dd(beta),
+                          _m(C), ldc)
+    return _check(rc, "mp_dd_Rsyrk") if check else rc
+
+
+def mp_dd_Rgemm_host(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgemm_host(_flag(transa), _flag(transb), m, n, k, _dd(alpha), _cm(A), lda,
+                               _cm(B), ldb, _dd(beta), _m(C), ldc)
+    return _check(rc, "mp_dd_Rgemm_host") if check else rc
+
+
+def mp_dd_Rsyrk_host(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rsyrk_host(_flag(uplo), _flag(trans), n, k, _dd(alpha), _cm(A), lda,
+                               _dd(beta), _m(C), ldc)
+    return _check(rc, "mp_dd_Rsyrk_host") if check else rc
+
+
+def mp_dd_peak_fp64() -> float:
+    _sync_stream()
+    r = ctypes.c_double()
+    _check(_LIB.mp_dd_peak_fp64(ctypes.byref(r)), "mp_dd_peak_fp64")
+    return r.value
+
+
+# ----------------------------------------------------------------------------
+# column-major dd tensors
+# ----------------------------------------------------------------------------
+
+def dd_empty(rows: int, cols: int, ld: int | None = None, device="cuda", fill=None):
+    """(hi, lo) float64 tensors of shape (rows, cols), strides (1, ld)."""
+    ld = max(1, rows if ld is None else ld)
+    out = []
+    for _ in range(2):
+        store = torch.empty((max(cols, 1), ld), dtype=torch.float64, device=device)
+        if fill is not None:
+            store.fill_(fill)
+        out.append(store.t()[:rows, :cols])
+    return tuple(out)
+
+
+def to_device(plane: np.ndarray, device="cuda") -> torch.Tensor:
+    """A column-major numpy plane (ld x cols, Fortran order) -> device tensor
+    with the same leading dimension; shape (ld, cols), strides (1, ld)."""
+    a = np.asfortranarray(plane, dtype=np.float64)
+    store = torch.from_numpy(np.ascontiguousarray(a.T)).to(device)
+    return store.t()
+
+
+def to_numpy(t: torch.Tensor) -> np.ndarray:
+    """Device column-major tensor -> Fortran-order numpy array of the same shape."""
+    return np.asfortranarray(t.detach().t().contiguous().cpu().numpy().T)
+
+
+def _ld(t: torch.Tensor) -> int:
+    if t.dim() != 2 or t.dtype != torch.float64:
+        raise ValueError("dd planes must be 2-D float64 tensors")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError("dd planes must be column-major (stride(0) == 1)")
+    if t.shape[1] > 1:
+        return max(1, t.stride(1))
+    return max(1, t.shape[0], t.stride(1))
+
+
+def Rgemm(transa, transb, alpha, A, B, beta, C, m=None, n=None, k=None):
+    """C := alpha op(A) op(B) + beta C on column-major dd tensors (in place)."""
+    ta, tb = transa.upper() in "TC", transb.upper() in "TC"
+    if m is None:
+        m = A[0].shape[1] if ta else A[0].shape[0]
+    if k is None:
+        k = A[0].shape[0] if ta else A[0].shape[1]
+    if n is None:
+        n = B[0].shape[0] if tb else B[0].shape[1]
+    return mp_dd_Rgemm(transa, transb, m, n, k, alpha, A, _ld(A[0]), B, _ld(B[0]), beta, C,
+                       _ld(C[0]))
+
+
+def Rsyrk(uplo, trans, alpha, A, beta, C, n=None, k=None):
+    t = trans.upper() in "TC"
+    if n is None:
+        n = A[0].shape[1] if t else A[0].shape[0]
+    if k is None:
+        k = A[0].shape[0] if t else A[0].shape[1]
+    return mp_dd_Rsyrk(uplo, trans, n, k, alpha, A, _ld(A[0]), beta, C, _ld(C[0]))

@@ -1,0 +1,71 @@
+"""ctypes declarations of the C ABI in ``include/mpdd.h`` (argument marshalling only).
+
+Every function of the header is bound here under its own name with its C
+argument types; nothing here computes.  ``load()`` fails loudly when the
+compiled library is missing: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmpdd.so")
+
+
+class MpDD(ctypes.Structure):
+    """``mp_dd``: dd scalar hi + lo, passed by value."""
+    _fields_ = [("hi", ctypes.c_double), ("lo", ctypes.c_double)]
+
+
+class MpDDCMat(ctypes.Structure):
+    """``mp_dd_cmat``: read-only hi/lo plane pointers."""
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
+
+
+class MpDDMat(ctypes.Structure):
+    """``mp_dd_mat``: writable hi/lo plane pointers."""
+    _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
+
+
+_c = ctypes.c_char_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); the order and types follow include/mpdd.h
+SIGNATURES = {
+    "mp_dd_set_stream": (_int, [_vp]),
+    "mp_dd_get_stream": (_vp, []),
+    "mp_dd_last_error": (ctypes.c_char_p, []),
+    "mp_dd_version": (_int, []),
+    "mp_dd_Rgemm": (_int, [_c, _c, _i64, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64, MpDD,
+                           MpDDMat, _i64]),
+    "mp_dd_Rsyrk": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDD, MpDDMat, _i64]),
+    "mp_dd_Rgemm_host": (_int, [_c, _c, _i64, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64,
+                                MpDD, MpDDMat, _i64]),
+    "mp_dd_Rsyrk_host": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDD, MpDDMat, _i64]),
+    "mp_dd_peak_fp64": (_int, [_dp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load ``libmpdd.so`` and declare every entry point.  Raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"libmpdd.so not found at {LIB_PATH}: the CUDA library must be built "
+                "(python -c 'import __graft_entry__ as g; g.build()'); there is no "
+                "fallback implementation")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib

@@ -1,0 +1,289 @@
+// C ABI of libmpdd (declared in include/mpdd.h): argument checking with the
+// BLAS numbering of illegal arguments, BLAS quick returns, per-thread stream
+// and error state, and dispatch to the kernels.
+#include <atomic>
+#include <cstring>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mpdd {
+
+ThreadState &tls() {
+    static thread_local ThreadState s;
+    return s;
+}
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(tls().msg, sizeof(tls().msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(MP_DD_ERR_CUDA_BASE + (int)e, "%s: %s (%s)", what, cudaGetErrorName(e),
+                cudaGetErrorString(e));
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_dev_ok[kMaxDevices];   // 0 unknown, 1 ok, 2 unsuitable
+std::atomic<int> g_sms[kMaxDevices];
+}  // namespace
+
+int require_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(MP_DD_ERR_NO_DEVICE, "device index %d", dev);
+    int st = g_dev_ok[dev].load();
+    if (st == 1) return 0;
+    if (st == 0) {
+        int major = 0, minor = 0, sms = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev].store(sms);
+        st = (major == 10 && minor == 3) ? 1 : 2;
+        g_dev_ok[dev].store(st);
+        if (st == 1) return 0;
+        return fail(MP_DD_ERR_NO_DEVICE,
+                    "libmpdd is built for sm_103a only; device %d is sm_%d%d", dev, major,
+                    minor);
+    }
+    return fail(MP_DD_ERR_NO_DEVICE, "libmpdd is built for sm_103a only");
+}
+
+int sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int s = (dev >= 0 && dev < kMaxDevices) ? g_sms[dev].load() : 0;
+    if (s <= 0) {
+        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        if (dev >= 0 && dev < kMaxDevices) g_sms[dev].store(s);
+    }
+    return s;
+}
+
+namespace {
+
+// DGEMM argument checks; returns 0 or -i.
+int check_gemm(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+               mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
+               mp_dd_mat C, int64_t ldc, GemmArgs &p) {
+    int ta = trans_flag(transa), tb = trans_flag(transb);
+    if (ta < 0) return fail(-1, "Rgemm: illegal transa");
+    if (tb < 0) return fail(-2, "Rgemm: illegal transb");
+    if (m < 0) return fail(-3, "Rgemm: m < 0");
+    if (n < 0) return fail(-4, "Rgemm: n < 0");
+    if (k < 0) return fail(-5, "Rgemm: k < 0");
+    int64_t nrowa = ta ? k : m, nrowb = tb ? n : k;
+    if (lda < imax(1, nrowa)) return fail(-8, "Rgemm: lda < max(1, %lld)", (long long)nrowa);
+    if (ldb < imax(1, nrowb)) return fail(-10, "Rgemm: ldb < max(1, %lld)", (long long)nrowb);
+    if (ldc < imax(1, m)) return fail(-13, "Rgemm: ldc < max(1, m)");
+    bool need_ab = m > 0 && n > 0 && k > 0 && !dd_is_zero(alpha);
+    if (need_ab && (A.hi == nullptr || A.lo == nullptr)) return fail(-7, "Rgemm: A is NULL");
+    if (need_ab && (B.hi == nullptr || B.lo == nullptr)) return fail(-9, "Rgemm: B is NULL");
+    if (m > 0 && n > 0 && (C.hi == nullptr || C.lo == nullptr))
+        return fail(-12, "Rgemm: C is NULL");
+    p = GemmArgs{};
+    p.m = m; p.n = n; p.k = k;
+    p.alpha = alpha; p.beta = beta;
+    p.ah = A.hi; p.al = A.lo; p.lda = lda;
+    p.bh = B.hi; p.bl = B.lo; p.ldb = ldb;
+    p.ch = C.hi; p.cl = C.lo; p.ldc = ldc;
+    p.ta = ta; p.tb = tb; p.tri = 0;
+    p.alpha_zero = dd_is_zero(alpha) || k == 0;
+    p.alpha_one = dd_is_one(alpha);
+    p.beta_zero = dd_is_zero(beta);
+    return 0;
+}
+
+// DSYRK argument checks; returns 0 or -i.  Fills p as the equivalent Rgemm
+// (N, T) or (T, N) on A, A restricted to one triangle.
+int check_syrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+               mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc, GemmArgs &p) {
+    int ul = uplo_flag(uplo), t = trans_flag(trans);
+    if (ul < 0) return fail(-1, "Rsyrk: illegal uplo");
+    if (t < 0) return fail(-2, "Rsyrk: illegal trans");
+    if (n < 0) return fail(-3, "Rsyrk: n < 0");
+    if (k < 0) return fail(-4, "Rsyrk: k < 0");
+    int64_t nrowa = t ? k : n;
+    if (lda < imax(1, nrowa)) return fail(-7, "Rsyrk: lda < max(1, %lld)", (long long)nrowa);
+    if (ldc < imax(1, n)) return fail(-10, "Rsyrk: ldc < max(1, n)");
+    bool need_a = n > 0 && k > 0 && !dd_is_zero(alpha);
+    if (need_a && (A.hi == nullptr || A.lo == nullptr)) return fail(-6, "Rsyrk: A is NULL");
+    if (n > 0 && (C.hi == nullptr || C.lo == nullptr)) return fail(-9, "Rsyrk: C is NULL");
+    p = GemmArgs{};
+    p.m = n; p.n = n; p.k = k;
+    p.alpha = alpha; p.beta = beta;
+    p.ah = A.hi; p.al = A.lo; p.lda = lda;
+    p.bh = A.hi; p.bl = A.lo; p.ldb = lda;
+    p.ch = C.hi; p.cl = C.lo; p.ldc = ldc;
+    p.ta = t; p.tb = 1 - t; p.tri = ul;
+    p.alpha_zero = dd_is_zero(alpha) || k == 0;
+    p.alpha_one = dd_is_one(alpha);
+    p.beta_zero = dd_is_zero(beta);
+    return 0;
+}
+
+// BLAS quick return: nothing to compute.
+bool quick_return(const GemmArgs &p) {
+    if (p.m == 0 || p.n == 0) return true;
+    return p.alpha_zero && dd_is_one(p.beta);
+}
+
+// Copy a rows x cols column-major plane between host and device with pitches.
+int copy_plane(void *dst, int64_t dld, const void *src, int64_t sld, int64_t rows,
+               int64_t cols, cudaMemcpyKind kind, cudaStream_t st) {
+    if (rows == 0 || cols == 0) return 0;
+    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)dld * 8, src, (size_t)sld * 8,
+                                      (size_t)rows * 8, (size_t)cols, kind, st);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "cudaMemcpy2DAsync");
+}
+
+// Run a validated problem whose A, B, C planes are host memory: stage them
+// in device buffers (tight leading dimensions), compute, copy C back.
+int run_host(GemmArgs p, int64_t arows, int64_t acols, int64_t brows, int64_t bcols,
+             bool same_ab) {
+    cudaStream_t st = tls().stream;
+    const int64_t m = p.m, n = p.n;
+    double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    int64_t asz = arows * acols, bsz = same_ab ? 0 : brows * bcols, csz = m * n;
+    int rc = 0;
+    cudaError_t e;
+    bool read_ab = !p.alpha_zero;
+    if (read_ab && asz > 0) {
+        e = cudaMallocAsync(&dA, sizeof(double) * 2 * asz, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A)");
+    }
+    if (read_ab && bsz > 0) {
+        e = cudaMallocAsync(&dB, sizeof(double) * 2 * bsz, st);
+        if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocAsync(B)"); goto done; }
+    }
+    e = cudaMallocAsync(&dC, sizeof(double) * 2 * csz, st);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocAsync(C)"); goto done; }
+    if (read_ab && asz > 0) {
+        if ((rc = copy_plane(dA, arows, p.ah, p.lda, arows, acols, cudaMemcpyHostToDevice, st)))
+            goto done;
+        if ((rc = copy_plane(dA + asz, arows, p.al, p.lda, arows, acols,
+                             cudaMemcpyHostToDevice, st)))
+            goto done;
+    }
+    if (read_ab && bsz > 0) {
+        if ((rc = copy_plane(dB, brows, p.bh, p.ldb, brows, bcols, cudaMemcpyHostToDevice, st)))
+            goto done;
+        if ((rc = copy_plane(dB + bsz, brows, p.bl, p.ldb, brows, bcols,
+                             cudaMemcpyHostToDevice, st)))
+            goto done;
+    }
+    {
+        double *hch = p.ch, *hcl = p.cl;
+        int64_t hldc = p.ldc;
+        if (!p.beta_zero) {
+            if ((rc = copy_plane(dC, m, hch, hldc, m, n, cudaMemcpyHostToDevice, st))) goto done;
+            if ((rc = copy_plane(dC + csz, m, hcl, hldc, m, n, cudaMemcpyHostToDevice, st)))
+                goto done;
+        } else if (p.tri != 0) {
+            // the untouched triangle must come back unchanged
+            if ((rc = copy_plane(dC, m, hch, hldc, m, n, cudaMemcpyHostToDevice, st))) goto done;
+            if ((rc = copy_plane(dC + csz, m, hcl, hldc, m, n, cudaMemcpyHostToDevice, st)))
+                goto done;
+        }
+        GemmArgs q = p;
+        q.ah = dA; q.al = dA ? dA + asz : nullptr; q.lda = imax(1, arows);
+        if (same_ab) { q.bh = q.ah; q.bl = q.al; q.ldb = q.lda; }
+        else { q.bh = dB; q.bl = dB ? dB + bsz : nullptr; q.ldb = imax(1, brows); }
+        q.ch = dC; q.cl = dC + csz; q.ldc = imax(1, m);
+        if ((rc = launch_gemm_plain(q, st))) goto done;
+        if ((rc = copy_plane(hch, hldc, dC, m, m, n, cudaMemcpyDeviceToHost, st))) goto done;
+        if ((rc = copy_plane(hcl, hldc, dC + csz, m, m, n, cudaMemcpyDeviceToHost, st)))
+            goto done;
+    }
+done:
+    if (dA) cudaFreeAsync(dA, st);
+    if (dB) cudaFreeAsync(dB, st);
+    if (dC) cudaFreeAsync(dC, st);
+    e = cudaStreamSynchronize(st);
+    if (rc == 0 && e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
+}
+
+}  // namespace
+}  // namespace mpdd
+
+using namespace mpdd;
+
+extern "C" {
+
+int mp_dd_set_stream(void *stream) {
+    tls().stream = (cudaStream_t)stream;
+    return 0;
+}
+
+void *mp_dd_get_stream(void) { return (void *)tls().stream; }
+
+const char *mp_dd_last_error(void) { return tls().msg; }
+
+int mp_dd_version(void) { return 1; }
+
+int mp_dd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
+                mp_dd_mat C, int64_t ldc) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_gemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if ((rc = require_device())) return rc;
+    return launch_gemm_plain(p, tls().stream);
+}
+
+int mp_dd_Rsyrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_syrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if ((rc = require_device())) return rc;
+    return launch_gemm_plain(p, tls().stream);
+}
+
+int mp_dd_Rgemm_host(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                     mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
+                     mp_dd beta, mp_dd_mat C, int64_t ldc) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_gemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if ((rc = require_device())) return rc;
+    int64_t ar = p.ta ? k : m, ac = p.ta ? m : k;
+    int64_t br = p.tb ? n : k, bc = p.tb ? k : n;
+    return run_host(p, ar, ac, br, bc, false);
+}
+
+int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                     mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_syrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if ((rc = require_device())) return rc;
+    int64_t ar = p.ta ? k : n, ac = p.ta ? n : k;
+    return run_host(p, ar, ac, 0, 0, true);
+}
+
+int mp_dd_peak_fp64(double *rate) {
+    clear_error();
+    if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return run_peak_fp64(tls().stream, rate);
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Device double-double arithmetic.
+//
+// A dd value is hi + lo with |lo| <= ulp(hi)/2 (the manual's dd format,
+// Sec. 5: Knuth's TwoSum and Dekker's exact product on binary64).  Every
+// operation here is written with the explicitly rounded intrinsics
+// __dadd_rn / __dsub_rn / __dmul_rn / __fma_rn: the compiler never fuses or
+// reassociates them, which the error-free transformations rely on (the
+// manual's compiler note asks for the same: no value-changing FP
+// optimisation for dd code).
+#pragma once
+
+namespace mpdd {
+
+struct dd {
+    double hi, lo;
+};
+
+// Knuth TwoSum: s + e == a + b exactly, s = fl(a + b).  6 FP64 operations.
+__device__ __forceinline__ void two_sum(double a, double b, double &s, double &e) {
+    s = __dadd_rn(a, b);
+    double bv = __dsub_rn(s, a);
+    double av = __dsub_rn(s, bv);
+    e = __dadd_rn(__dsub_rn(a, av), __dsub_rn(b, bv));
+}
+
+// Dekker FastTwoSum (|a| >= |b| or a == 0): s + e == a + b.  3 operations.
+__device__ __forceinline__ void fast_two_sum(double a, double b, double &s, double &e) {
+    s = __dadd_rn(a, b);
+    e = __dsub_rn(b, __dsub_rn(s, a));
+}
+
+// Product terms of a*b: p = fl(ah*bh), e = its exact error plus the two
+// cross products ah*bl + al*bh (al*bl, below 2^-106 relative, is dropped).
+// 1 DMUL + 3 DFMA.
+__device__ __forceinline__ void prod_terms(dd a, dd b, double &p, double &e) {
+    p = __dmul_rn(a.hi, b.hi);
+    e = __fma_rn(a.hi, b.hi, -p);
+    e = __fma_rn(a.hi, b.lo, e);
+    e = __fma_rn(a.lo, b.hi, e);
+}
+
+// acc += (p + e), renormalised: TwoSum on the leading parts, the low parts
+// added, FastTwoSum.  11 FP64 operations; absolute error at most ~2u^2
+// (|acc| + |p|) per step (u = 2^-53).
+__device__ __forceinline__ void acc_add(dd &acc, double p, double e) {
+    double s, t;
+    two_sum(acc.hi, p, s, t);
+    t = __dadd_rn(t, __dadd_rn(acc.lo, e));
+    fast_two_sum(s, t, acc.hi, acc.lo);
+}
+
+// One dd multiply-add: acc += a * b (15 FP64 operations).
+__device__ __forceinline__ void mac(dd &acc, dd a, dd b) {
+    double p, e;
+    prod_terms(a, b, p, e);
+    acc_add(acc, p, e);
+}
+
+// dd product, renormalised.
+__device__ __forceinline__ dd mul(dd a, dd b) {
+    double p, e;
+    prod_terms(a, b, p, e);
+    dd r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+// Accurate dd addition (two TwoSums, two renormalisations): relative error
+// at most 3u^2 + 13u^3.
+__device__ __forceinline__ dd add(dd a, dd b) {
+    double s1, s2, t1, t2;
+    two_sum(a.hi, b.hi, s1, s2);
+    two_sum(a.lo, b.lo, t1, t2);
+    s2 = __dadd_rn(s2, t1);
+    fast_two_sum(s1, s2, s1, s2);
+    s2 = __dadd_rn(s2, t2);
+    dd r;
+    fast_two_sum(s1, s2, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ dd neg(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ __forceinline__ dd sub(dd a, dd b) { return add(a, neg(b)); }
+
+// dd division: three binary64 quotient digits by long division.
+__device__ __forceinline__ dd div(dd a, dd b) {
+    double q1 = __ddiv_rn(a.hi, b.hi);
+    dd r = sub(a, mul(dd{q1, 0.0}, b));
+    double q2 = __ddiv_rn(r.hi, b.hi);
+    r = sub(r, mul(dd{q2, 0.0}, b));
+    double q3 = __ddiv_rn(r.hi, b.hi);
+    dd q;
+    fast_two_sum(q1, q2, q.hi, q.lo);
+    return add(q, dd{q3, 0.0});
+}
+
+// dd square root: binary64 root plus one Newton correction (a - x^2)/(2x)
+// with the residual in dd.  Returns 0 for a <= 0.
+__device__ __forceinline__ dd sqrt_dd(dd a) {
+    if (!(a.hi > 0.0)) return dd{0.0, 0.0};
+    double x = __dsqrt_rn(a.hi);
+    dd res = sub(a, mul(dd{x, 0.0}, dd{x, 0.0}));
+    double corr = __ddiv_rn(res.hi, __dmul_rn(2.0, x));
+    dd r;
+    fast_two_sum(x, corr, r.hi, r.lo);
+    return r;
+}
+
+}  // namespace mpdd

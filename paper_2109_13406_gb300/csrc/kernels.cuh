@@ -1,0 +1,35 @@
+// Internal launch interfaces between the C ABI (abi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mpdd.h"
+
+namespace mpdd {
+
+// One dd Rgemm / Rsyrk problem, already validated by the ABI layer.
+struct GemmArgs {
+    int64_t m, n, k;
+    mp_dd alpha, beta;
+    const double *ah, *al;
+    int64_t lda;
+    const double *bh, *bl;
+    int64_t ldb;
+    double *ch, *cl;
+    int64_t ldc;
+    int ta, tb;      // op(A), op(B): 0 = as stored, 1 = transposed
+    int tri;         // 0 = full C (Rgemm); 1 = upper, 2 = lower triangle (Rsyrk)
+    int alpha_zero;  // alpha == 0: A and B are not read
+    int alpha_one;   // alpha == 1: the product is stored without scaling
+    int beta_zero;   // beta == 0: C is write-only
+};
+
+// Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).
+int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream);
+
+// FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.
+int run_peak_fp64(cudaStream_t stream, double *rate);
+
+}  // namespace mpdd
