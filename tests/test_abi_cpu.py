@@ -16,9 +16,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def mp():
-    from paper_2109_13406_gb300 import build as b
+    import __graft_entry__
 
-    b.build()
+    __graft_entry__._build_module().build()
     import paper_2109_13406_gb300 as mp
 
     return mp
