@@ -144,6 +144,57 @@ int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, 
                      mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
 
 /* ------------------------------------------------------------------------ */
+/* Split-precision Rgemm on the tensor cores (no counterpart in the manual)  */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace bytes mp_dd_Rgemm_sliced needs for an m x n x k product with
+ * `slices` digits per operand entry (0 = the default, 14). */
+size_t mp_dd_Rgemm_sliced_workspace(int64_t m, int64_t n, int64_t k, int slices);
+
+/* Rgemm with the same arguments and result contract as mp_dd_Rgemm
+ * (arguments 1-13 numbered as there), computed by the Ozaki scheme on the
+ * fp16 tensor cores instead of FP64 DFMA:
+ *  - each row of op(A) and column of op(B) is scaled by a power of two so
+ *    its entries are below 1/2 in magnitude; every dd entry is then rounded
+ *    to a multiple of 2^-8S of that scale (error at most one unit) and cut
+ *    into `slices` = S signed base-256 digits in [-128, 128];
+ *  - the digit products are exact integer GEMMs (fp16 inputs, fp32
+ *    accumulation kept exact by draining every 512 products, int32 sums),
+ *    grouped by digit significance t + u = b for b < S;
+ *  - the band sums are combined exactly in integer arithmetic, rounded once
+ *    to dd, scaled back, and alpha/beta are applied in dd arithmetic.
+ * Accuracy: per product the truncation error is at most ~4.3 *
+ * 2^(e_i + f_j - 8S) with 2^(e_i-1) > max_l |A_il| and 2^(f_j-1) > max_l
+ * |B_lj|; S = 14 (the default) keeps the result within the mp_dd_Rgemm
+ * bound whenever (|A||B|)_ij >= k 2^(e_i+f_j) 2^-8 (e.g. entries of one
+ * row/column within a few binades of its maximum, any scaling between rows
+ * and columns).  Larger S (<= 15) tightens it by 2^-8 per slice.
+ * Limits: 2 <= slices <= 15; k * slices <= 131071 (int32 band sums).
+ * `workspace` is device memory of at least
+ * mp_dd_Rgemm_sliced_workspace(m, n, k, slices) bytes owned by the caller;
+ * its first 4 bytes receive a device status word (0, or 2001 when a device
+ * wait timed out), readable with mp_dd_workspace_status after the call.
+ * Calls sharing a workspace must not overlap on the device.  Asynchronous.
+ * Errors: as mp_dd_Rgemm, plus -14 slices out of range, -15 workspace NULL,
+ * 2003 workspace too small, 2002 k * slices too large. */
+int mp_dd_Rgemm_sliced(const char *transa, const char *transb, int64_t m, int64_t n,
+                       int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
+                       int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices,
+                       void *workspace, size_t workspace_bytes);
+
+/* Byte offsets of the intermediate arrays inside a sliced-Rgemm workspace
+ * (for inspection and testing): offsets[0] row maxima of op(A) (uint64 bit
+ * patterns of max |hi|, m_pad entries), [1] column maxima of op(B) (n_pad),
+ * [2] digit planes of op(A) (fp16 [slices][m_pad][k_pad]), [3] digit planes
+ * of op(B)^T (fp16 [slices][n_pad][k_pad]), [4] band sums (int32
+ * [slices][n_pad][m_pad], column-major per band); offsets[5..7] hold m_pad,
+ * n_pad, k_pad.  Returns 0. */
+int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offsets[8]);
+
+/* Read the device status word of a workspace (synchronous copy). */
+int mp_dd_workspace_status(const void *workspace, int *status);
+
+/* ------------------------------------------------------------------------ */
 /* Measured roofline denominators (no counterpart in the manual)             */
 /* ------------------------------------------------------------------------ */
 

@@ -1,0 +1,110 @@
+"""Oracle for the split-precision (Ozaki-scheme) dd Rgemm.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``); shares nothing with
+the CUDA code.  The manual has no split-precision Rgemm: this follows the
+method's definition as the library documents it, in exact integer
+arithmetic (Python ints and ``fractions``), one function per step:
+
+1. ``scale_exponent``: e with max |hi| < 2^(e-1) for a row of op(A) (a column
+   of op(B)); 0 for an all-zero row.
+2. ``split_row``: for x = hi + lo, X = RNE(hi 2^(8S-e)) + RNE(lo 2^(8S-e));
+   its digits d_0..d_{S-1} with X = sum_t d_t 256^(S-1-t), d_t in
+   [-128, 127] for t >= 1 (the residue of X mod 256 taken in that range) and
+   d_0 the remaining top part.
+3. ``band_products``: P_b = sum_{t+u=b} D_A[t] D_B[u]^T, b < S, exact
+   integer matrix products (numpy int64; the values stay far below 2^63).
+4. ``recombine_exact``: sum_b P_b 2^(e_i+f_j-8(b+2)) as exact rationals.
+
+Parity status: pinned by ``tests/test_ozaki_oracle.py`` -- digit expansions
+reproduce X exactly and stay in range, X approximates x within one unit of
+2^(e-8S), the recombined value approximates the exact product within the
+documented truncation bound, and it equals the exact product when every
+digit beyond the first band is zero (integer and power-of-two inputs).
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+
+def scale_exponent(row_hi) -> int:
+    m = max((abs(float(v)) for v in row_hi), default=0.0)
+    if m == 0.0:
+        return 0
+    _, E = math.frexp(m)          # m = f 2^E with 1/2 <= f < 1, so m < 2^E
+    return E + 1                  # 2^(e-1) = 2^E > m
+
+
+def rne_scaled(v: float, s: int) -> int:
+    """Round-half-even of v * 2^s to an integer (exact rational arithmetic)."""
+    return round(Fraction(v) * (Fraction(2) ** s))
+
+
+def digits_of(X: int, S: int) -> list[int]:
+    d = [0] * S
+    for t in range(S - 1, 0, -1):
+        r = ((X + 128) % 256) - 128
+        d[t] = r
+        X = (X - r) // 256
+    d[0] = X
+    return d
+
+
+def split_row(hi_row, lo_row, S: int):
+    """Digits (S x len) and the exponent of one row of op(A) (column of op(B))."""
+    e = scale_exponent(hi_row)
+    out = np.zeros((S, len(hi_row)), dtype=np.int64)
+    for l, (h, lo) in enumerate(zip(hi_row, lo_row)):
+        X = rne_scaled(float(h), 8 * S - e) + rne_scaled(float(lo), 8 * S - e)
+        out[:, l] = digits_of(X, S)
+    return out, e
+
+
+def split_matrix(rows_hi: np.ndarray, rows_lo: np.ndarray, S: int):
+    """rows x k planes (row r = one row of op(A) or one column of op(B)) ->
+    digits [S][rows][k] and exponents [rows]."""
+    R, K = rows_hi.shape
+    D = np.zeros((S, R, K), dtype=np.int64)
+    E = np.zeros(R, dtype=np.int64)
+    for r in range(R):
+        D[:, r, :], E[r] = split_row(rows_hi[r], rows_lo[r], S)
+    return D, E
+
+
+def band_products(DA: np.ndarray, DB: np.ndarray) -> np.ndarray:
+    """P[b] = sum_{t+u=b} DA[t] @ DB[u]^T for b < S (int64)."""
+    S = DA.shape[0]
+    P = np.zeros((S, DA.shape[1], DB.shape[1]), dtype=np.int64)
+    for b in range(S):
+        for t in range(b + 1):
+            P[b] += DA[t] @ DB[b - t].T
+    return P
+
+
+def recombine_exact(P: np.ndarray, ea, fb):
+    """Exact value of sum_b P_b 2^(e_i + f_j - 8(b+2)) per entry (Fractions)."""
+    S, m, n = P.shape
+    out = [[Fraction(0)] * n for _ in range(m)]
+    for i in range(m):
+        for j in range(n):
+            v = sum(int(P[b, i, j]) * 256 ** (S - 1 - b) for b in range(S))
+            out[i][j] = Fraction(v) * Fraction(2) ** (int(ea[i]) + int(fb[j]) - 8 * S - 8)
+    return out
+
+
+def op_rows(X, trans: bool, rows: int, k: int):
+    """Rows of op(X) (rows x k) from a column-major stored (hi, lo) pair."""
+    h, l = X
+    if trans:
+        return np.ascontiguousarray(h[:k, :rows].T), np.ascontiguousarray(l[:k, :rows].T)
+    return np.ascontiguousarray(h[:rows, :k]), np.ascontiguousarray(l[:rows, :k])
+
+
+def op_cols(X, trans: bool, k: int, cols: int):
+    """Columns of op(X) (k x cols) as rows (cols x k)."""
+    h, l = X
+    if trans:
+        return np.ascontiguousarray(h[:cols, :k]), np.ascontiguousarray(l[:cols, :k])
+    return np.ascontiguousarray(h[:k, :cols].T), np.ascontiguousarray(l[:k, :cols].T)

@@ -24,8 +24,9 @@ from ._abi import MpDD, MpDDCMat, MpDDMat
 
 __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
-    "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "Rgemm", "Rsyrk", "dd_empty",
-    "to_device", "to_numpy", "lib",
+    "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
+    "mp_dd_Rgemm_sliced_workspace", "mp_dd_sliced_layout", "mp_dd_workspace_status", "Rgemm",
+    "Rsyrk", "Rgemm_sliced", "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
 
 _LIB = _abi.load()
@@ -130,6 +131,57 @@ def mp_dd_Rsyrk_host(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, check=True)
     rc = _LIB.mp_dd_Rsyrk_host(_flag(uplo), _flag(trans), n, k, _dd(alpha), _cm(A), lda,
                                _dd(beta), _m(C), ldc)
     return _check(rc, "mp_dd_Rsyrk_host") if check else rc
+
+
+def mp_dd_Rgemm_sliced_workspace(m, n, k, slices=0) -> int:
+    return int(_LIB.mp_dd_Rgemm_sliced_workspace(m, n, k, slices))
+
+
+def mp_dd_Rgemm_sliced(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices,
+                       workspace, workspace_bytes, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgemm_sliced(_flag(transa), _flag(transb), m, n, k, _dd(alpha), _cm(A), lda,
+                                 _cm(B), ldb, _dd(beta), _m(C), ldc, slices, _ptr(workspace),
+                                 workspace_bytes)
+    return _check(rc, "mp_dd_Rgemm_sliced") if check else rc
+
+
+def mp_dd_sliced_layout(m, n, k, slices=0) -> dict:
+    off = (ctypes.c_size_t * 8)()
+    _check(_LIB.mp_dd_sliced_layout(m, n, k, slices, off), "mp_dd_sliced_layout")
+    keys = ["rowmax", "colmax", "digits_a", "digits_b", "bands", "m_pad", "n_pad", "k_pad"]
+    return dict(zip(keys, [int(x) for x in off]))
+
+
+def mp_dd_workspace_status(workspace) -> int:
+    st = ctypes.c_int()
+    _check(_LIB.mp_dd_workspace_status(_ptr(workspace), ctypes.byref(st)),
+           "mp_dd_workspace_status")
+    return st.value
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """A device byte buffer for the calls that take a workspace."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def Rgemm_sliced(transa, transb, alpha, A, B, beta, C, m=None, n=None, k=None, slices=0,
+                 ws=None):
+    """Sliced Rgemm on column-major dd tensors; allocates a workspace when
+    none is given and returns it (reuse it for later calls)."""
+    ta, tb = transa.upper() in "TC", transb.upper() in "TC"
+    if m is None:
+        m = A[0].shape[1] if ta else A[0].shape[0]
+    if k is None:
+        k = A[0].shape[0] if ta else A[0].shape[1]
+    if n is None:
+        n = B[0].shape[0] if tb else B[0].shape[1]
+    need = mp_dd_Rgemm_sliced_workspace(m, n, k, slices)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, C[0].device)
+    mp_dd_Rgemm_sliced(transa, transb, m, n, k, alpha, A, _ld(A[0]), B, _ld(B[0]), beta, C,
+                       _ld(C[0]), slices, ws, ws.numel())
+    return ws
 
 
 def mp_dd_peak_fp64() -> float:

@@ -278,6 +278,41 @@ int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, 
     return run_host(p, ar, ac, 0, 0, true);
 }
 
+size_t mp_dd_Rgemm_sliced_workspace(int64_t m, int64_t n, int64_t k, int slices) {
+    if (m < 0 || n < 0 || k < 0 || slices < 0 || slices > kMaxSlices) return 0;
+    return sliced_workspace_bytes(m, n, k, slices);
+}
+
+int mp_dd_Rgemm_sliced(const char *transa, const char *transb, int64_t m, int64_t n,
+                       int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
+                       int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices,
+                       void *workspace, size_t workspace_bytes) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_gemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, p);
+    if (rc) return rc;
+    if (slices != 0 && (slices < 2 || slices > kMaxSlices))
+        return fail(-14, "Rgemm_sliced: slices = %d outside [2, %d]", slices, kMaxSlices);
+    if (quick_return(p)) return 0;
+    if (workspace == nullptr) return fail(-15, "Rgemm_sliced: workspace is NULL");
+    if ((rc = require_device())) return rc;
+    return run_sliced(p, slices, workspace, workspace_bytes, tls().stream);
+}
+
+int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offsets[8]) {
+    clear_error();
+    if (offsets == nullptr) return fail(-5, "sliced_layout: offsets is NULL");
+    if (slices < 0 || slices > kMaxSlices) return fail(-4, "sliced_layout: slices");
+    return sliced_layout(m, n, k, slices, offsets);
+}
+
+int mp_dd_workspace_status(const void *workspace, int *status) {
+    clear_error();
+    if (workspace == nullptr) return fail(-1, "workspace_status: workspace is NULL");
+    if (status == nullptr) return fail(-2, "workspace_status: status is NULL");
+    return read_status(workspace, status);
+}
+
 int mp_dd_peak_fp64(double *rate) {
     clear_error();
     if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");

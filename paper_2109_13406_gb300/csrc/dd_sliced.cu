@@ -1,0 +1,697 @@
+// Split-precision dd Rgemm on the fp16 tensor cores (tcgen05, sm_103a).
+//
+// C := alpha op(A) op(B) + beta C with the products of op(A) op(B) formed
+// from error-free integer slices (the Ozaki scheme):
+//
+//  1. Scaling.  Row i of op(A) gets e_i with max_l |A_il| < 2^(e_i - 1); column
+//     j of op(B) gets f_j likewise.  Then |a 2^-e_i| < 1/2 for every entry.
+//  2. Slicing.  Each dd entry x = hi + lo of row i becomes the integer
+//     X = RNE(hi 2^(8S - e_i)) + RNE(lo 2^(8S - e_i))  (|x 2^(8S-e_i) - X| <= 1)
+//     written in balanced base 256: X = sum_{t<S} d_t 256^(S-1-t), with
+//     d_t in [-128, 128].  Each digit plane is stored as fp16 (exact) in a
+//     K-major [row][k] layout padded to the tile sizes with zeros.
+//  3. Band products.  For b = 0 .. S-1 the exact integer matrix
+//     P_b = sum_{t+u=b} D_A[t] D_B[u]^T is computed on the tensor cores with
+//     fp32 accumulation in tensor memory, drained every 512 products: a run
+//     of 512 products of |d| <= 128 stays within 2^23, so every partial sum
+//     is an integer the fp32 accumulator holds exactly.  The drained values
+//     are summed in int32 registers (|P_b| < 2^31 for k (b+1) 2^14 < 2^31).
+//     Pairs with t + u >= S are dropped (triangular truncation).
+//  4. Recombination.  V = sum_b P_b 256^(S-1-b) is formed exactly in 192-bit
+//     integer arithmetic, rounded once to the nearest dd and scaled by
+//     2^(e_i + f_j - 8S - 8); the alpha/beta epilogue is dd arithmetic.
+//
+// Error: per product |a b - sum_{t+u<S} d_t d'_u 256^-(t+u+2) 2^(e_i+f_j)|
+// <= ~4.3 2^(e_i + f_j - 8S); with S = 14 and entries whose row/column
+// maxima are within a few binades of the entries themselves this is a
+// small fraction of the bound 4 k 2^-104 (|alpha||A||B| + |beta||C|).
+//
+// Only the scaling epilogue uses the FP64 pipe (about 30 instructions per
+// output entry); slicing and recombination are integer arithmetic, and the
+// O(mnk) work runs on the tensor cores.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "dd_arith.cuh"
+#include "kernels.cuh"
+#include "sm100.cuh"
+
+namespace mpdd {
+namespace {
+
+using namespace sm100;
+
+constexpr int TM = 128, TN = 128, TK = 64;   // output tile and k-block
+constexpr int STAGES = 6;                   // smem ring depth (32 KB per stage)
+constexpr int CHUNK_KB = 8;                 // k-blocks per exact fp32 run (512 products)
+constexpr int GROUP_N = 8;                  // tile columns per rasterisation group
+constexpr int kEpiWarps = 8;                // two warps per tensor-memory lane quadrant
+constexpr int kEpiCols = TN / 2;            // accumulator columns per epilogue thread
+constexpr int kThreadsGemm = 32 * (2 + kEpiWarps);  // producer, MMA, epilogue
+constexpr int kTmemCols = 2 * TN;           // two fp32 accumulator buffers
+constexpr uint32_t kStageBytes = (TM + TN) * TK * 2;
+
+// ------------------------------------------------------------------ layout
+
+struct Layout {
+    int64_t m, n, k, S, m_pad, n_pad, k_pad;
+    size_t off_rowmax, off_colmax, off_da, off_db, off_p, total;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+Layout make_layout(int64_t m, int64_t n, int64_t k, int S) {
+    Layout L{};
+    L.m = m; L.n = n; L.k = k; L.S = S;
+    L.m_pad = ceil_div(imax(m, 1), TM) * TM;
+    L.n_pad = ceil_div(imax(n, 1), TN) * TN;
+    L.k_pad = ceil_div(imax(k, 1), TK) * TK;
+    size_t o = 1024;  // header: status word and call parameters
+    L.off_rowmax = o; o = align_up(o + 8 * (size_t)L.m_pad, 1024);
+    L.off_colmax = o; o = align_up(o + 8 * (size_t)L.n_pad, 1024);
+    L.off_da = o; o = align_up(o + 2 * (size_t)S * L.m_pad * L.k_pad, 1024);
+    L.off_db = o; o = align_up(o + 2 * (size_t)S * L.n_pad * L.k_pad, 1024);
+    L.off_p = o; o = align_up(o + 4 * (size_t)S * L.n_pad * L.m_pad, 1024);
+    L.total = o;
+    return L;
+}
+
+// ------------------------------------------------------------------ step 1
+
+// Running maximum of |hi| (as the bit pattern of a non-negative double, which
+// orders like the value) over row r of a column-major plane viewed as
+// rows x k: element (r, l) at X[r + l*ld] (row_contig) or X[l + r*ld].
+__global__ void absmax_kernel(const double *__restrict__ X, int64_t ld, int row_contig,
+                              int64_t rows, int64_t k, int64_t lchunk,
+                              unsigned long long *__restrict__ out) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    int64_t l0 = (int64_t)blockIdx.y * lchunk, l1 = l0 + lchunk < k ? l0 + lchunk : k;
+    unsigned long long mx = 0;
+    for (int64_t l = l0; l < l1; ++l) {
+        double v = row_contig ? X[r + l * ld] : X[l + r * ld];
+        unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+        mx = b > mx ? b : mx;
+    }
+    if (mx) atomicMax(out + r, mx);
+}
+
+// e with max |x| < 2^(e-1): from the biased exponent E of the maximum,
+// max in [2^(E-1023), 2^(E-1022)) -> e = E - 1021 (E = 0, subnormal: same).
+__device__ __forceinline__ int scale_exponent(unsigned long long maxbits) {
+    if (maxbits == 0) return 0;
+    return (int)(maxbits >> 52) - 1021;
+}
+
+// ------------------------------------------------------------------ step 2
+
+// RNE(v * 2^s) as a signed 128-bit integer, by integer operations on the
+// binary64 fields (|v 2^s| < 2^127 by construction).
+__device__ __forceinline__ __int128 scaled_round(double v, int s) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    int E = (int)((bits >> 52) & 0x7FF);
+    unsigned long long mant = bits & ((1ull << 52) - 1);
+    int ex;
+    if (E == 0) {
+        ex = 1 - 1075;
+    } else {
+        mant |= 1ull << 52;
+        ex = E - 1075;
+    }
+    if (mant == 0) return 0;
+    int sh = ex + s;
+    __int128 r;
+    if (sh >= 0) {
+        r = (__int128)((unsigned __int128)mant << sh);
+    } else {
+        int rs = -sh;
+        if (rs > 54) {
+            r = 0;
+        } else {
+            unsigned long long q = mant >> rs;
+            unsigned long long rem = mant & ((1ull << rs) - 1);
+            unsigned long long half = 1ull << (rs - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+            r = (__int128)q;
+        }
+    }
+    return (bits >> 63) ? -r : r;
+}
+
+// Digits of 8 consecutive entries (l0 .. l0+7) of one row, written as S
+// planes of 8 fp16 values (16 bytes each).
+template <int S>
+__device__ __forceinline__ void slice8(const double *__restrict__ Xh,
+                                       const double *__restrict__ Xl, int64_t ld, int row_contig,
+                                       int64_t r, int64_t rows, int64_t l0, int64_t k, int shift,
+                                       __half *__restrict__ D, int64_t rows_pad, int64_t k_pad) {
+    __half2 out[S][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        int dg[2][S];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int64_t l = l0 + e + h;
+            double hi = 0.0, lo = 0.0;
+            if (r < rows && l < k) {
+                int64_t off = row_contig ? (r + l * ld) : (l + r * ld);
+                hi = Xh[off];
+                lo = Xl[off];
+            }
+            __int128 X = scaled_round(hi, shift) + scaled_round(lo, shift);
+            unsigned __int128 u = (unsigned __int128)X;
+            int carry = 0;
+#pragma unroll
+            for (int t = S - 1; t >= 1; --t) {
+                int byte = (int)((unsigned)(u >> (8 * (S - 1 - t))) & 0xFFu) + carry;
+                carry = byte >= 128;
+                dg[h][t] = byte - (carry << 8);
+            }
+            dg[h][0] = (int)(X >> (8 * (S - 1))) + carry;
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            out[t][e / 2] = __halves2half2(__int2half_rn(dg[0][t]), __int2half_rn(dg[1][t]));
+    }
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        uint4 v;
+        memcpy(&v, &out[t][0], 16);
+        *reinterpret_cast<uint4 *>(D + ((int64_t)t * rows_pad + r) * k_pad + l0) = v;
+    }
+}
+
+// One thread per (row, 16 consecutive k): thread rows are consecutive, so the
+// row_contig reads coalesce; each digit store is 32 contiguous bytes.
+template <int S>
+__global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ Xh,
+                                                    const double *__restrict__ Xl, int64_t ld,
+                                                    int row_contig, int64_t rows, int64_t k,
+                                                    int64_t rows_pad, int64_t k_pad,
+                                                    const unsigned long long *__restrict__ rmax,
+                                                    __half *__restrict__ D) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows_pad) return;
+    int64_t l0 = (int64_t)blockIdx.y * 16;
+    int e = r < rows ? scale_exponent(rmax[r]) : 0;
+    int shift = 8 * S - e;
+    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0, k, shift, D, rows_pad, k_pad);
+    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0 + 8, k, shift, D, rows_pad, k_pad);
+}
+
+// ------------------------------------------------------------------ step 3
+
+struct BandArgs {
+    int S, kb_count, tiles_m, tiles_n;
+    int64_t m_pad, n_pad;
+    int32_t *P;   // [S][n_pad][m_pad]
+    int *status;
+};
+
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int &tm,
+                                            int &tn) {
+    int group = tile / (tiles_m * GROUP_N);
+    int first = group * GROUP_N;
+    int gn = tiles_n - first < GROUP_N ? tiles_n - first : GROUP_N;
+    int local = tile - group * tiles_m * GROUP_N;
+    tn = first + local % gn;
+    tm = local / gn;
+}
+
+__global__ void __launch_bounds__(kThreadsGemm, 1)
+    band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                     const __grid_constant__ CUtensorMap tmB, const BandArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * TM * TK * 2;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint64_t *acce = accf + 2;
+    uint64_t *fin = acce + 2;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(fin + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 32 * kEpiWarps);
+        }
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_holder, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    const int num_tiles = p.tiles_m * p.tiles_n;
+    const int KB = p.kb_count, S = p.S;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            prefetch_tmap(&tmA);
+            prefetch_tmap(&tmB);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+                int tm, tn;
+                tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+                for (int b = 0; b < S && ok; ++b)
+                    for (int t = 0; t <= b && ok; ++t) {
+                        const int ya = (int)(t * p.m_pad) + tm * TM;
+                        const int yb = (int)((b - t) * p.n_pad) + tn * TN;
+                        for (int kb = 0; kb < KB; ++kb, ++it) {
+                            const int s = it % STAGES;
+                            const uint32_t f = it / STAGES;
+                            if (!mbar_wait(&empty[s], (f & 1) ^ 1, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&full[s], kStageBytes);
+                            tma_load_2d(sA + s * TM * TK * 2, &tmA, &full[s], kb * TK, ya);
+                            tma_load_2d(sB + s * TN * TK * 2, &tmB, &full[s], kb * TK, yb);
+                        }
+                    }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                const uint32_t first = it > STAGES ? it - STAGES : 0;
+                for (uint32_t j = first; j < it; ++j) {
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1) &&
+                           clock64() - t0 < kWaitCycles / 4) {
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16_f32(TM, TN);
+            uint32_t it = 0, chunk = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+                for (int b = 0; b < S && ok; ++b) {
+                    const int steps = (b + 1) * KB;
+                    int sidx = 0;
+                    for (int t = 0; t <= b && ok; ++t)
+                        for (int kb = 0; kb < KB; ++kb, ++it, ++sidx) {
+                            const int s = it % STAGES;
+                            const uint32_t f = it / STAGES;
+                            const bool first = (sidx % CHUNK_KB) == 0;
+                            const bool last = ((sidx + 1) % CHUNK_KB) == 0 || sidx + 1 == steps;
+                            const uint32_t buf = chunk & 1, use = chunk >> 1;
+                            if (first) {
+                                if (!mbar_wait(&acce[buf], (use & 1) ^ 1, abort_flag)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc_fence_after();
+                            }
+                            if (!mbar_wait(&full[s], f & 1, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t d = tmem + buf * TN;
+                            const uint32_t a0 = smem_u32(sA + s * TM * TK * 2);
+                            const uint32_t b0 = smem_u32(sB + s * TN * TK * 2);
+#pragma unroll
+                            for (int kk = 0; kk < TK / 16; ++kk)
+                                mma_f16(d, desc_sw128_kmajor(a0 + kk * 32),
+                                        desc_sw128_kmajor(b0 + kk * 32), idesc,
+                                        (first && kk == 0) ? 0u : 1u);
+                            mma_commit(&empty[s]);
+                            if (last) {
+                                mma_commit(&accf[buf]);
+                                ++chunk;
+                            }
+                        }
+                }
+            }
+            // every issued MMA has completed before the tensor memory is freed
+            mma_commit(fin);
+            long long t0 = clock64();
+            while (!mbar_try_wait(fin, 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: drain chunks into int32 band sums
+        const int q = warp % 4;                 // tensor-memory lane quadrant
+        const int col0 = ((warp - 2) / 4) * kEpiCols;  // first accumulator column
+        const int row = q * 32 + lane;          // row of the tile this thread owns
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        uint32_t chunk = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+            int tm, tn;
+            tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+            for (int b = 0; b < S && ok; ++b) {
+                int32_t acc[kEpiCols];
+#pragma unroll
+                for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
+                const int steps = (b + 1) * KB;
+                const int nchunks = (steps + CHUNK_KB - 1) / CHUNK_KB;
+                for (int c = 0; c < nchunks; ++c, ++chunk) {
+                    const uint32_t buf = chunk & 1, use = chunk >> 1;
+                    if (!mbar_wait(&accf[buf], use & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int cc = 0; cc < kEpiCols / 16; ++cc) {
+                        uint32_t r[16];
+                        tmem_ld_32x32b_x16(tmem + lane_base + buf * TN + col0 + cc * 16, r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            acc[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&acce[buf]);
+                }
+                if (!ok) break;
+                int32_t *dst = p.P + ((int64_t)b * p.n_pad + (int64_t)tn * TN + col0) * p.m_pad +
+                               (int64_t)tm * TM + row;
+#pragma unroll
+                for (int j = 0; j < kEpiCols; ++j) dst[(int64_t)j * p.m_pad] = acc[j];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, MP_DD_ERR_TIMEOUT);
+}
+
+// ------------------------------------------------------------------ step 4
+
+struct RecArgs {
+    int S;
+    int64_t m, n, m_pad, n_pad;
+    const int32_t *P;
+    const unsigned long long *rmax, *cmax;
+    mp_dd alpha, beta;
+    int alpha_one, beta_zero;
+    double *ch, *cl;
+    int64_t ldc;
+};
+
+// x * 2^e, exact for results in the normal range.
+__device__ __forceinline__ double mul_pow2(double x, int e) {
+    while (e > 1000) {
+        x = __dmul_rn(x, __longlong_as_double((long long)(1000 + 1023) << 52));
+        e -= 1000;
+    }
+    while (e < -1000) {
+        x = __dmul_rn(x, __longlong_as_double((long long)(-1000 + 1023) << 52));
+        e += 1000;
+    }
+    return __dmul_rn(x, __longlong_as_double((long long)(e + 1023) << 52));
+}
+
+__device__ __forceinline__ int msb64(unsigned long long x) { return 63 - __clzll(x); }
+
+// Signed 128-bit integer to the nearest binary64.
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    bool neg = v < 0;
+    unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    double r;
+    if (hi == 0) {
+        r = __ull2double_rn(lo);
+    } else {
+        int p = 64 + msb64(hi);               // >= 64
+        int sh = p - 63;                      // keep the top 64 bits
+        unsigned __int128 top = a >> sh;
+        unsigned long long w = (unsigned long long)top;
+        unsigned __int128 dropped = a & (((unsigned __int128)1 << sh) - 1);
+        if (dropped != 0) w |= 1ull;          // sticky bit below the rounding point
+        r = mul_pow2(__ull2double_rn(w), sh);
+    }
+    return neg ? -r : r;
+}
+
+__global__ void __launch_bounds__(256) recombine_kernel(const RecArgs p) {
+    const int64_t total = p.m * p.n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % p.m, j = idx / p.m;
+        // V = sum_b P_b 256^(S-1-b) in 192-bit two's complement (hi:lo)
+        unsigned __int128 lo = 0;
+        long long hi = 0;
+        for (int b = 0; b < p.S; ++b) {
+            const int32_t v = p.P[((int64_t)b * p.n_pad + j) * p.m_pad + i];
+            hi = (long long)(((unsigned long long)hi << 8) | (unsigned long long)(lo >> 120));
+            lo <<= 8;
+            const unsigned __int128 ext = (unsigned __int128)(__int128)(long long)v;
+            const unsigned __int128 sum = lo + ext;
+            hi += (sum < lo ? 1 : 0) + (v < 0 ? -1 : 0);
+            lo = sum;
+        }
+        const bool neg = hi < 0;
+        if (neg) {
+            lo = ~lo + 1;
+            hi = (long long)(~(unsigned long long)hi + (lo == 0 ? 1ull : 0ull));
+        }
+        double vh = 0.0, vl = 0.0;
+        const unsigned long long w2 = (unsigned long long)hi;
+        const unsigned long long w1 = (unsigned long long)(lo >> 64), w0 = (unsigned long long)lo;
+        int pbit = -1;
+        if (w2) pbit = 128 + msb64(w2);
+        else if (w1) pbit = 64 + msb64(w1);
+        else if (w0) pbit = msb64(w0);
+        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 8 * p.S - 8;
+        if (pbit >= 0 && pbit <= 52) {
+            vh = mul_pow2(__ull2double_rn(w0), sc);
+        } else if (pbit > 52) {
+            const int q = pbit - 52;          // <= 88 for |V| < 2^141
+            const unsigned __int128 shifted =
+                (lo >> q) | (q < 128 ? ((unsigned __int128)w2 << (128 - q)) : 0);
+            unsigned long long H = (unsigned long long)shifted;
+            const unsigned __int128 mask = ((unsigned __int128)1 << q) - 1;
+            const unsigned __int128 R = lo & mask;
+            const unsigned __int128 half = (unsigned __int128)1 << (q - 1);
+            __int128 Rs = (__int128)R;
+            if (R > half || (R == half && (H & 1))) {
+                ++H;
+                Rs = (__int128)R - ((__int128)1 << q);
+            }
+            vh = mul_pow2(__ull2double_rn(H), q + sc);
+            vl = mul_pow2(i128_to_double(Rs), sc);
+        }
+        if (neg) {
+            vh = -vh;
+            vl = -vl;
+        }
+        dd v{vh, vl};
+        if (!p.alpha_one) v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
+        const int64_t off = i + j * p.ldc;
+        if (!p.beta_zero) v = add(v, mul(dd{p.beta.hi, p.beta.lo}, dd{p.ch[off], p.cl[off]}));
+        p.ch[off] = v.hi;
+        p.cl[off] = v.lo;
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a [rows][k_pad] fp16 digit array, box 64 (k) x box_rows.
+int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(MP_DD_ERR_NO_DEVICE, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(MP_DD_ERR_NO_DEVICE, "cuTensorMapEncodeTiled failed: CUresult %d", (int)r);
+    return 0;
+}
+
+int launch_absmax(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
+                  unsigned long long *out, cudaStream_t st) {
+    if (rows == 0 || k == 0) return 0;
+    const int64_t lchunk = 256;
+    dim3 grid((unsigned)ceil_div(rows, 128), (unsigned)ceil_div(k, lchunk));
+    if (grid.y > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for the scaling pass");
+    absmax_kernel<<<grid, 128, 0, st>>>(X, ld, row_contig, rows, k, lchunk, out);
+    return check_launch("absmax_kernel");
+}
+
+template <int S>
+void launch_slice_s(const double *Xh, const double *Xl, int64_t ld, int row_contig,
+                    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+                    const unsigned long long *rmax, __half *D, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(rows_pad, 128), (unsigned)(k_pad / 16));
+    slice_kernel<S><<<grid, 128, 0, st>>>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad,
+                                          rmax, D);
+}
+
+int launch_slice(int S, const double *Xh, const double *Xl, int64_t ld, int row_contig,
+                 int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+                 const unsigned long long *rmax, __half *D, cudaStream_t st) {
+    if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for slicing");
+#define MPDD_SLICE_CASE(SS)                                                                 \
+    case SS:                                                                                \
+        launch_slice_s<SS>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, D, st); \
+        break;
+    switch (S) {
+        MPDD_SLICE_CASE(2) MPDD_SLICE_CASE(3) MPDD_SLICE_CASE(4) MPDD_SLICE_CASE(5)
+        MPDD_SLICE_CASE(6) MPDD_SLICE_CASE(7) MPDD_SLICE_CASE(8) MPDD_SLICE_CASE(9)
+        MPDD_SLICE_CASE(10) MPDD_SLICE_CASE(11) MPDD_SLICE_CASE(12) MPDD_SLICE_CASE(13)
+        MPDD_SLICE_CASE(14) MPDD_SLICE_CASE(15)
+        default:
+            return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, 15]", S);
+    }
+#undef MPDD_SLICE_CASE
+    return check_launch("slice_kernel");
+}
+
+}  // namespace
+
+size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int S) {
+    if (S == 0) S = kDefaultSlices;
+    return make_layout(m, n, k, S).total;
+}
+
+int sliced_layout(int64_t m, int64_t n, int64_t k, int S, size_t *offsets) {
+    if (S == 0) S = kDefaultSlices;
+    Layout L = make_layout(m, n, k, S);
+    offsets[0] = L.off_rowmax;
+    offsets[1] = L.off_colmax;
+    offsets[2] = L.off_da;
+    offsets[3] = L.off_db;
+    offsets[4] = L.off_p;
+    offsets[5] = (size_t)L.m_pad;
+    offsets[6] = (size_t)L.n_pad;
+    offsets[7] = (size_t)L.k_pad;
+    return 0;
+}
+
+int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (S == 0) S = kDefaultSlices;
+    if (S < 2 || S > kMaxSlices)
+        return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, %d]", S, kMaxSlices);
+    // |P_b| <= (b + 1) k 2^14 must stay below 2^31 for the int32 band sums
+    if ((int64_t)S * p.k > ((int64_t)1 << 17) - 1)
+        return fail(MP_DD_ERR_TOO_LARGE, "k * slices = %lld exceeds 131071",
+                    (long long)(S * p.k));
+    Layout L = make_layout(p.m, p.n, p.k, S);
+    if (ws == nullptr || ws_bytes < L.total)
+        return fail(MP_DD_ERR_WORKSPACE, "sliced Rgemm needs %zu workspace bytes, got %zu",
+                    L.total, ws_bytes);
+    if (L.n_pad * (int64_t)S > 0x7fffffffLL || L.m_pad * (int64_t)S > 0x7fffffffLL)
+        return fail(MP_DD_ERR_TOO_LARGE, "matrix too large for the sliced path");
+    if (p.alpha_zero) return launch_gemm_plain(p, st);  // C := beta C only
+
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    cudaError_t e = cudaMemsetAsync(w, 0, L.off_da, st);  // status word and maxima
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    auto *rmax = reinterpret_cast<unsigned long long *>(w + L.off_rowmax);
+    auto *cmax = reinterpret_cast<unsigned long long *>(w + L.off_colmax);
+    auto *DA = reinterpret_cast<__half *>(w + L.off_da);
+    auto *DB = reinterpret_cast<__half *>(w + L.off_db);
+    auto *P = reinterpret_cast<int32_t *>(w + L.off_p);
+    int *status = reinterpret_cast<int *>(w);
+
+    // op(A) rows: A[i + l lda] when transa = N; op(B) columns as rows: B[l + j ldb]
+    // when transb = N (contiguous in l), B[j + l ldb] when transb = T.
+    const int a_rc = p.ta ? 0 : 1, b_rc = p.tb ? 1 : 0;
+    int rc;
+    if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
+    if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
+    if ((rc = launch_slice(S, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax, DA,
+                           st)))
+        return rc;
+    if ((rc = launch_slice(S, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax, DB,
+                           st)))
+        return rc;
+
+    CUtensorMap tmA, tmB;
+    if ((rc = make_tmap(&tmA, DA, (int64_t)S * L.m_pad, L.k_pad, TM))) return rc;
+    if ((rc = make_tmap(&tmB, DB, (int64_t)S * L.n_pad, L.k_pad, TN))) return rc;
+    BandArgs ba{};
+    ba.S = S;
+    ba.kb_count = (int)(L.k_pad / TK);
+    ba.tiles_m = (int)(L.m_pad / TM);
+    ba.tiles_n = (int)(L.n_pad / TN);
+    ba.m_pad = L.m_pad;
+    ba.n_pad = L.n_pad;
+    ba.P = P;
+    ba.status = status;
+    const size_t smem = STAGES * kStageBytes + 1024 + 256;
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [smem] {
+        cudaFuncSetAttribute(band_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    });
+    const int tiles = ba.tiles_m * ba.tiles_n;
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    band_gemm_kernel<<<grid, kThreadsGemm, smem, st>>>(tmA, tmB, ba);
+    if ((rc = check_launch("band_gemm_kernel"))) return rc;
+
+    RecArgs ra{};
+    ra.S = S;
+    ra.m = p.m; ra.n = p.n; ra.m_pad = L.m_pad; ra.n_pad = L.n_pad;
+    ra.P = P; ra.rmax = rmax; ra.cmax = cmax;
+    ra.alpha = p.alpha; ra.beta = p.beta;
+    ra.alpha_one = p.alpha_one; ra.beta_zero = p.beta_zero;
+    ra.ch = p.ch; ra.cl = p.cl; ra.ldc = p.ldc;
+    const int64_t total = p.m * p.n;
+    int64_t blocks = ceil_div(total, 256);
+    if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
+    recombine_kernel<<<(unsigned)blocks, 256, 0, st>>>(ra);
+    return check_launch("recombine_kernel");
+}
+
+int read_status(const void *ws, int *status) {
+    cudaError_t e = cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "status read");
+}
+
+}  // namespace mpdd

@@ -32,4 +32,12 @@ int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream);
 // FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.
 int run_peak_fp64(cudaStream_t stream, double *rate);
 
+// Split-precision (sliced) Rgemm on the fp16 tensor cores.
+constexpr int kDefaultSlices = 14;  // base-256 digits per operand entry
+constexpr int kMaxSlices = 15;      // the slicing integer must fit 128 bits
+size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
+int sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
+int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t stream);
+int read_status(const void *ws, int *status);
+
 }  // namespace mpdd
