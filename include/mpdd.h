@@ -182,6 +182,31 @@ int mp_dd_Rgemm_sliced(const char *transa, const char *transb, int64_t m, int64_
                        int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices,
                        void *workspace, size_t workspace_bytes);
 
+/* Allocation-free form of mp_dd_Rgemm_sliced (the manual has no
+ * counterpart).  For callers that keep the MPBLAS Rgemm argument list (no
+ * workspace argument) in a program where the library may not allocate
+ * device memory: an application that hands all device memory to its own
+ * pool at start-up, or a latency-critical loop that must never reach a
+ * cudaMalloc.  The scratch memory is a fixed array of
+ * MP_DD_NOALLOC_SCRATCH_BYTES compiled into the library; every device on
+ * which the library's device code is loaded holds it until the process
+ * exits.  Neither this call nor anything it calls allocates or frees memory.
+ * Same arguments 1-14, result and errors as mp_dd_Rgemm_sliced; a problem
+ * whose workspace (mp_dd_Rgemm_sliced_workspace) exceeds the array --
+ * e.g. anything above m = n = k = 512 at the default 14 slices -- is
+ * rejected with 2002 before any device work.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it; make that first call before any stream
+ * capture starts.  All calls share the one array, which keeps the last
+ * call's contents: each call clears what must start at zero itself, and
+ * calls that overlap on the GPU (different streams or unordered threads)
+ * race on it and give wrong results.  The device status word is the first
+ * 4 bytes of the array (not readable through mp_dd_workspace_status). */
+#define MP_DD_NOALLOC_SCRATCH_BYTES (32u << 20)
+int mp_dd_Rgemm_sliced_noalloc(const char *transa, const char *transb, int64_t m, int64_t n,
+                               int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
+                               int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices);
+
 /* Byte offsets of the intermediate arrays inside a sliced-Rgemm workspace
  * (for inspection and testing): offsets[0] row maxima of op(A) (uint64 bit
  * patterns of max |hi|, m_pad entries), [1] column maxima of op(B) (n_pad),

@@ -25,7 +25,7 @@ from ._abi import MpDD, MpDDCMat, MpDDMat
 __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
-    "mp_dd_Rgemm_sliced_workspace", "mp_dd_sliced_layout", "mp_dd_workspace_status", "Rgemm",
+    "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout", "mp_dd_workspace_status", "Rgemm",
     "Rsyrk", "Rgemm_sliced", "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
 
@@ -144,6 +144,17 @@ def mp_dd_Rgemm_sliced(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, 
                                  _cm(B), ldb, _dd(beta), _m(C), ldc, slices, _ptr(workspace),
                                  workspace_bytes)
     return _check(rc, "mp_dd_Rgemm_sliced") if check else rc
+
+
+def mp_dd_Rgemm_sliced_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                               slices=0, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgemm_sliced_noalloc(_flag(transa), _flag(transb), m, n, k, _dd(alpha),
+                                         _cm(A), lda, _cm(B), ldb, _dd(beta), _m(C), ldc, slices)
+    return _check(rc, "mp_dd_Rgemm_sliced_noalloc") if check else rc
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20   # MP_DD_NOALLOC_SCRATCH_BYTES in include/mpdd.h
 
 
 def mp_dd_sliced_layout(m, n, k, slices=0) -> dict:

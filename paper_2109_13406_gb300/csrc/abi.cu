@@ -299,6 +299,21 @@ int mp_dd_Rgemm_sliced(const char *transa, const char *transb, int64_t m, int64_
     return run_sliced(p, slices, workspace, workspace_bytes, tls().stream);
 }
 
+int mp_dd_Rgemm_sliced_noalloc(const char *transa, const char *transb, int64_t m, int64_t n,
+                               int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
+                               int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_gemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, p);
+    if (rc) return rc;
+    if (slices != 0 && (slices < 2 || slices > kMaxSlices))
+        return fail(-14, "Rgemm_sliced_noalloc: slices = %d outside [2, %d]", slices,
+                    kMaxSlices);
+    if (quick_return(p)) return 0;
+    if ((rc = require_device())) return rc;
+    return run_sliced_noalloc(p, slices, tls().stream);
+}
+
 int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offsets[8]) {
     clear_error();
     if (offsets == nullptr) return fail(-5, "sliced_layout: offsets is NULL");

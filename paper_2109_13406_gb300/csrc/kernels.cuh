@@ -40,4 +40,8 @@ int sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
 int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t stream);
 int read_status(const void *ws, int *status);
 
+// Sliced Rgemm on the library's built-in scratch array (no allocation).
+size_t noalloc_scratch_bytes();
+int run_sliced_noalloc(const GemmArgs &p, int slices, cudaStream_t stream);
+
 }  // namespace mpdd
