@@ -50,10 +50,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "sliced"])
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sliced", action="store_true")
+    ap.add_argument("--sliced-size", type=int, default=8192)
     return ap.parse_args()
 
 
@@ -227,6 +229,13 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, mp, torch, nn, tn, syrk, world)
+    sliced = None
+    if not args.no_sliced:
+        del dnn, dtn, dsy
+        torch.cuda.empty_cache()
+        sliced = {"vs_plain_2048": sliced_section(mp, torch, 2048, compare_plain=True),
+                  "well_scaled": sliced_section(mp, torch, args.sliced_size),
+                  "ill_scaled_outer": sliced_section(mp, torch, args.sliced_size, ill="outer")}
     if rank == 0:
         cpu = None if args.no_cpu or world > 1 else cpu_baseline(size, budget_s=15.0)
         line = {
@@ -243,12 +252,104 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "sliced": sliced,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# sliced (split-precision, tensor-core) dd Rgemm
+# ----------------------------------------------------------------------------
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def tensor_peak_tflops():
+    """Measured dense bf16 peak (burst) of the GB300s; fp16 runs at the
+    same nominal rate, so it is the fp16 denominator too."""
+    try:
+        return float(json.load(open(MEASURED))["bf16_tflops"]), "measured (bf16 burst, = fp16 rate)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
+
+
+def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=False):
+    """Time mp_dd_Rgemm_sliced (NN, m=n=k=size) with CUDA events on the
+    launching stream; per-phase times from the library's own events."""
+    c = datagen.gemm_case(2, "N", "N", size, size, size, ill=ill)
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    A, B, C = dev(c.A), dev(c.B), dev(c.C)
+    ws = mp.workspace(mp.mp_dd_Rgemm_sliced_workspace(size, size, size, slices))
+    st = torch.cuda.current_stream()
+
+    def call(Cout):
+        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta,
+                              Cout, size, slices, ws, ws.numel())
+
+    C0 = tuple(x.clone() for x in C)
+    call(C0)
+    torch.cuda.synchronize()
+    status = mp.mp_dd_workspace_status(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    mp.mp_dd_sliced_timing(True)
+    phases = []
+    e0.record(st)
+    for _ in range(reps):
+        Ct = tuple(x.clone() for x in C)
+        call(Ct)
+    e1.record(st)
+    torch.cuda.synchronize()
+    # per-phase times of the last call (clones sit between calls, not inside)
+    phases = mp.mp_dd_sliced_phase_ms()
+    mp.mp_dd_sliced_timing(False)
+    total_ms = sum(phases)
+    L = mp.mp_dd_sliced_layout(size, size, size, slices)
+    pairs = slices * (slices + 1) // 2
+    band_flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * pairs
+    peak, src = tensor_peak_tflops()
+    achieved = band_flops / (phases[1] * 1e-3) / 1e12
+    out = {
+        "workload": f"sliced dd Rgemm NN m=n=k={size}, {slices} slices, "
+                    f"{'well-scaled' if ill is None else ill + ' ill-scaled'}",
+        "ms": total_ms, "dd_GFlops": 2.0 * size ** 3 / (total_ms * 1e-3) / 1e9,
+        "phase_ms": {"scale_and_slice": phases[0], "band_products": phases[1],
+                     "recombine_epilogue": phases[2]},
+        "status": status,
+        "roofline_band_kernel": {"bound": "tensor", "kernel": "band_gemm_kernel",
+                                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": achieved / peak, "peak_source": src,
+                                 "algorithmic_flops": band_flops,
+                                 "traffic": None},
+    }
+    if compare_plain:
+        # the plain FP64 path on the same inputs, and their agreement measured
+        # against the accuracy bound (numpy |A||B| on sampled entries)
+        Cp = tuple(x.clone() for x in C)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(st)
+        mp.mp_dd_Rgemm("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta, Cp, size)
+        p1.record(st)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1)
+        g = datagen.rng(5)
+        rows = g.integers(0, size, 512)
+        cols = g.integers(0, size, 512)
+        s_h, s_l = (mp.to_numpy(x)[rows, cols] for x in C0)
+        p_h, p_l = (mp.to_numpy(x)[rows, cols] for x in Cp)
+        ab = np.einsum("ij,ji->i", np.abs(c.A[0][rows, :]), np.abs(c.B[0][:, cols]))
+        bound = 4 * size * 2.0 ** -104 * (abs(c.alpha[0]) * ab + abs(c.beta[0]) *
+                                          np.abs(c.C[0][rows, cols])) * (1 + 2.0 ** -40)
+        diff = np.abs((s_h - p_h) + (s_l - p_l))
+        out["plain"] = {"ms": plain_ms, "dd_GFlops": 2.0 * size ** 3 / (plain_ms * 1e-3) / 1e9,
+                        "speedup_sliced_over_plain": plain_ms / total_ms,
+                        "max_abs_diff_over_bound_512_entries": float(np.max(diff / bound))}
+    del A, B, C, C0, ws
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(args, mp, torch, nn, tn, syrk, world):
@@ -359,10 +460,104 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sliced_workload(args):
+    """--workload sliced: one step = one sliced dd Rgemm NN at m=n=k=size
+    (well-scaled inputs); value in dd-GFlop/s; e2e through the Python
+    binding with pinned host buffers copied in and the result copied out."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2109_13406_gb300 as mp
+
+    size, S = args.sliced_size, 14
+    c = datagen.gemm_case(2, "N", "N", size, size, size)
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    A, B, C = dev(c.A), dev(c.B), dev(c.C)
+    ws = mp.workspace(mp.mp_dd_Rgemm_sliced_workspace(size, size, size, S))
+    st = torch.cuda.current_stream()
+
+    def step():
+        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta, C,
+                              size, S, ws, ws.numel())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    band = []
+    t0.record(st)
+    for _ in range(args.steps):
+        mp.mp_dd_sliced_timing(True)
+        step()
+        band.append(mp.mp_dd_sliced_phase_ms())
+    t1.record(st)
+    torch.cuda.synchronize()
+    mp.mp_dd_sliced_timing(False)
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    value = 2.0 * size ** 3 * args.steps / (ms * 1e-3) / 1e9
+    L = mp.mp_dd_sliced_layout(size, size, size, S)
+    band_ms = sum(b[1] for b in band) / len(band)
+    flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * S * (S + 1) // 2
+    peak, src = tensor_peak_tflops()
+    ach = flops / (band_ms * 1e-3) / 1e12
+    # e2e: pinned host inputs -> device -> sliced Rgemm -> host result
+    pin = lambda pair: [torch.from_numpy(np.ascontiguousarray(np.asfortranarray(x).T))
+                        .pin_memory() for x in pair]
+    hA, hB, hC = pin(c.A), pin(c.B), pin(c.C)
+    hOut = [torch.empty_like(hC[0]).pin_memory(), torch.empty_like(hC[1]).pin_memory()]
+    dA = [torch.empty_like(x, device="cuda") for x in hA]
+    dB = [torch.empty_like(x, device="cuda") for x in hB]
+    dC = [torch.empty_like(x, device="cuda") for x in hC]
+
+    def e2e_step():
+        for d, h in zip(dA + dB + dC, hA + hB + hC):
+            d.copy_(h, non_blocking=True)
+        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, (dA[0], dA[1]), size,
+                              (dB[0], dB[1]), size, c.beta, (dC[0], dC[1]), size, S, ws,
+                              ws.numel())
+        for h, d in zip(hOut, dC):
+            h.copy_(d, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    tt = time.perf_counter()
+    n_e2e = max(1, min(args.steps, 3))
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - tt
+    mat = 16 * size * size
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor (exact integer slices) + i64",
+        "data": "synthetic (seeded PCG64; dd entries hi~U(-1,1), lo=hi*2^-53*U(-1,1) "
+                "renormalised; alpha,beta random dd in [0.5,2])",
+        "config": {"workload": f"sliced dd Rgemm NN m=n=k={size}, {S} slices, well-scaled",
+                   "m": size, "n": size, "k": size, "slices": S,
+                   "l2": f"inputs {3 * mat / 1e6:.0f} MB > 129 MB L2, no flush"},
+        "roofline": {"bound": "tensor", "kernel": "band_gemm_kernel", "achieved": ach,
+                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
+                     "traffic": None},
+        "phase_ms": {"scale_and_slice": band[-1][0], "band_products": band[-1][1],
+                     "recombine_epilogue": band[-1][2]},
+        "e2e": {"value": 2.0 * size ** 3 * n_e2e / dt / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": 3 * mat, "d2h_bytes_per_step": mat,
+                "api": "Python binding mp_dd_Rgemm_sliced, pinned host buffers"},
+        "gpu_launches": 7 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sliced":
+        run_sliced_workload(args)
     else:
         run_ours(args)
 

@@ -219,6 +219,15 @@ int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offs
 /* Read the device status word of a workspace (synchronous copy). */
 int mp_dd_workspace_status(const void *workspace, int *status);
 
+/* Per-phase timing of sliced calls (no counterpart in the manual).  With
+ * enable != 0, later mp_dd_Rgemm_sliced calls from this thread record CUDA
+ * events around their three phases on the current stream;
+ * mp_dd_sliced_phase_ms waits for the last timed call and writes the
+ * milliseconds of (0) scaling and slicing, (1) band products on the tensor
+ * cores, (2) recombination and epilogue.  Returns 2002 if no call was timed. */
+int mp_dd_sliced_timing(int enable);
+int mp_dd_sliced_phase_ms(float ms[3]);
+
 /* ------------------------------------------------------------------------ */
 /* Measured roofline denominators (no counterpart in the manual)             */
 /* ------------------------------------------------------------------------ */

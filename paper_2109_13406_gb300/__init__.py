@@ -171,6 +171,17 @@ def mp_dd_workspace_status(workspace) -> int:
     return st.value
 
 
+def mp_dd_sliced_timing(enable: bool) -> None:
+    _LIB.mp_dd_sliced_timing(1 if enable else 0)
+
+
+def mp_dd_sliced_phase_ms() -> list:
+    """[scaling + slicing, band products, recombination] of the last timed call (ms)."""
+    ms = (ctypes.c_float * 3)()
+    _check(_LIB.mp_dd_sliced_phase_ms(ms), "mp_dd_sliced_phase_ms")
+    return [float(x) for x in ms]
+
+
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
     """A device byte buffer for the calls that take a workspace."""
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)

@@ -55,6 +55,8 @@ SIGNATURES = {
                                           MpDDCMat, _i64, MpDD, MpDDMat, _i64, _int]),
     "mp_dd_sliced_layout": (_int, [_i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "mp_dd_workspace_status": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mp_dd_sliced_timing": (_int, [_int]),
+    "mp_dd_sliced_phase_ms": (_int, [ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None

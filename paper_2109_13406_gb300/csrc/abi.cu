@@ -328,6 +328,18 @@ int mp_dd_workspace_status(const void *workspace, int *status) {
     return read_status(workspace, status);
 }
 
+int mp_dd_sliced_timing(int enable) {
+    clear_error();
+    sliced_timing_enable(enable);
+    return 0;
+}
+
+int mp_dd_sliced_phase_ms(float ms[3]) {
+    clear_error();
+    if (ms == nullptr) return fail(-1, "sliced_phase_ms: ms is NULL");
+    return sliced_timing_read(ms);
+}
+
 int mp_dd_peak_fp64(double *rate) {
     clear_error();
     if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");

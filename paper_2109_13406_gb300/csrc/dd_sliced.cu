@@ -592,7 +592,40 @@ int launch_slice(int S, const double *Xh, const double *Xl, int64_t ld, int row_
     return check_launch("slice_kernel");
 }
 
+// Optional per-phase CUDA-event timing of sliced calls made by this thread
+// (scaling + slicing, band products, recombination).
+struct PhaseTimer {
+    bool on = false;
+    bool recorded = false;
+    cudaEvent_t ev[4] = {};
+    void mark(int i, cudaStream_t st) {
+        if (!on) return;
+        if (ev[i] == nullptr) cudaEventCreate(&ev[i]);
+        cudaEventRecord(ev[i], st);
+        if (i == 3) recorded = true;
+    }
+};
+
+PhaseTimer &timer() {
+    static thread_local PhaseTimer t;
+    return t;
+}
+
 }  // namespace
+
+void sliced_timing_enable(int on) {
+    timer().on = on != 0;
+    timer().recorded = false;
+}
+
+int sliced_timing_read(float *ms) {
+    PhaseTimer &t = timer();
+    if (!t.recorded) return fail(MP_DD_ERR_TOO_LARGE, "no timed sliced call on this thread");
+    cudaError_t e = cudaEventSynchronize(t.ev[3]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], t.ev[i], t.ev[i + 1]);
+    return 0;
+}
 
 size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int S) {
     if (S == 0) S = kDefaultSlices;
@@ -643,6 +676,7 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     // when transb = N (contiguous in l), B[j + l ldb] when transb = T.
     const int a_rc = p.ta ? 0 : 1, b_rc = p.tb ? 1 : 0;
     int rc;
+    timer().mark(0, st);
     if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
     if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
     if ((rc = launch_slice(S, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax, DA,
@@ -652,6 +686,7 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
                            st)))
         return rc;
 
+    timer().mark(1, st);
     CUtensorMap tmA, tmB;
     if ((rc = make_tmap(&tmA, DA, (int64_t)S * L.m_pad, L.k_pad, TM))) return rc;
     if ((rc = make_tmap(&tmB, DB, (int64_t)S * L.n_pad, L.k_pad, TN))) return rc;
@@ -674,6 +709,7 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     const int grid = tiles < sm_count() ? tiles : sm_count();
     band_gemm_kernel<<<grid, kThreadsGemm, smem, st>>>(tmA, tmB, ba);
     if ((rc = check_launch("band_gemm_kernel"))) return rc;
+    timer().mark(2, st);
 
     RecArgs ra{};
     ra.S = S;
@@ -686,7 +722,9 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
     recombine_kernel<<<(unsigned)blocks, 256, 0, st>>>(ra);
-    return check_launch("recombine_kernel");
+    rc = check_launch("recombine_kernel");
+    timer().mark(3, st);
+    return rc;
 }
 
 int read_status(const void *ws, int *status) {

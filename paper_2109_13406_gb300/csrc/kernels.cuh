@@ -39,6 +39,8 @@ size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
 int sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
 int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t stream);
 int read_status(const void *ws, int *status);
+void sliced_timing_enable(int on);
+int sliced_timing_read(float *ms);
 
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();
