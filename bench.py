@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="plain", choices=["plain", "sliced"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "sliced", "grouped"])
+    ap.add_argument("--groups", type=int, default=4096)
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -552,12 +553,104 @@ def run_sliced_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def grouped_problems_host(count: int, seed: int = 0):
+    """Config of the grouped workload: m, n, k log-uniform integers in
+    [16, 512], NN, alpha/beta random dd in [0.5, 2], entries as elsewhere."""
+    sizes = datagen.grouped_problems(seed, count)
+    return [datagen.gemm_case(100000 + i, "N", "N", int(m), int(n), int(k))
+            for i, (m, n, k) in enumerate(sizes)]
+
+
+def run_grouped_workload(args):
+    """--workload grouped: one step = the whole group of ``--groups``
+    problems in one CUDA-graph replay of the persistent grouped kernel; the
+    per-problem launch loop (one mp_dd_Rgemm call each) is timed beside it."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2109_13406_gb300 as mp
+    from paper_2109_13406_gb300 import grouped as gr
+
+    cases = grouped_problems_host(args.groups)
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    devs = [(dev(c.A), dev(c.B), dev(c.C)) for c in cases]
+    problems = [(c.transa, c.transb, c.m, c.n, c.k, c.alpha, A, B, c.beta, C)
+                for c, (A, B, C) in zip(cases, devs)]
+    t_tune = time.perf_counter()
+    table = gr.autotune()
+    t_tune = time.perf_counter() - t_tune
+    G = gr.GroupedGemm(problems, table)
+    G.capture()
+    for _ in range(args.warmup):
+        G.replay()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        G.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-problem launch loop on the same problems
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(st)
+    for c, (A, B, C) in zip(cases, devs):
+        mp.mp_dd_Rgemm("N", "N", c.m, c.n, c.k, c.alpha, A, c.m, B, c.k, c.beta, C, c.m)
+    l1.record(st)
+    torch.cuda.synchronize()
+    loop_ms = l0.elapsed_time(l1)
+    # untuned group (library default shapes) for comparison
+    Gd = gr.GroupedGemm(problems, None)
+    Gd.run()
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(st)
+    Gd.run()
+    d1.record(st)
+    torch.cuda.synchronize()
+    default_ms = d0.elapsed_time(d1)
+    flops = G.flops
+    macs = flops / 2.0
+    nbytes = sum(16.0 * (c.m * c.k + c.k * c.n + 2 * c.m * c.n) for c in cases)
+    achieved = FP64_OPS_PER_MAC * macs / (ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; m,n,k log-uniform integers in [16,512], NN, random dd "
+                "alpha/beta in [0.5,2])",
+        "config": {"workload": f"grouped dd Rgemm, {args.groups} problems, one CUDA-graph "
+                               "launch of the persistent kernel", "problems": args.groups,
+                   "total_dd_flops": flops,
+                   "l2": f"operands {nbytes / 1e9:.2f} GB > 129 MB L2, no flush"},
+        "roofline": {"bound": "alu", "kernel": "grouped_gemm_kernel", "achieved": achieved,
+                     "peak": NOMINAL_FP64_INSTR / 1e9, "unit": "GFP64instr/s",
+                     "frac": achieved / (NOMINAL_FP64_INSTR / 1e9),
+                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FP64 instr/s "
+                                    "(derived)", "traffic": None,
+                     "useful_over_padded_macs": macs / G.padded_macs()},
+        "hbm_GBs": nbytes / (ms * 1e-3) / 1e9,
+        "per_problem_loop": {"ms": loop_ms, "dd_GFlops": flops / (loop_ms * 1e-3) / 1e9,
+                             "launches": len(cases), "speedup_graph_over_loop": loop_ms / ms},
+        "untuned_default_shapes_ms": default_ms,
+        "autotune_seconds": t_tune,
+        "gpu_launches": 2 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "sliced":
         run_sliced_workload(args)
+    elif args.workload == "grouped":
+        run_grouped_workload(args)
     else:
         run_ours(args)
 

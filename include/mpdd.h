@@ -144,6 +144,51 @@ int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, 
                      mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
 
 /* ------------------------------------------------------------------------ */
+/* Grouped Rgemm: many independent problems in one launch (no counterpart    */
+/* in the manual, which batches nothing)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* One problem C := alpha op(A) op(B) + beta C of a group; fields as the
+ * mp_dd_Rgemm arguments (device pointers), transa/transb 0 = N, 1 = T, and
+ * tile the output tile shape: -1 = the library's choice (least zero-padded
+ * work weighted by per-shape speed), 0 = 32x32, 1 = 64x32, 2 = 32x64,
+ * 3 = 16x16 (m x n).  The shape changes speed only: every entry is bitwise
+ * equal to mp_dd_Rgemm's for the same problem. */
+typedef struct {
+    int64_t m, n, k;
+    mp_dd alpha, beta;
+    const double *a_hi, *a_lo;
+    int64_t lda;
+    const double *b_hi, *b_lo;
+    int64_t ldb;
+    double *c_hi, *c_lo;
+    int64_t ldc;
+    int32_t transa, transb;
+    int32_t tile;
+    int32_t reserved;
+} mp_dd_gemm_desc;
+
+/* Device workspace bytes a group of `count` host descriptors needs. */
+size_t mp_dd_Rgemm_grouped_workspace(int64_t count, const mp_dd_gemm_desc *descs);
+
+/* Check the host descriptors (DGEMM rules per problem; a bad one returns -2
+ * and mp_dd_last_error names it), cut every problem into tiles of its shape,
+ * order all tiles longest first (k x tile area), and copy descriptors and
+ * tile list into `workspace` (device memory owned by the caller).
+ * Synchronous.  The problems' matrices are not touched.  Errors: -1 count,
+ * -2 descriptor, -3 workspace NULL, 2003 workspace too small. */
+int mp_dd_Rgemm_grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *workspace,
+                                size_t workspace_bytes);
+
+/* Run a prepared group: resets the work counter and launches one persistent
+ * kernel whose CTAs take tiles from the list until it is empty.  Only
+ * enqueues work on the current stream (a memset and one kernel), so it can
+ * be captured in a CUDA graph and replayed; the group's matrices may change
+ * between runs, its descriptors may not.  Runs that share a workspace must
+ * not overlap on the device. */
+int mp_dd_Rgemm_grouped_run(void *workspace);
+
+/* ------------------------------------------------------------------------ */
 /* Split-precision Rgemm on the tensor cores (no counterpart in the manual)  */
 /* ------------------------------------------------------------------------ */
 

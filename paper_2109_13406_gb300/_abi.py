@@ -28,6 +28,19 @@ class MpDDMat(ctypes.Structure):
     _fields_ = [("hi", ctypes.c_void_p), ("lo", ctypes.c_void_p)]
 
 
+class MpDDGemmDesc(ctypes.Structure):
+    """``mp_dd_gemm_desc``: one problem of a grouped Rgemm (144 bytes)."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("alpha", MpDD), ("beta", MpDD),
+                ("a_hi", ctypes.c_void_p), ("a_lo", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("b_hi", ctypes.c_void_p), ("b_lo", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("c_hi", ctypes.c_void_p), ("c_lo", ctypes.c_void_p), ("ldc", ctypes.c_int64),
+                ("transa", ctypes.c_int32), ("transb", ctypes.c_int32),
+                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+assert ctypes.sizeof(MpDDGemmDesc) == 144
+
 _c = ctypes.c_char_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -56,6 +69,9 @@ SIGNATURES = {
     "mp_dd_sliced_layout": (_int, [_i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "mp_dd_workspace_status": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mp_dd_sliced_timing": (_int, [_int]),
+    "mp_dd_Rgemm_grouped_workspace": (_sz, [_i64, ctypes.POINTER(MpDDGemmDesc)]),
+    "mp_dd_Rgemm_grouped_prepare": (_int, [_i64, ctypes.POINTER(MpDDGemmDesc), _vp, _sz]),
+    "mp_dd_Rgemm_grouped_run": (_int, [_vp]),
     "mp_dd_sliced_phase_ms": (_int, [ctypes.POINTER(ctypes.c_float)]),
 }
 

@@ -328,6 +328,30 @@ int mp_dd_workspace_status(const void *workspace, int *status) {
     return read_status(workspace, status);
 }
 
+size_t mp_dd_Rgemm_grouped_workspace(int64_t count, const mp_dd_gemm_desc *descs) {
+    if (count < 0 || (count > 0 && descs == nullptr)) return 0;
+    return grouped_workspace_bytes(count, descs);
+}
+
+int mp_dd_Rgemm_grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *workspace,
+                                size_t workspace_bytes) {
+    clear_error();
+    if (count < 0) return fail(-1, "grouped_prepare: count < 0");
+    if (count > 0 && descs == nullptr) return fail(-2, "grouped_prepare: descs is NULL");
+    if (workspace == nullptr) return fail(-3, "grouped_prepare: workspace is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return grouped_prepare(count, descs, workspace, workspace_bytes, tls().stream);
+}
+
+int mp_dd_Rgemm_grouped_run(void *workspace) {
+    clear_error();
+    if (workspace == nullptr) return fail(-1, "grouped_run: workspace is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return grouped_run(workspace, tls().stream);
+}
+
 int mp_dd_sliced_timing(int enable) {
     clear_error();
     sliced_timing_enable(enable);

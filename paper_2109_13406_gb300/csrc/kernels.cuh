@@ -42,6 +42,12 @@ int read_status(const void *ws, int *status);
 void sliced_timing_enable(int on);
 int sliced_timing_read(float *ms);
 
+// Grouped dd Rgemm (one persistent launch over many problems).
+size_t grouped_workspace_bytes(int64_t count, const mp_dd_gemm_desc *descs);
+int grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *ws, size_t bytes,
+                    cudaStream_t stream);
+int grouped_run(void *ws, cudaStream_t stream);
+
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();
 int run_sliced_noalloc(const GemmArgs &p, int slices, cudaStream_t stream);
