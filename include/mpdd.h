@@ -144,6 +144,66 @@ int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, 
                      mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
 
 /* ------------------------------------------------------------------------ */
+/* MPLAPACK: dd Cholesky factorisation and solve                             */
+/* ------------------------------------------------------------------------ */
+
+/* Rpotrf (MPLAPACK routine table, Sec. 6; Rpotrf benchmark, Sec. 10.5;
+ * DPOTRF semantics): A = U^T U (uplo 'U', U in the upper triangle) or
+ * A = L L^T ('L'), A n x n symmetric positive definite, the other triangle
+ * not referenced.  Blocked right-looking in blocks of 64: unblocked dd
+ * Cholesky of each diagonal block, dd triangular solve for the panel, dd
+ * Rsyrk trailing update.  *info (DEVICE int64, required) receives 0 or
+ * j > 0 when the leading minor of order j is not positive definite; the
+ * factorisation stops there (later blocks are left as they were).
+ * Asynchronous.  Errors: -1 uplo, -2 n < 0, -3 A NULL, -4 lda < max(1,n),
+ * -5 info NULL. */
+int mp_dd_Rpotrf(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info);
+
+/* Rpotrs (DPOTRS semantics): solve A X = B with the factor from
+ * mp_dd_Rpotrf (same uplo); B (n x nrhs, ldb) is overwritten by X.  Blocked
+ * forward (U^T) and backward (U) substitution with dd Rgemm updates.
+ * factor_info (device, may be NULL): when it holds a non-zero value the
+ * solve leaves B unchanged.  Asynchronous.  Errors: -1 uplo, -2 n < 0,
+ * -3 nrhs < 0, -4 A NULL, -5 lda, -6 B NULL, -7 ldb < max(1, n). */
+int mp_dd_Rpotrs(const char *uplo, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_t lda,
+                 mp_dd_mat B, int64_t ldb, const int64_t *factor_info);
+
+/* Batched building blocks of the two routines (no counterpart in the
+ * manual), used to advance many independent factorisations in one launch.
+ * Descriptor arrays are DEVICE memory. */
+
+/* Unblocked dd Cholesky of one diagonal block (n <= 64) whose top-left
+ * element is a_hi/a_lo; lower selects the 'L' storage.  offset is the
+ * block's first column in the whole matrix (for info = offset + j + 1). */
+typedef struct {
+    double *a_hi, *a_lo;
+    int64_t lda, n, offset;
+    int64_t *info;
+    int32_t lower, reserved;
+} mp_dd_potrf_diag_desc;
+
+/* Solve U^T X = B (trans 1) or U X = B (trans 0) in place, U the n x n
+ * (n <= 64) upper factor block at u_hi/u_lo (lower_u: read it from 'L'
+ * storage), B n x nrhs at b_hi/b_lo (lower_b: B is stored transposed, as
+ * the panel of an 'L' factor is). */
+typedef struct {
+    const double *u_hi, *u_lo;
+    int64_t ldu;
+    double *b_hi, *b_lo;
+    int64_t ldb;
+    int64_t n, nrhs;
+    const int64_t *info;
+    int32_t trans, lower_u, lower_b, reserved;
+} mp_dd_trsm_desc;
+
+/* One launch: one CTA per diagonal block.  Errors: -1 count, -2 descs. */
+int mp_dd_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *descs);
+
+/* One launch over count descriptors, 32 right-hand-side columns per CTA;
+ * max_nrhs is the largest nrhs in the batch.  Errors: -1, -2, -3. */
+int mp_dd_trsm_batch(int64_t count, const mp_dd_trsm_desc *descs, int64_t max_nrhs);
+
+/* ------------------------------------------------------------------------ */
 /* Grouped Rgemm: many independent problems in one launch (no counterpart    */
 /* in the manual, which batches nothing)                                     */
 /* ------------------------------------------------------------------------ */
@@ -165,7 +225,10 @@ typedef struct {
     int64_t ldc;
     int32_t transa, transb;
     int32_t tile;
-    int32_t reserved;
+    int32_t uplo;             /* 0 = all of C; 1 / 2 = only the upper / lower
+                                 triangle of a square C (Rsyrk-style update) */
+    const int64_t *info;      /* optional device word: if non-zero when the
+                                 kernel reaches this problem, C is left as is */
 } mp_dd_gemm_desc;
 
 /* Device workspace bytes a group of `count` host descriptors needs. */

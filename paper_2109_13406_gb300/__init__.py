@@ -206,6 +206,31 @@ def Rgemm_sliced(transa, transb, alpha, A, B, beta, C, m=None, n=None, k=None, s
     return ws
 
 
+def mp_dd_Rpotrf(uplo, n, A, lda, info, check=True):
+    """info: a device int64 tensor (one element) that receives LAPACK's info."""
+    _sync_stream()
+    rc = _LIB.mp_dd_Rpotrf(_flag(uplo), n, _m(A), lda, _ptr(info))
+    return _check(rc, "mp_dd_Rpotrf") if check else rc
+
+
+def mp_dd_Rpotrs(uplo, n, nrhs, A, lda, B, ldb, factor_info=None, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rpotrs(_flag(uplo), n, nrhs, _cm(A), lda, _m(B), ldb, _ptr(factor_info))
+    return _check(rc, "mp_dd_Rpotrs") if check else rc
+
+
+def mp_dd_potrf_diag_batch(count, descs_dev, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_potrf_diag_batch(count, _ptr(descs_dev))
+    return _check(rc, "mp_dd_potrf_diag_batch") if check else rc
+
+
+def mp_dd_trsm_batch(count, descs_dev, max_nrhs, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_trsm_batch(count, _ptr(descs_dev), max_nrhs)
+    return _check(rc, "mp_dd_trsm_batch") if check else rc
+
+
 def mp_dd_peak_fp64() -> float:
     _sync_stream()
     r = ctypes.c_double()

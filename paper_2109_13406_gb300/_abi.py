@@ -36,10 +36,27 @@ class MpDDGemmDesc(ctypes.Structure):
                 ("b_hi", ctypes.c_void_p), ("b_lo", ctypes.c_void_p), ("ldb", ctypes.c_int64),
                 ("c_hi", ctypes.c_void_p), ("c_lo", ctypes.c_void_p), ("ldc", ctypes.c_int64),
                 ("transa", ctypes.c_int32), ("transb", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("uplo", ctypes.c_int32),
+                ("info", ctypes.c_void_p)]
 
 
-assert ctypes.sizeof(MpDDGemmDesc) == 144
+assert ctypes.sizeof(MpDDGemmDesc) == 152
+
+
+class MpDDPotrfDiagDesc(ctypes.Structure):
+    """``mp_dd_potrf_diag_desc``."""
+    _fields_ = [("a_hi", ctypes.c_void_p), ("a_lo", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("offset", ctypes.c_int64), ("info", ctypes.c_void_p),
+                ("lower", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class MpDDTrsmDesc(ctypes.Structure):
+    """``mp_dd_trsm_desc``."""
+    _fields_ = [("u_hi", ctypes.c_void_p), ("u_lo", ctypes.c_void_p), ("ldu", ctypes.c_int64),
+                ("b_hi", ctypes.c_void_p), ("b_lo", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("info", ctypes.c_void_p),
+                ("trans", ctypes.c_int32), ("lower_u", ctypes.c_int32),
+                ("lower_b", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 _c = ctypes.c_char_p
 _i64 = ctypes.c_int64
@@ -69,6 +86,10 @@ SIGNATURES = {
     "mp_dd_sliced_layout": (_int, [_i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
     "mp_dd_workspace_status": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mp_dd_sliced_timing": (_int, [_int]),
+    "mp_dd_Rpotrf": (_int, [_c, _i64, MpDDMat, _i64, _vp]),
+    "mp_dd_Rpotrs": (_int, [_c, _i64, _i64, MpDDCMat, _i64, MpDDMat, _i64, _vp]),
+    "mp_dd_potrf_diag_batch": (_int, [_i64, _vp]),
+    "mp_dd_trsm_batch": (_int, [_i64, _vp, _i64]),
     "mp_dd_Rgemm_grouped_workspace": (_sz, [_i64, ctypes.POINTER(MpDDGemmDesc)]),
     "mp_dd_Rgemm_grouped_prepare": (_int, [_i64, ctypes.POINTER(MpDDGemmDesc), _vp, _sz]),
     "mp_dd_Rgemm_grouped_run": (_int, [_vp]),

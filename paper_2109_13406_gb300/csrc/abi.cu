@@ -328,6 +328,61 @@ int mp_dd_workspace_status(const void *workspace, int *status) {
     return read_status(workspace, status);
 }
 
+int mp_dd_Rpotrf(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info) {
+    clear_error();
+    int ul = uplo_flag(uplo);
+    if (ul < 0) return fail(-1, "Rpotrf: illegal uplo");
+    if (n < 0) return fail(-2, "Rpotrf: n < 0");
+    if (n > 0 && (A.hi == nullptr || A.lo == nullptr)) return fail(-3, "Rpotrf: A is NULL");
+    if (lda < imax(1, n)) return fail(-4, "Rpotrf: lda < max(1, n)");
+    if (info == nullptr) return fail(-5, "Rpotrf: info is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), tls().stream);
+        return e == cudaSuccess ? 0 : cuda_fail(e, "info reset");
+    }
+    return run_potrf(ul == 2, n, A.hi, A.lo, lda, info, tls().stream);
+}
+
+int mp_dd_Rpotrs(const char *uplo, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_t lda,
+                 mp_dd_mat B, int64_t ldb, const int64_t *factor_info) {
+    clear_error();
+    int ul = uplo_flag(uplo);
+    if (ul < 0) return fail(-1, "Rpotrs: illegal uplo");
+    if (n < 0) return fail(-2, "Rpotrs: n < 0");
+    if (nrhs < 0) return fail(-3, "Rpotrs: nrhs < 0");
+    if (n > 0 && (A.hi == nullptr || A.lo == nullptr)) return fail(-4, "Rpotrs: A is NULL");
+    if (lda < imax(1, n)) return fail(-5, "Rpotrs: lda < max(1, n)");
+    if (n > 0 && nrhs > 0 && (B.hi == nullptr || B.lo == nullptr))
+        return fail(-6, "Rpotrs: B is NULL");
+    if (ldb < imax(1, n)) return fail(-7, "Rpotrs: ldb < max(1, n)");
+    if (n == 0 || nrhs == 0) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    return run_potrs(ul == 2, n, nrhs, A.hi, A.lo, lda, B.hi, B.lo, ldb, factor_info,
+                     tls().stream);
+}
+
+int mp_dd_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *descs) {
+    clear_error();
+    if (count < 0) return fail(-1, "potrf_diag_batch: count < 0");
+    if (count > 0 && descs == nullptr) return fail(-2, "potrf_diag_batch: descs is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return launch_potrf_diag_batch(count, descs, tls().stream);
+}
+
+int mp_dd_trsm_batch(int64_t count, const mp_dd_trsm_desc *descs, int64_t max_nrhs) {
+    clear_error();
+    if (count < 0) return fail(-1, "trsm_batch: count < 0");
+    if (count > 0 && descs == nullptr) return fail(-2, "trsm_batch: descs is NULL");
+    if (max_nrhs < 0) return fail(-3, "trsm_batch: max_nrhs < 0");
+    int rc = require_device();
+    if (rc) return rc;
+    return launch_trsm_batch(count, descs, max_nrhs, tls().stream);
+}
+
 size_t mp_dd_Rgemm_grouped_workspace(int64_t count, const mp_dd_gemm_desc *descs) {
     if (count < 0 || (count > 0 && descs == nullptr)) return 0;
     return grouped_workspace_bytes(count, descs);

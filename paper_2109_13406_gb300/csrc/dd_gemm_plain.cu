@@ -57,6 +57,7 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &p, int64_t &bi, int6
 template <int TA, int TB>
 __global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
     __shared__ PlainSmem s;
+    if (p.info != nullptr && *p.info != 0) return;  // an earlier step failed
     int64_t bi, bj;
     tile_coords(p, bi, bj);
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;

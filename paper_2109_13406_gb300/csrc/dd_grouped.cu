@@ -65,6 +65,7 @@ __device__ __forceinline__ void dd_tile(const mp_dd_gemm_desc &d, int64_t bi, in
     constexpr int BM = 16 * RM, BN = 16 * RN;
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     const int64_t i0 = bi * BM, j0 = bj * BN;
+    if (d.info != nullptr && *d.info != 0) return;   // the problem's owner failed earlier
     const bool alpha_zero = (d.alpha.hi == 0.0 && d.alpha.lo == 0.0) || d.k == 0;
     const int64_t kk = alpha_zero ? 0 : d.k;
     const int ta = d.transa, tb = d.transb;
@@ -157,6 +158,7 @@ __device__ __forceinline__ void dd_tile(const mp_dd_gemm_desc &d, int64_t bi, in
         for (int c = 0; c < RN; ++c) {
             int64_t i = i0 + tx + 16 * r, j = j0 + ty + 16 * c;
             if (i >= d.m || j >= d.n) continue;
+            if ((d.uplo == 1 && i > j) || (d.uplo == 2 && i < j)) continue;
             dd v = alpha_one ? acc[r][c] : mul(alpha, acc[r][c]);
             int64_t off = i + j * d.ldc;
             if (!beta_zero) v = add(v, mul(beta, dd{d.c_hi[off], d.c_lo[off]}));
@@ -195,11 +197,24 @@ size_t tiles_offset(int64_t count) {
     return (desc_offset() + sizeof(mp_dd_gemm_desc) * (size_t)count + 255) / 256 * 256;
 }
 
+// Whether tile (bi, bj) of shape (bm x bn) holds any entry of the stored
+// triangle of a triangular (uplo != 0) problem.
+bool tile_in_triangle(int uplo, int64_t bi, int64_t bj, int bm, int bn) {
+    if (uplo == 1) return bi * bm <= (bj + 1) * bn - 1;   // some i <= j
+    if (uplo == 2) return (bi + 1) * bm - 1 >= bj * bn;   // some i >= j
+    return true;
+}
+
 int64_t tiles_of(const mp_dd_gemm_desc &d, int shape) {
     int rm, rn;
     shape_dims(shape, rm, rn);
     if (d.m == 0 || d.n == 0) return 0;
-    return ceil_div(d.m, 16 * rm) * ceil_div(d.n, 16 * rn);
+    const int64_t tm = ceil_div(d.m, 16 * rm), tn = ceil_div(d.n, 16 * rn);
+    if (d.uplo == 0) return tm * tn;
+    int64_t c = 0;
+    for (int64_t bj = 0; bj < tn; ++bj)
+        for (int64_t bi = 0; bi < tm; ++bi) c += tile_in_triangle(d.uplo, bi, bj, 16 * rm, 16 * rn);
+    return c;
 }
 
 // Default shape when a descriptor leaves it to the library (tile < 0): the
@@ -234,6 +249,8 @@ int check_desc(const mp_dd_gemm_desc &d, int64_t idx) {
         return fail(-2, "grouped: descriptor %lld: leading dimension too small", (long long)idx);
     if (d.tile > 3) return fail(-2, "grouped: descriptor %lld: tile shape %d", (long long)idx,
                                 d.tile);
+    if (d.uplo < 0 || d.uplo > 2 || (d.uplo != 0 && d.m != d.n))
+        return fail(-2, "grouped: descriptor %lld: uplo needs 0..2 and m == n", (long long)idx);
     bool need_ab = d.m > 0 && d.n > 0 && d.k > 0 && !(d.alpha.hi == 0.0 && d.alpha.lo == 0.0);
     if (need_ab && (!d.a_hi || !d.a_lo || !d.b_hi || !d.b_lo))
         return fail(-2, "grouped: descriptor %lld: NULL operand", (long long)idx);
@@ -280,7 +297,8 @@ int grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *ws, size_
             return fail(MP_DD_ERR_TOO_LARGE, "grouped: problem %lld too large", (long long)i);
         for (int64_t bj = 0; bj < tn; ++bj)
             for (int64_t bi = 0; bi < tm; ++bi)
-                tiles.push_back(TileRef{(int32_t)i, (int32_t)bi, (int32_t)bj, s});
+                if (tile_in_triangle(dv[i].uplo, bi, bj, 16 * rm, 16 * rn))
+                    tiles.push_back(TileRef{(int32_t)i, (int32_t)bi, (int32_t)bj, s});
     }
     const size_t need = tiles_offset(count) + sizeof(TileRef) * (tiles.empty() ? 1 : tiles.size());
     if (ws == nullptr) return fail(-3, "grouped: workspace is NULL");

@@ -24,6 +24,7 @@ struct GemmArgs {
     int alpha_zero;  // alpha == 0: A and B are not read
     int alpha_one;   // alpha == 1: the product is stored without scaling
     int beta_zero;   // beta == 0: C is write-only
+    const int64_t *info = nullptr;  // optional device word: non-zero -> leave C as is
 };
 
 // Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).
@@ -47,6 +48,16 @@ size_t grouped_workspace_bytes(int64_t count, const mp_dd_gemm_desc *descs);
 int grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *ws, size_t bytes,
                     cudaStream_t stream);
 int grouped_run(void *ws, cudaStream_t stream);
+
+// dd Cholesky (blocked, LAPACK order) and its building blocks.
+int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
+              cudaStream_t stream);
+int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double *al,
+              int64_t lda, double *bh, double *bl, int64_t ldb, const int64_t *info,
+              cudaStream_t stream);
+int launch_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *ds, cudaStream_t st);
+int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
+                      cudaStream_t st);
 
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();

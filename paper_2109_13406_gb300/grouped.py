@@ -25,7 +25,8 @@ from ._abi import MpDDGemmDesc
 SHAPES = {0: (32, 32), 1: (64, 32), 2: (32, 64), 3: (16, 16)}
 
 
-def desc(transa, transb, m, n, k, alpha, A, B, beta, C, tile=-1) -> MpDDGemmDesc:
+def desc(transa, transb, m, n, k, alpha, A, B, beta, C, tile=-1, uplo=0,
+         info=None) -> MpDDGemmDesc:
     """Descriptor of one problem on column-major dd tensors (hi, lo)."""
     d = MpDDGemmDesc()
     d.m, d.n, d.k = int(m), int(n), int(k)
@@ -36,6 +37,8 @@ def desc(transa, transb, m, n, k, alpha, A, B, beta, C, tile=-1) -> MpDDGemmDesc
     d.transa = 1 if transa.upper() in "TC" else 0
     d.transb = 1 if transb.upper() in "TC" else 0
     d.tile = int(tile)
+    d.uplo = int(uplo)
+    d.info = None if info is None else info.data_ptr()
     return d
 
 

@@ -1,0 +1,260 @@
+"""Continuous-batching server of dd SPD solves: F = Rsyrk(G), Rpotrf(F), Rpotrs.
+
+Each request brings G (n x 2n) and B (n x nrhs) as dd matrices.  Its work is
+a fixed list of operations on its own device buffers:
+
+  * F := G G^T (upper triangle) as 2n/nb chunked Rsyrk updates F += G_c G_c^T
+    over column chunks G_c of G (so no single operation is large enough to
+    hold a scheduler step hostage);
+  * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
+    factorisation, the panel solve U_JJ^T X = F(J, J+1:), and the trailing
+    update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) (upper triangle);
+  * the solve F X = B: blocked forward (U^T) and backward (U) substitution.
+
+A scheduler step takes the next operation of every admitted request and runs
+all of them in at most three launches: one grouped dd Rgemm launch for every
+Rsyrk/Rgemm-type operation (``mp_dd_Rgemm_grouped``), one batched diagonal
+factorisation (``mp_dd_potrf_diag_batch``) and one batched triangular solve
+(``mp_dd_trsm_batch``).  Requests arriving while others run are admitted as
+soon as a slot and device memory (the budget) are free, and join the next
+step.  A request's operation sequence and every operation's arithmetic are
+independent of which other requests share the step, so each result is
+bitwise the same alone and in the mix.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_trsm_batch, to_device, to_numpy,
+               workspace)
+from . import grouped as gr
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    G: tuple | None     # (hi, lo) n x 2n, column-major: numpy (host) or torch (device)
+    B: tuple | None     # (hi, lo) n x nrhs
+    arrival: float = 0.0
+    nrhs_: int = 4
+    loader: object = None   # callable returning (G, B) at admission, when G is None
+    # filled in by the server
+    admit_t: float = 0.0
+    done_t: float = 0.0
+    ops: list = field(default_factory=list)
+    pos: int = 0
+    dev: dict = field(default_factory=dict)
+    X: tuple | None = None
+    info: int = 0
+
+    @property
+    def nrhs(self) -> int:
+        return int(self.B[0].shape[1]) if self.B is not None else self.nrhs_
+
+    def footprint(self) -> int:
+        """Device bytes while admitted: G, F, X planes and the info word."""
+        n = self.n
+        return 16 * (2 * n * n + n * n + n * self.nrhs) + 64
+
+    def flops(self) -> float:
+        """dd operation count: Rsyrk k n (n+1) with k = 2n, Rpotrf n^3/3,
+        Rpotrs 2 n^2 nrhs (the LAPACK counts)."""
+        n = float(self.n)
+        return 2 * n * n * (n + 1) + n ** 3 / 3 + 2 * n * n * self.nrhs
+
+
+def _view(P, r0, c0, rows, cols):
+    return P[r0:r0 + rows, c0:c0 + cols]
+
+
+def _pair(D, r0, c0, rows, cols):
+    return (_view(D[0], r0, c0, rows, cols), _view(D[1], r0, c0, rows, cols))
+
+
+class SpdServer:
+    """Admission, per-request operation lists and the batched scheduler step."""
+
+    def __init__(self, budget_bytes: float = 120e9, slots: int = 256, nb: int = 64,
+                 table: dict | None = None):
+        self.budget = float(budget_bytes)
+        self.slots = int(slots)
+        self.nb = int(nb)
+        self.table = table
+        self.active: list[Request] = []
+        self.used = 0
+        self.steps = 0
+        self.max_active = 0
+        self.launches = 0
+
+    # ---------------------------------------------------------------- admission
+
+    def can_admit(self, r: Request) -> bool:
+        return (len(self.active) < self.slots
+                and self.used + r.footprint() <= self.budget)
+
+    def admit(self, r: Request, now: float) -> None:
+        n, nrhs = r.n, r.nrhs
+        Gs, Bs = (r.G, r.B) if r.G is not None else r.loader()
+        G = tuple(x if isinstance(x, torch.Tensor) else to_device(x) for x in Gs)
+        F = tuple(torch.zeros((n, n), dtype=torch.float64, device="cuda").t()
+                  for _ in range(2))
+        X = tuple(x.clone() if isinstance(x, torch.Tensor) else to_device(x) for x in Bs)
+        info = torch.zeros(1, dtype=torch.int64, device="cuda")
+        r.dev = {"G": G, "F": F, "X": X, "info": info}
+        r.ops = self._plan(r)
+        r.pos = 0
+        r.admit_t = now
+        self.active.append(r)
+        self.used += r.footprint()
+        self.max_active = max(self.max_active, len(self.active))
+
+    def _plan(self, r: Request) -> list:
+        n, nrhs, nb = r.n, r.nrhs, self.nb
+        G, F, X, info = r.dev["G"], r.dev["F"], r.dev["X"], r.dev["info"]
+        ops = []
+        one, mone, zero = (1.0, 0.0), (-1.0, 0.0), (0.0, 0.0)
+        # F := G G^T, upper triangle, in column chunks of G
+        for c0 in range(0, 2 * n, nb):
+            w = min(nb, 2 * n - c0)
+            Gc = _pair(G, 0, c0, n, w)
+            ops.append(("gemm", ("N", "T", n, n, w, one, Gc, Gc, zero if c0 == 0 else one,
+                                 F, 1)))
+        # blocked Cholesky, upper
+        for j in range(0, n, nb):
+            b = min(nb, n - j)
+            ops.append(("diag", (_pair(F, j, j, b, b), b, j)))
+            rest = n - j - b
+            if rest > 0:
+                P = _pair(F, j, j + b, b, rest)
+                ops.append(("trsm", (_pair(F, j, j, b, b), P, b, rest, 1)))
+                ops.append(("gemm", ("T", "N", rest, rest, b, mone, P, P, one,
+                                     _pair(F, j + b, j + b, rest, rest), 1)))
+        # forward substitution U^T Y = B, then backward U X = Y
+        for j in range(0, n, nb):
+            b = min(nb, n - j)
+            ops.append(("trsm", (_pair(F, j, j, b, b), _pair(X, j, 0, b, nrhs), b, nrhs, 1)))
+            rest = n - j - b
+            if rest > 0:
+                ops.append(("gemm", ("T", "N", rest, nrhs, b, mone, _pair(F, j, j + b, b, rest),
+                                     _pair(X, j, 0, b, nrhs), one, _pair(X, j + b, 0, rest, nrhs),
+                                     0)))
+        for j in reversed(range(0, n, nb)):
+            b = min(nb, n - j)
+            ops.append(("trsm", (_pair(F, j, j, b, b), _pair(X, j, 0, b, nrhs), b, nrhs, 0)))
+            if j > 0:
+                ops.append(("gemm", ("N", "N", j, nrhs, b, mone, _pair(F, 0, j, j, b),
+                                     _pair(X, j, 0, b, nrhs), one, _pair(X, 0, 0, j, nrhs), 0)))
+        return ops
+
+    # ---------------------------------------------------------------- one step
+
+    def step(self) -> list[Request]:
+        """Run the next operation of every active request; return the requests
+        that finished (their results copied to the host)."""
+        gemm, diag, trsm = [], [], []
+        for r in self.active:
+            kind, args = r.ops[r.pos]
+            info = r.dev["info"]
+            if kind == "gemm":
+                ta, tb, m, n, k, al, A, B, be, C, uplo = args
+                gemm.append(gr.desc(ta, tb, m, n, k, al, A, B, be, C,
+                                    gr.shape_for(self.table, m, n), uplo, info))
+            elif kind == "diag":
+                P, b, off = args
+                d = _abi.MpDDPotrfDiagDesc()
+                d.a_hi, d.a_lo = P[0].data_ptr(), P[1].data_ptr()
+                d.lda, d.n, d.offset = P[0].stride(1), b, off
+                d.info, d.lower = info.data_ptr(), 0
+                diag.append(d)
+            else:
+                U, Bm, b, cols, trans = args
+                d = _abi.MpDDTrsmDesc()
+                d.u_hi, d.u_lo, d.ldu = U[0].data_ptr(), U[1].data_ptr(), U[0].stride(1)
+                d.b_hi, d.b_lo = Bm[0].data_ptr(), Bm[1].data_ptr()
+                d.ldb = max(Bm[0].stride(1), Bm[0].shape[0])
+                d.n, d.nrhs, d.info = b, cols, info.data_ptr()
+                d.trans, d.lower_u, d.lower_b = trans, 0, 0
+                trsm.append(d)
+        if gemm:
+            arr = gr.descs_array(gemm)
+            ws = workspace(gr.mp_dd_Rgemm_grouped_workspace(len(arr), arr))
+            gr.mp_dd_Rgemm_grouped_prepare(len(arr), arr, ws, ws.numel())
+            gr.mp_dd_Rgemm_grouped_run(ws)
+            self.launches += 1
+        if diag:
+            buf = _to_device_bytes((_abi.MpDDPotrfDiagDesc * len(diag))(*diag))
+            mp_dd_potrf_diag_batch(len(diag), buf)
+            self.launches += 1
+        if trsm:
+            buf = _to_device_bytes((_abi.MpDDTrsmDesc * len(trsm))(*trsm))
+            mp_dd_trsm_batch(len(trsm), buf, max(d.nrhs for d in trsm))
+            self.launches += 1
+        for r in self.active:
+            r.pos += 1
+        finished = [r for r in self.active if r.pos == len(r.ops)]
+        if finished:
+            torch.cuda.synchronize()
+            now = time.perf_counter()
+            for r in finished:
+                r.X = (to_numpy(r.dev["X"][0]), to_numpy(r.dev["X"][1]))
+                r.info = int(r.dev["info"].item())
+                r.done_t = now
+                self.used -= r.footprint()
+                r.dev = {}
+            self.active = [r for r in self.active if r.pos < len(r.ops)]
+        self.steps += 1
+        return finished
+
+    # ---------------------------------------------------------------- driver
+
+    def serve(self, requests: list[Request], time_scale: float = 1.0) -> list[Request]:
+        """Serve requests arriving at r.arrival seconds (relative to the start):
+        admit whatever has arrived and fits, run a step, repeat.  Returns the
+        requests in completion order with admit/done times on the same clock."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        done: list[Request] = []
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(pending) or self.active:
+            now = time.perf_counter() - t0
+            if i < len(pending) and pending[i].footprint() > self.budget:
+                raise ValueError(f"request {pending[i].rid} needs more than the memory budget")
+            while i < len(pending) and pending[i].arrival * time_scale <= now and \
+                    self.can_admit(pending[i]):
+                self.admit(pending[i], now)
+                i += 1
+            if not self.active:
+                if i < len(pending):
+                    time.sleep(max(0.0, min(0.002, pending[i].arrival * time_scale - now)))
+                continue
+            for r in self.step():
+                r.done_t -= t0
+                done.append(r)
+        return done
+
+
+def _to_device_bytes(carr) -> torch.Tensor:
+    raw = np.frombuffer(bytes(carr), dtype=np.uint8)
+    return torch.from_numpy(raw.copy()).to("cuda", non_blocking=False)
+
+
+def residual_ratio(F_host, X_host, B_host, mp) -> float:
+    """LAPACK test ratio ||B - F X||_1 / (||F||_1 ||X||_1 eps_dd) with the
+    residual computed by the library's dd Rgemm on the device (F symmetric,
+    both triangles given)."""
+    Fd = tuple(to_device(x) for x in F_host)
+    Xd = tuple(to_device(x) for x in X_host)
+    Rd = tuple(to_device(x) for x in B_host)
+    n, nrhs = F_host[0].shape[0], X_host[0].shape[1]
+    mp.mp_dd_Rgemm("N", "N", n, nrhs, n, (-1.0, 0.0), Fd, n, Xd, n, (1.0, 0.0), Rd, n)
+    torch.cuda.synchronize()
+    R = mp.to_numpy(Rd[0]) + mp.to_numpy(Rd[1])
+    fn = np.abs(F_host[0]).sum(axis=0).max()
+    xn = np.abs(X_host[0]).sum(axis=0).max()
+    return float(np.abs(R).sum(axis=0).max() / (fn * xn * 2.0 ** -104))

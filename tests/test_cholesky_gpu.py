@@ -1,0 +1,151 @@
+"""dd Rpotrf / Rpotrs and the continuous-batching SPD-solve server (GPU).
+
+Pins: exact recovery of an integer Cholesky factor (bit-exact), LAPACK test
+ratios (< 30, the manual's LAPACK test threshold) on an SPD matrix of
+condition ~1e20 with the residuals evaluated by the oracle's exact tier,
+agreement with the oracle's solution within cond * eps, LAPACK info for
+non-positive-definite input; the server's results are bitwise the same for a
+request served alone and in a mix, and agree with the single-matrix routines.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+from ddcheck import EPS_DD
+from gpucase import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_potrf(mp, uplo, Fh, Fl):
+    n = Fh.shape[0]
+    F = dev((Fh, Fl))
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    mp.mp_dd_Rpotrf(uplo, n, F, n, info)
+    torch.cuda.synchronize()
+    return F, int(info.item())
+
+
+@pytest.mark.parametrize("uplo", ["U", "L"])
+@pytest.mark.parametrize("n", [5, 64, 130])
+def test_integer_factor_recovered_exactly(cuda_lib, uplo, n):
+    g = datagen.rng(600 + n)
+    U = np.triu(g.integers(-3, 4, (n, n))).astype(np.float64)
+    np.fill_diagonal(U, g.integers(1, 5, n))
+    Fm = U.T @ U
+    assert np.abs(Fm).max() < 2 ** 52
+    F, info = gpu_potrf(cuda_lib, uplo, np.asfortranarray(Fm), np.zeros((n, n), order="F"))
+    assert info == 0
+    fh, fl = host(F)
+    if uplo == "U":
+        assert np.array_equal(np.triu(fh), U) and not np.triu(fl).any()
+    else:
+        assert np.array_equal(np.tril(fh), U.T) and not np.tril(fl).any()
+
+
+def test_not_positive_definite_info(cuda_lib):
+    Fm = np.diag([4.0, 9.0, -1.0, 16.0])
+    _, info = gpu_potrf(cuda_lib, "U", np.asfortranarray(Fm), np.zeros((4, 4), order="F"))
+    assert info == 3
+    n = 150
+    Fm = np.eye(n) * 4.0
+    Fm[99, 99] = -5.0                  # the leading minor of order 100 fails (block 2)
+    _, info = gpu_potrf(cuda_lib, "L", np.asfortranarray(Fm), np.zeros((n, n), order="F"))
+    assert info == 100
+
+
+def spd_problem(seed, n):
+    G, B = datagen.spd_request(seed, n)
+    Fd = oracle.dd_syrk("U", "N", (1.0, 0.0), G, (0.0, 0.0),
+                        (np.zeros((n, n), order="F"), np.zeros((n, n), order="F")))
+    Fs = tuple(np.asfortranarray(np.triu(P) + np.triu(P, 1).T) for P in Fd)
+    return G, B, Fs
+
+
+@pytest.mark.parametrize("uplo", ["U", "L"])
+def test_ill_conditioned_lapack_ratios_and_oracle(cuda_lib, uplo):
+    n = 150
+    G, B, Fs = spd_problem(610, n)
+    F, info = gpu_potrf(cuda_lib, uplo, *Fs)
+    assert info == 0
+    fh, fl = host(F)
+    Ut = (np.triu(fh), np.triu(fl)) if uplo == "U" else (np.tril(fh).T.copy(order="F"),
+                                                         np.tril(fl).T.copy(order="F"))
+    rr, cc = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    R = oracle.exact_gemm_entries("T", "N", n, (1.0, 0.0), Ut, Ut, (-1.0, 0.0), Fs,
+                                  rr.ravel(), cc.ravel())
+    fn = np.abs(Fs[0]).sum(axis=0).max()
+    ratio_f = np.abs(R[0].reshape(n, n)).sum(axis=0).max() / (n * fn * EPS_DD)
+    assert ratio_f < 30
+    X = dev(B)
+    cuda_lib.mp_dd_Rpotrs(uplo, n, 4, F, n, X, n)
+    xh, xl = host(X)
+    rr, cc = np.meshgrid(np.arange(n), np.arange(4), indexing="ij")
+    R = oracle.exact_gemm_entries("N", "N", n, (-1.0, 0.0), Fs, (xh, xl), (1.0, 0.0), B,
+                                  rr.ravel(), cc.ravel())
+    xn = np.abs(xh).sum(axis=0).max()
+    ratio_s = np.abs(R[0].reshape(n, 4)).sum(axis=0).max() / (fn * xn * EPS_DD)
+    assert ratio_s < 30
+    # the oracle's own factor-and-solve agrees to cond(F) * eps
+    oh, ol, oinfo = oracle.dd_potrf("U", Fs)
+    assert oinfo == 0
+    Xo = oracle.dd_potrs("U", (oh, ol), B)
+    rel = np.abs((xh - Xo[0]) + (xl - Xo[1])).max() / np.abs(Xo[0]).max()
+    assert rel < 1e20 * EPS_DD * 100
+
+
+def make_requests(seed, sizes):
+    from paper_2109_13406_gb300.server import Request
+
+    reqs = []
+    for i, n in enumerate(sizes):
+        G, B = datagen.spd_request(seed + i, int(n))
+        reqs.append(Request(rid=i, n=int(n), G=G, B=B, arrival=0.002 * i))
+    return reqs
+
+
+def test_server_alone_equals_mix_bitwise(cuda_lib):
+    from paper_2109_13406_gb300.server import SpdServer
+
+    sizes = [64, 100, 130, 70, 200, 90, 64, 160]
+    mix = SpdServer(slots=5).serve(make_requests(620, sizes))
+    assert sorted(r.rid for r in mix) == list(range(len(sizes)))
+    by_id = {r.rid: r for r in mix}
+    for i in (0, 4, 7):
+        alone = SpdServer().serve([make_requests(620, sizes)[i]])[0]
+        assert alone.info == 0 and by_id[i].info == 0
+        assert np.array_equal(alone.X[0], by_id[i].X[0])
+        assert np.array_equal(alone.X[1], by_id[i].X[1])
+
+
+def test_server_matches_single_matrix_routines(cuda_lib):
+    from paper_2109_13406_gb300.server import SpdServer
+
+    n = 130
+    r = SpdServer().serve(make_requests(630, [n]))[0]
+    G, B = datagen.spd_request(630, n)
+    Gd = dev(G)
+    F = cuda_lib.dd_empty(n, n, fill=0.0)
+    cuda_lib.mp_dd_Rsyrk("U", "N", n, 2 * n, (1.0, 0.0), Gd, n, (0.0, 0.0), F, n)
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cuda_lib.mp_dd_Rpotrf("U", n, F, n, info)
+    X = dev(B)
+    cuda_lib.mp_dd_Rpotrs("U", n, 4, F, n, X, n, info)
+    xh, xl = host(X)
+    rel = np.abs((xh - r.X[0]) + (xl - r.X[1])).max() / np.abs(xh).max()
+    assert rel < 1e20 * EPS_DD * 100
+
+
+def test_server_admission_respects_budget_and_slots(cuda_lib):
+    from paper_2109_13406_gb300.server import SpdServer
+
+    reqs = make_requests(640, [64, 80, 96, 64, 72, 88])
+    budget = 2.5 * max(r.footprint() for r in reqs)
+    srv = SpdServer(budget_bytes=budget, slots=2)
+    done = srv.serve(reqs)
+    assert len(done) == 6 and srv.max_active <= 2 and srv.used == 0
+    assert all(r.info == 0 for r in done)
