@@ -120,3 +120,28 @@ def test_config2_sampled_blocks_2048(cuda_lib, ill):
     rows, cols = sample_blocks(n, n, bs=16, count=8)
     ratio = check_against_exact(c, got, rows, cols)
     assert ratio <= 1.0
+
+
+def test_wide_tiles_4096x4096_k256_bands_and_result(cuda_lib):
+    """m = n = 4096 selects the 128 x 256 tile kernel: band sums at sampled
+    entries bit-exact against the integer oracle, the result within the bound."""
+    m = n = 4096
+    k, S = 256, 14
+    c = datagen.gemm_case(400, "N", "N", m, n, k)
+    got, ws = run_sliced(cuda_lib, c, S)
+    L = cuda_lib.mp_dd_sliced_layout(m, n, k, S)
+    assert L["n_pad"] % 256 == 0
+    g = datagen.rng(401)
+    rows = np.concatenate([[0, 127, 128, m - 1], g.integers(0, m, 12)])
+    cols = np.concatenate([[0, 255, 256, n - 1], g.integers(0, n, 12)])
+    Ah, Al = oz.op_rows(c.A, False, m, k)
+    Bh, Bl = oz.op_cols(c.B, False, k, n)
+    DA, _ = oz.split_matrix(Ah[rows], Al[rows], S)
+    DB, _ = oz.split_matrix(Bh[cols], Bl[cols], S)
+    P = oz.band_products(DA, DB)
+    mp_, np_ = L["m_pad"], L["n_pad"]
+    bands = ws_view(ws, L["bands"], S * np_ * mp_, np.int32).reshape(S, np_, mp_)
+    got_bands = bands[:, cols][:, :, rows].transpose(0, 2, 1).astype(np.int64)
+    assert np.array_equal(got_bands, P)
+    rr, cc = sample_blocks(m, n, bs=16, count=8)
+    assert check_against_exact(c, got, rr, cc) <= 1.0
