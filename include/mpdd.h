@@ -100,7 +100,8 @@ int mp_dd_version(void);
  * for B (k x n or n x k, ldb) and C (m x n, ldc >= max(1, m)).
  * Arithmetic: every multiply-add is dd arithmetic -- the exact product of
  * the hi parts by FMA plus the two cross products, accumulated with TwoSum
- * and renormalised after every step; the summation order over k is fixed
+ * (exact) with a FastTwoSum renormalisation every 4 steps of k (at the same
+ * k positions in every kernel); the summation order over k is fixed
  * (l = 0, 1, ..., k-1), so results are bitwise reproducible run to run and
  * independent of the launch configuration.  Accuracy: componentwise
  * |C - C_exact| <= 4 k 2^-104 (|alpha| |op(A)| |op(B)| + |beta| |C|).

@@ -56,6 +56,29 @@ __device__ __forceinline__ void mac(dd &acc, dd a, dd b) {
     acc_add(acc, p, e);
 }
 
+// GEMM-loop multiply-add with deferred renormalisation: the leading parts
+// are summed with TwoSum (exact), the TwoSum error and the product's low
+// part are added into acc.lo, and the FastTwoSum is left to renorm(), which
+// the GEMM kernels call after every kRenormEvery steps of k (at l = 3, 7, 11,
+// ... counted from the start of k, so every kernel renormalises at the same
+// places).  4 + 6 + 2 = 12 FP64 operations per step, 12.75 with the
+// renormalisation.  Between renormalisations |acc.lo| stays within a few
+// ulps of acc.hi, so each step's rounding error is at most ~(G+4) u^2
+// (|acc| + |a b|) with G = 4: within the Rgemm bound 4 k 2^-104 (...).  A
+// zero product leaves the state unchanged, so zero padding of k does not
+// alter the result.
+constexpr int kRenormEvery = 4;
+
+__device__ __forceinline__ void mac_deferred(dd &acc, dd a, dd b) {
+    double p, e, s, e1;
+    prod_terms(a, b, p, e);
+    two_sum(acc.hi, p, s, e1);
+    acc.hi = s;
+    acc.lo = __dadd_rn(acc.lo, __dadd_rn(e1, e));
+}
+
+__device__ __forceinline__ void renorm(dd &acc) { fast_two_sum(acc.hi, acc.lo, acc.hi, acc.lo); }
+
 // dd product, renormalised.
 __device__ __forceinline__ dd mul(dd a, dd b) {
     double p, e;

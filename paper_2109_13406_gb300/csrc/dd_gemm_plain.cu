@@ -4,9 +4,10 @@
 // alpha A A^T + beta C (Rsyrk), MPBLAS semantics (manual Sec. 7.3 and the
 // routine table of Sec. 6).  Every multiply-add is dd arithmetic: the exact
 // product of the hi parts by FMA, the two cross products, TwoSum into the
-// accumulator and a FastTwoSum renormalisation (dd_arith.cuh).
+// accumulator, and a FastTwoSum renormalisation every 4 steps of k
+// (dd_arith.cuh).
 //
-// On GB300 the FP64 pipe is the bottleneck by a wide margin (15 FP64
+// On GB300 the FP64 pipe is the bottleneck by a wide margin (12.75 FP64
 // instructions per dd multiply-add), so the kernel is organised to keep that
 // pipe busy and nothing else: each CTA owns a 64 x 64 tile of C, each thread
 // a 4 x 4 block of dd accumulators (16 independent dependency chains), and
@@ -122,17 +123,26 @@ __global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
             stage();
             __syncthreads();
             if (l0 + BK < kk) load(l0 + BK);
-#pragma unroll 2
-            for (int l = 0; l < BK; ++l) {
-                dd a[4], b[4];
+#pragma unroll 1
+            for (int l4 = 0; l4 < BK; l4 += kRenormEvery) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] = dd{s.ah[l][tx + 16 * r], s.al[l][tx + 16 * r]};
+                for (int l = l4; l < l4 + kRenormEvery; ++l) {
+                    dd a[4], b[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) b[c] = dd{s.bh[l][ty + 16 * c], s.bl[l][ty + 16 * c]};
+                    for (int r = 0; r < 4; ++r)
+                        a[r] = dd{s.ah[l][tx + 16 * r], s.al[l][tx + 16 * r]};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        b[c] = dd{s.bh[l][ty + 16 * c], s.bl[l][ty + 16 * c]};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) mac_deferred(acc[r][c], a[r], b[c]);
+                }
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) mac(acc[r][c], a[r], b[c]);
+                    for (int c = 0; c < 4; ++c) renorm(acc[r][c]);
             }
         }
     }

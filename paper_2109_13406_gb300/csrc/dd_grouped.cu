@@ -10,7 +10,7 @@
 // Device side (mp_dd_Rgemm_grouped_run): one launch of a persistent kernel,
 // one CTA per SM slot; CTAs take tiles from the list through an atomic
 // counter and run the same dd multiply-add as the plain kernel (TwoProd by
-// FMA, TwoSum, renormalisation; l = 0 .. k-1 in order), so every entry is
+// FMA, TwoSum, renormalisation every 4 steps; l = 0 .. k-1 in order), so every entry is
 // bitwise equal to what mp_dd_Rgemm produces for that problem alone,
 // whatever tile shape it was computed with.  run only enqueues a memset of
 // the counter and the kernel, so it can be captured in a CUDA graph.
@@ -18,7 +18,7 @@
 // Tile shapes: 16*RM x 16*RN with (RM, RN) in {(2,2), (4,2), (2,4), (1,1)};
 // the 256 threads form a 16 x 16 grid and each holds an RM x RN block of dd
 // accumulators.  Small shapes waste fewer zero-padded multiply-adds on
-// ragged problems (each costs the full 15 FP64 instructions); larger ones
+// ragged problems (each costs the full 12.75 FP64 instructions); larger ones
 // give each thread more independent chains.  All shapes fit 128 registers,
 // so two CTAs share an SM.
 #include <algorithm>
@@ -134,17 +134,26 @@ __device__ __forceinline__ void dd_tile(const mp_dd_gemm_desc &d, int64_t bi, in
             stage();
             __syncthreads();
             if (l0 + BK < kk) load(l0 + BK);
-#pragma unroll 2
-            for (int l = 0; l < BK; ++l) {
-                dd a[RM], b[RN];
+#pragma unroll 1
+            for (int l4 = 0; l4 < BK; l4 += kRenormEvery) {
 #pragma unroll
-                for (int r = 0; r < RM; ++r) a[r] = dd{s.ah[l][tx + 16 * r], s.al[l][tx + 16 * r]};
+                for (int l = l4; l < l4 + kRenormEvery; ++l) {
+                    dd a[RM], b[RN];
 #pragma unroll
-                for (int c = 0; c < RN; ++c) b[c] = dd{s.bh[l][ty + 16 * c], s.bl[l][ty + 16 * c]};
+                    for (int r = 0; r < RM; ++r)
+                        a[r] = dd{s.ah[l][tx + 16 * r], s.al[l][tx + 16 * r]};
+#pragma unroll
+                    for (int c = 0; c < RN; ++c)
+                        b[c] = dd{s.bh[l][ty + 16 * c], s.bl[l][ty + 16 * c]};
+#pragma unroll
+                    for (int r = 0; r < RM; ++r)
+#pragma unroll
+                        for (int c = 0; c < RN; ++c) mac_deferred(acc[r][c], a[r], b[c]);
+                }
 #pragma unroll
                 for (int r = 0; r < RM; ++r)
 #pragma unroll
-                    for (int c = 0; c < RN; ++c) mac(acc[r][c], a[r], b[c]);
+                    for (int c = 0; c < RN; ++c) renorm(acc[r][c]);
             }
         }
     }

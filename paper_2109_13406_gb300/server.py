@@ -3,9 +3,11 @@
 Each request brings G (n x 2n) and B (n x nrhs) as dd matrices.  Its work is
 a fixed list of operations on its own device buffers:
 
-  * F := G G^T (upper triangle) as 2n/nb chunked Rsyrk updates F += G_c G_c^T
-    over column chunks G_c of G (so no single operation is large enough to
-    hold a scheduler step hostage);
+  * F := G G^T: for n >= ``sliced_min_n`` one split-precision Rgemm on the
+    tensor cores (``mp_dd_Rgemm_sliced``, both triangles written, within the
+    same accuracy bound); for smaller n as 2n/nb chunked Rsyrk updates
+    F += G_c G_c^T over column chunks G_c of G (so no single FP64 operation
+    is large enough to hold a scheduler step hostage);
   * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
     factorisation, the panel solve U_JJ^T X = F(J, J+1:), and the trailing
     update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) (upper triangle);
@@ -30,8 +32,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_trsm_batch, to_device, to_numpy,
-               workspace)
+from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rgemm_sliced,
+               mp_dd_Rgemm_sliced_workspace, mp_dd_trsm_batch, to_device, to_numpy, workspace)
 from . import grouped as gr
 
 
@@ -57,10 +59,13 @@ class Request:
     def nrhs(self) -> int:
         return int(self.B[0].shape[1]) if self.B is not None else self.nrhs_
 
+    sliced_ws: int = 0    # workspace bytes of the sliced Rsyrk (0 = FP64 path)
+
     def footprint(self) -> int:
-        """Device bytes while admitted: G, F, X planes and the info word."""
+        """Device bytes while admitted: G, F, X planes, the info word and the
+        sliced-Rsyrk workspace when that path is used."""
         n = self.n
-        return 16 * (2 * n * n + n * n + n * self.nrhs) + 64
+        return 16 * (2 * n * n + n * n + n * self.nrhs) + 64 + self.sliced_ws
 
     def flops(self) -> float:
         """dd operation count: Rsyrk k n (n+1) with k = 2n, Rpotrf n^3/3,
@@ -81,7 +86,8 @@ class SpdServer:
     """Admission, per-request operation lists and the batched scheduler step."""
 
     def __init__(self, budget_bytes: float = 120e9, slots: int = 256, nb: int = 64,
-                 table: dict | None = None):
+                 table: dict | None = None, sliced_min_n: int = 256):
+        self.sliced_min_n = int(sliced_min_n)
         self.budget = float(budget_bytes)
         self.slots = int(slots)
         self.nb = int(nb)
@@ -95,10 +101,16 @@ class SpdServer:
     # ---------------------------------------------------------------- admission
 
     def can_admit(self, r: Request) -> bool:
+        self._size(r)
         return (len(self.active) < self.slots
                 and self.used + r.footprint() <= self.budget)
 
+    def _size(self, r: Request) -> None:
+        if r.n >= self.sliced_min_n and r.sliced_ws == 0:
+            r.sliced_ws = mp_dd_Rgemm_sliced_workspace(r.n, r.n, 2 * r.n, 0)
+
     def admit(self, r: Request, now: float) -> None:
+        self._size(r)
         n, nrhs = r.n, r.nrhs
         Gs, Bs = (r.G, r.B) if r.G is not None else r.loader()
         G = tuple(x if isinstance(x, torch.Tensor) else to_device(x) for x in Gs)
@@ -119,12 +131,15 @@ class SpdServer:
         G, F, X, info = r.dev["G"], r.dev["F"], r.dev["X"], r.dev["info"]
         ops = []
         one, mone, zero = (1.0, 0.0), (-1.0, 0.0), (0.0, 0.0)
-        # F := G G^T, upper triangle, in column chunks of G
-        for c0 in range(0, 2 * n, nb):
-            w = min(nb, 2 * n - c0)
-            Gc = _pair(G, 0, c0, n, w)
-            ops.append(("gemm", ("N", "T", n, n, w, one, Gc, Gc, zero if c0 == 0 else one,
-                                 F, 1)))
+        # F := G G^T
+        if r.sliced_ws:
+            ops.append(("sliced", (G, F)))
+        else:   # upper triangle, in column chunks of G
+            for c0 in range(0, 2 * n, nb):
+                w = min(nb, 2 * n - c0)
+                Gc = _pair(G, 0, c0, n, w)
+                ops.append(("gemm", ("N", "T", n, n, w, one, Gc, Gc,
+                                     zero if c0 == 0 else one, F, 1)))
         # blocked Cholesky, upper
         for j in range(0, n, nb):
             b = min(nb, n - j)
@@ -161,7 +176,14 @@ class SpdServer:
         for r in self.active:
             kind, args = r.ops[r.pos]
             info = r.dev["info"]
-            if kind == "gemm":
+            if kind == "sliced":
+                G, F = args
+                n = r.n
+                ws = workspace(r.sliced_ws)
+                mp_dd_Rgemm_sliced("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F,
+                                   n, 0, ws, ws.numel())
+                self.launches += 1
+            elif kind == "gemm":
                 ta, tb, m, n, k, al, A, B, be, C, uplo = args
                 gemm.append(gr.desc(ta, tb, m, n, k, al, A, B, be, C,
                                     gr.shape_for(self.table, m, n), uplo, info))

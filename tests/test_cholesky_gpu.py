@@ -111,21 +111,22 @@ def make_requests(seed, sizes):
 def test_server_alone_equals_mix_bitwise(cuda_lib):
     from paper_2109_13406_gb300.server import SpdServer
 
-    sizes = [64, 100, 130, 70, 200, 90, 64, 160]
+    # n >= 256 takes the tensor-core (sliced) Rsyrk, smaller n the FP64 one
+    sizes = [64, 100, 300, 70, 200, 90, 64, 260]
     mix = SpdServer(slots=5).serve(make_requests(620, sizes))
     assert sorted(r.rid for r in mix) == list(range(len(sizes)))
     by_id = {r.rid: r for r in mix}
-    for i in (0, 4, 7):
+    for i in (0, 2, 4, 7):
         alone = SpdServer().serve([make_requests(620, sizes)[i]])[0]
         assert alone.info == 0 and by_id[i].info == 0
         assert np.array_equal(alone.X[0], by_id[i].X[0])
         assert np.array_equal(alone.X[1], by_id[i].X[1])
 
 
-def test_server_matches_single_matrix_routines(cuda_lib):
+@pytest.mark.parametrize("n", [130, 300])
+def test_server_matches_single_matrix_routines(cuda_lib, n):
     from paper_2109_13406_gb300.server import SpdServer
 
-    n = 130
     r = SpdServer().serve(make_requests(630, [n]))[0]
     G, B = datagen.spd_request(630, n)
     Gd = dev(G)
