@@ -102,6 +102,20 @@ __device__ __forceinline__ dd add(dd a, dd b) {
     return r;
 }
 
+// Sloppy dd addition (TwoSum on the leading parts, low parts added,
+// FastTwoSum): 11 FP64 operations, absolute error at most ~2u^2 (|a| + |b|)
+// (the relative error can be large under cancellation).  Used where the
+// accuracy target is the absolute bound 4 k 2^-104 (|alpha||A||B| +
+// |beta||C|), e.g. the final alpha/beta combination.
+__device__ __forceinline__ dd add_sloppy(dd a, dd b) {
+    double s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+    dd r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
 __device__ __forceinline__ dd neg(dd a) { return dd{-a.hi, -a.lo}; }
 __device__ __forceinline__ dd sub(dd a, dd b) { return add(a, neg(b)); }
 

@@ -32,13 +32,24 @@ struct PlainSmem {
     double bh[BK][BN + 1], bl[BK][BN + 1];  // op(B) panel, [l][j]
 };
 
-// Tile (bi, bj) of this CTA.  Rgemm: a 2-D grid.  Rsyrk: a 1-D grid over the
-// tiles of one triangle, t -> (row, col) with row <= col (upper) or
-// row >= col (lower).
+constexpr int GROUP_N = 8;  // tile columns per rasterisation group
+
+// Tile (bi, bj) of this CTA.  Rgemm: a 1-D grid walked in groups of GROUP_N
+// tile columns with the tile row fastest inside a group, so the CTAs
+// resident at one time share a few A row panels and B column panels in L2
+// (a plain column-by-column order re-reads all of A for every tile column).
+// Rsyrk: a 1-D grid over the tiles of one triangle, t -> (row, col) with
+// row <= col (upper) or row >= col (lower).
 __device__ __forceinline__ void tile_coords(const GemmArgs &p, int64_t &bi, int64_t &bj) {
     if (p.tri == 0) {
-        bi = blockIdx.x;
-        bj = blockIdx.y;
+        const int64_t tm = (p.m + BM - 1) / BM, tn = (p.n + BN - 1) / BN;
+        const int64_t t = blockIdx.x;
+        const int64_t group = t / (tm * GROUP_N);
+        const int64_t first = group * GROUP_N;
+        const int64_t gn = tn - first < GROUP_N ? tn - first : GROUP_N;
+        const int64_t local = t - group * tm * GROUP_N;
+        bj = first + local % gn;
+        bi = local / gn;
         return;
     }
     int64_t t = blockIdx.x;
@@ -170,9 +181,8 @@ int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream) {
     dim3 grid;
     int64_t tm = ceil_div(p.m, BM), tn = ceil_div(p.n, BN);
     if (p.tri == 0) {
-        if (tn > 65535) return fail(MP_DD_ERR_TOO_LARGE, "n = %lld exceeds the grid limit",
-                                    (long long)p.n);
-        grid = dim3((unsigned)tm, (unsigned)tn);
+        if (tm * tn > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "m x n too large");
+        grid = dim3((unsigned)(tm * tn));
     } else {
         int64_t tiles = tm * (tm + 1) / 2;
         if (tiles > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "n too large");

@@ -189,9 +189,17 @@ __device__ __forceinline__ void slice8(const double *__restrict__ Xh,
             }
             dg[h][0] = (int)(X >> (8 * (S - 1))) + carry;
         }
+        // fp16 of a digit d in [-128, 128] without a conversion instruction:
+        // the fp16 with bits 0x6600 + d is exactly 1536 + d (binade
+        // [1024, 2048), unit spacing), so subtracting 1536 leaves d exactly.
 #pragma unroll
-        for (int t = 0; t < S; ++t)
-            out[t][e / 2] = __halves2half2(__int2half_rn(dg[0][t]), __int2half_rn(dg[1][t]));
+        for (int t = 0; t < S; ++t) {
+            const uint32_t bits = (uint32_t)(0x6600 + dg[0][t]) |
+                                  ((uint32_t)(0x6600 + dg[1][t]) << 16);
+            __half2 x;
+            memcpy(&x, &bits, 4);
+            out[t][e / 2] = __hsub2(x, __floats2half2_rn(1536.0f, 1536.0f));
+        }
     }
 #pragma unroll
     for (int t = 0; t < S; ++t) {
@@ -201,8 +209,10 @@ __device__ __forceinline__ void slice8(const double *__restrict__ Xh,
     }
 }
 
-// One thread per (row, 16 consecutive k): thread rows are consecutive, so the
-// row_contig reads coalesce; each digit store is 32 contiguous bytes.
+// Two threads per (row, 16 consecutive k): the lane pair (2i, 2i+1) takes row
+// i of the block and k halves l0 .. l0+7 and l0+8 .. l0+15, so every 32-byte
+// sector of a digit plane is written whole by one store instruction, and the
+// row_contig reads of 16 consecutive rows per k column coalesce.
 template <int S>
 __global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ Xh,
                                                     const double *__restrict__ Xl, int64_t ld,
@@ -210,13 +220,11 @@ __global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ X
                                                     int64_t rows_pad, int64_t k_pad,
                                                     const unsigned long long *__restrict__ rmax,
                                                     __half *__restrict__ D) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 2) + threadIdx.x / 2;
     if (r >= rows_pad) return;
-    int64_t l0 = (int64_t)blockIdx.y * 16;
-    int e = r < rows ? scale_exponent(rmax[r]) : 0;
-    int shift = 8 * S - e;
-    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0, k, shift, D, rows_pad, k_pad);
-    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0 + 8, k, shift, D, rows_pad, k_pad);
+    const int64_t l0 = (int64_t)blockIdx.y * 16 + 8 * (threadIdx.x & 1);
+    const int e = r < rows ? scale_exponent(rmax[r]) : 0;
+    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0, k, 8 * S - e, D, rows_pad, k_pad);
 }
 
 // ------------------------------------------------------------------ step 3
@@ -531,7 +539,8 @@ __global__ void __launch_bounds__(256) recombine_kernel(const RecArgs p) {
         dd v{vh, vl};
         if (!p.alpha_one) v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
         const int64_t off = i + j * p.ldc;
-        if (!p.beta_zero) v = add(v, mul(dd{p.beta.hi, p.beta.lo}, dd{p.ch[off], p.cl[off]}));
+        if (!p.beta_zero)
+            v = add_sloppy(v, mul(dd{p.beta.hi, p.beta.lo}, dd{p.ch[off], p.cl[off]}));
         p.ch[off] = v.hi;
         p.cl[off] = v.lo;
     }
@@ -588,7 +597,7 @@ template <int S>
 void launch_slice_s(const double *Xh, const double *Xl, int64_t ld, int row_contig,
                     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
                     const unsigned long long *rmax, __half *D, cudaStream_t st) {
-    dim3 grid((unsigned)ceil_div(rows_pad, 128), (unsigned)(k_pad / 16));
+    dim3 grid((unsigned)ceil_div(rows_pad, 64), (unsigned)(k_pad / 16));
     slice_kernel<S><<<grid, 128, 0, st>>>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad,
                                           rmax, D);
 }
