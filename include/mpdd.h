@@ -316,6 +316,36 @@ int mp_dd_Rgemm_sliced_noalloc(const char *transa, const char *transb, int64_t m
                                int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
                                int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices);
 
+/* Residue (CRT) form of the split-precision Rgemm (no counterpart in the
+ * manual).  Same arguments 1-13, result contract and errors as
+ * mp_dd_Rgemm_sliced at 14 slices, and the same rounding of the operands
+ * (every entry of a row of op(A) / column of op(B) rounded to a multiple of
+ * 2^(e-112) of its power-of-two scale, |error| <= one unit), but the exact
+ * integer product of the rounded operands is formed through the Chinese
+ * remainder theorem: residues modulo N pairwise coprime moduli <= 256 (N
+ * about 32 for k = 8192; the product of the moduli exceeds 2 k 2^222), one
+ * fp16 tensor-core GEMM per modulus with exact int32 accumulation, and an
+ * exact multiword reconstruction rounded once to dd.  About N products
+ * instead of S(S+1)/2 = 105, and no truncation of digit pairs: the only
+ * error is the operand rounding, at most 2^(e_i + f_j - 112) per product.
+ * Limits: k <= 131071.  workspace: device memory of at least
+ * mp_dd_Rgemm_crt_workspace(m, n, k) bytes, status word first (read it with
+ * mp_dd_workspace_status).  Asynchronous.  Errors: as mp_dd_Rgemm, -14
+ * workspace NULL, 2003 workspace too small, 2002 k too large. */
+size_t mp_dd_Rgemm_crt_workspace(int64_t m, int64_t n, int64_t k);
+int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                    mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
+                    mp_dd beta, mp_dd_mat C, int64_t ldc, void *workspace,
+                    size_t workspace_bytes);
+
+/* Workspace layout of mp_dd_Rgemm_crt (for inspection and testing):
+ * offsets[0..4] byte offsets of the row maxima (uint64), column maxima,
+ * residue planes of op(A) (fp16 [N][m_pad][k_pad]), of op(B)^T (fp16
+ * [N][n_pad][k_pad]) and the products reduced mod p_i (uint8
+ * [N][n_pad][m_pad]); offsets[5..7] m_pad, n_pad, k_pad; offsets[8..8+N)
+ * the moduli; *moduli = N.  Returns 0. */
+int mp_dd_crt_layout(int64_t m, int64_t n, int64_t k, size_t offsets[48], int *moduli);
+
 /* Byte offsets of the intermediate arrays inside a sliced-Rgemm workspace
  * (for inspection and testing): offsets[0] row maxima of op(A) (uint64 bit
  * patterns of max |hi|, m_pad entries), [1] column maxima of op(B) (n_pad),

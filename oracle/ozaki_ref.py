@@ -15,11 +15,17 @@ arithmetic (Python ints and ``fractions``), one function per step:
    integer matrix products (numpy int64; the values stay far below 2^63).
 4. ``recombine_exact``: sum_b P_b 2^(e_i+f_j-8(b+2)) as exact rationals.
 
+5. the residue (CRT) form: ``crt_moduli``, ``residue_planes`` (symmetric
+   residues of the same integers X), ``crt_products`` (R^A_i R^B_i^T mod p_i)
+   and ``crt_reconstruct`` (the textbook CRT sum mapped to (-P/2, P/2]).
+
 Parity status: pinned by ``tests/test_ozaki_oracle.py`` -- digit expansions
 reproduce X exactly and stay in range, X approximates x within one unit of
 2^(e-8S), the recombined value approximates the exact product within the
 documented truncation bound, and it equals the exact product when every
-digit beyond the first band is zero (integer and power-of-two inputs).
+digit beyond the first band is zero (integer and power-of-two inputs); the
+CRT reconstruction equals the integer product of the rounded operands, and
+the moduli are pairwise coprime.
 """
 from __future__ import annotations
 
@@ -108,3 +114,70 @@ def op_cols(X, trans: bool, k: int, cols: int):
     if trans:
         return np.ascontiguousarray(h[:cols, :k]), np.ascontiguousarray(l[:cols, :k])
     return np.ascontiguousarray(h[:k, :cols].T), np.ascontiguousarray(l[:k, :cols].T)
+
+
+# ----------------------------------------------------------------------------
+# Residue (CRT) form: the same rounded integers multiplied through the
+# Chinese remainder theorem
+# ----------------------------------------------------------------------------
+
+def _is_prime(p: int) -> bool:
+    return p > 1 and all(p % d for d in range(2, int(p ** 0.5) + 1))
+
+
+def crt_moduli(count: int = 40) -> list[int]:
+    """Pairwise coprime moduli <= 256, largest first: 2^8, 3*5*17, 11*23,
+    13*19, then the primes below 256, in decreasing order, that divide none
+    of those four."""
+    composites = [256, 255, 253, 247]
+    primes = [p for p in range(2, 256) if _is_prime(p) and all(c % p for c in composites)]
+    return sorted(composites + primes, reverse=True)[:count]
+
+
+def scaled_integers(hi_row, lo_row, S: int = 14):
+    """The exact integers X = RNE(hi 2^(8S-e)) + RNE(lo 2^(8S-e)) of one row
+    (Python ints) and its exponent e."""
+    e = scale_exponent(hi_row)
+    return [rne_scaled(float(h), 8 * S - e) + rne_scaled(float(l), 8 * S - e)
+            for h, l in zip(hi_row, lo_row)], e
+
+
+def sym_residue(x: int, p: int) -> int:
+    """x mod p in [-floor(p/2), ceil(p/2) - 1]."""
+    r = x % p
+    return r - p if r > (p - 1) // 2 else r
+
+
+def residue_planes(rows_hi, rows_lo, moduli, S: int = 14):
+    """[N][rows][k] symmetric residues of the scaled integers, and exponents."""
+    R, K = rows_hi.shape
+    out = np.zeros((len(moduli), R, K), dtype=np.int64)
+    ex = np.zeros(R, dtype=np.int64)
+    for r in range(R):
+        X, ex[r] = scaled_integers(rows_hi[r], rows_lo[r], S)
+        for i, p in enumerate(moduli):
+            out[i, r, :] = [sym_residue(x, p) for x in X]
+    return out, ex
+
+
+def crt_products(RA, RB, moduli):
+    """(R^A_i R^B_i^T) mod p_i in [0, p_i) (exact int64 products)."""
+    return np.stack([np.mod(RA[i] @ RB[i].T, p) for i, p in enumerate(moduli)])
+
+
+def crt_reconstruct(res, moduli):
+    """The unique x in (-P/2, P/2] with x = res_i mod p_i (P = prod p_i), by
+    the textbook CRT sum (Python ints), for every entry of res[i]."""
+    P = 1
+    for p in moduli:
+        P *= p
+    weights = []
+    for p in moduli:
+        M = P // p
+        weights.append(M * pow(M % p, -1, p))
+    shape = res.shape[1:]
+    out = np.empty(shape, dtype=object)
+    for idx in np.ndindex(*shape):
+        s = sum(int(res[(i,) + idx]) * w for i, w in enumerate(weights)) % P
+        out[idx] = s - P if 2 * s > P else s
+    return out

@@ -25,7 +25,8 @@ from ._abi import MpDD, MpDDCMat, MpDDMat
 __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
-    "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout", "mp_dd_workspace_status", "Rgemm",
+    "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
+    "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status", "Rgemm",
     "Rsyrk", "Rgemm_sliced", "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
 
@@ -155,6 +156,30 @@ def mp_dd_Rgemm_sliced_noalloc(transa, transb, m, n, k, alpha, A, lda, B, ldb, b
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20   # MP_DD_NOALLOC_SCRATCH_BYTES in include/mpdd.h
+
+
+def mp_dd_Rgemm_crt_workspace(m, n, k) -> int:
+    return int(_LIB.mp_dd_Rgemm_crt_workspace(m, n, k))
+
+
+def mp_dd_Rgemm_crt(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, workspace,
+                    workspace_bytes, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgemm_crt(_flag(transa), _flag(transb), m, n, k, _dd(alpha), _cm(A), lda,
+                              _cm(B), ldb, _dd(beta), _m(C), ldc, _ptr(workspace),
+                              workspace_bytes)
+    return _check(rc, "mp_dd_Rgemm_crt") if check else rc
+
+
+def mp_dd_crt_layout(m, n, k) -> dict:
+    off = (ctypes.c_size_t * 48)()
+    cnt = ctypes.c_int()
+    _check(_LIB.mp_dd_crt_layout(m, n, k, off, ctypes.byref(cnt)), "mp_dd_crt_layout")
+    keys = ["rowmax", "colmax", "residues_a", "residues_b", "products", "m_pad", "n_pad",
+            "k_pad"]
+    d = dict(zip(keys, [int(x) for x in off[:8]]))
+    d["moduli"] = [int(x) for x in off[8:8 + cnt.value]]
+    return d
 
 
 def mp_dd_sliced_layout(m, n, k, slices=0) -> dict:

@@ -84,6 +84,11 @@ SIGNATURES = {
     "mp_dd_Rgemm_sliced_noalloc": (_int, [_c, _c, _i64, _i64, _i64, MpDD, MpDDCMat, _i64,
                                           MpDDCMat, _i64, MpDD, MpDDMat, _i64, _int]),
     "mp_dd_sliced_layout": (_int, [_i64, _i64, _i64, _int, ctypes.POINTER(ctypes.c_size_t)]),
+    "mp_dd_Rgemm_crt_workspace": (_sz, [_i64, _i64, _i64]),
+    "mp_dd_Rgemm_crt": (_int, [_c, _c, _i64, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64,
+                               MpDD, MpDDMat, _i64, _vp, _sz]),
+    "mp_dd_crt_layout": (_int, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_int)]),
     "mp_dd_workspace_status": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mp_dd_sliced_timing": (_int, [_int]),
     "mp_dd_Rpotrf": (_int, [_c, _i64, MpDDMat, _i64, _vp]),

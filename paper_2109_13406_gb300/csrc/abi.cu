@@ -314,6 +314,32 @@ int mp_dd_Rgemm_sliced_noalloc(const char *transa, const char *transb, int64_t m
     return run_sliced_noalloc(p, slices, tls().stream);
 }
 
+size_t mp_dd_Rgemm_crt_workspace(int64_t m, int64_t n, int64_t k) {
+    if (m < 0 || n < 0 || k < 0) return 0;
+    return crt_workspace_bytes(m, n, k);
+}
+
+int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                    mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
+                    mp_dd beta, mp_dd_mat C, int64_t ldc, void *workspace,
+                    size_t workspace_bytes) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_gemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if (workspace == nullptr) return fail(-14, "Rgemm_crt: workspace is NULL");
+    if ((rc = require_device())) return rc;
+    return run_crt(p, workspace, workspace_bytes, tls().stream);
+}
+
+int mp_dd_crt_layout(int64_t m, int64_t n, int64_t k, size_t offsets[48], int *moduli) {
+    clear_error();
+    if (offsets == nullptr || moduli == nullptr) return fail(-4, "crt_layout: NULL output");
+    if (m < 0 || n < 0 || k < 0) return fail(-1, "crt_layout: negative size");
+    return crt_layout_query(m, n, k, offsets, moduli);
+}
+
 int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offsets[8]) {
     clear_error();
     if (offsets == nullptr) return fail(-5, "sliced_layout: offsets is NULL");

@@ -1,0 +1,546 @@
+// Residue (CRT) form of the split-precision dd Rgemm on the fp16 tensor cores.
+//
+// The same exact integers as the sliced form -- X = RNE(hi 2^(112 - e)) +
+// RNE(lo 2^(112 - e)) for an entry x = hi + lo of a row of op(A) with scale
+// e (and likewise for the columns of op(B)), |X| <= 2^111 -- are multiplied
+// exactly through the Chinese remainder theorem instead of through digit
+// pairs:
+//
+//  1. residues: r_i = X mod p_i in the symmetric range (|r_i| <= 128) for
+//     N pairwise coprime moduli p_i <= 256, stored as exact fp16 planes;
+//  2. products: C_i = R^A_i (R^B_i)^T on the tensor cores with the exact
+//     fp32-run / int32 accumulation of the band kernel (diagonal mode), each
+//     stored reduced mod p_i (one byte);
+//  3. reconstruction: C' = sum_i c_i w_i mod P with P = prod p_i and the CRT
+//     weights w_i = (P/p_i) ((P/p_i)^-1 mod p_i), in multiword integer
+//     arithmetic, mapped to the symmetric range; since P > 2 k 2^222 >=
+//     2 |A' B'|, C' is exactly the integer product A'B'; it is rounded once
+//     to dd, scaled by 2^(e_i + f_j - 224), and alpha/beta are applied in dd.
+//
+// N is the smallest count with P > k 2^223 (32 moduli for k = 8192), against
+// S(S+1)/2 = 105 pair products of the 14-digit form, for the same rounding
+// of the operands; the only error is the rounding of A and B to 112 bits
+// (at most 2^(e_i + f_j - 112) per product).
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "dd_arith.cuh"
+#include "kernels.cuh"
+#include "ozaki_common.cuh"
+
+namespace mpdd {
+namespace {
+
+constexpr int kDigits = 14;          // X is formed as 14 base-256 digits (112 bits)
+constexpr int kMaxMod = 40;
+constexpr int kWords = 11;           // 32-bit words for sums below 2^352
+// pairwise coprime moduli <= 256, largest first: 2^8, 3*5*17, 11*23, 13*19
+// and primes not dividing those
+__host__ __device__ constexpr int modulus(int i) {
+    constexpr int m[kMaxMod] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227,
+                                223, 211, 199, 197, 193, 191, 181, 179, 173, 167,
+                                163, 157, 151, 149, 139, 137, 131, 127, 113, 109,
+                                107, 103, 101, 97,  89,  83,  79,  73,  71,  67};
+    return m[i];
+}
+
+// 256^(kDigits-1-t) mod (p_{2j} p_{2j+1}) for the moduli pairs (products < 2^16).
+struct PairWeights {
+    int w[kMaxMod / 2][kDigits];
+};
+
+constexpr PairWeights make_pair_weights() {
+    PairWeights pw{};
+    for (int j = 0; j < kMaxMod / 2; ++j) {
+        const long long m = (long long)modulus(2 * j) * modulus(2 * j + 1);
+        long long v = 1;
+        for (int t = kDigits - 1; t >= 0; --t) {
+            pw.w[j][t] = (int)v;
+            v = (v * 256) % m;
+        }
+    }
+    return pw;
+}
+
+__constant__ PairWeights c_pair_weights = make_pair_weights();
+
+__device__ __forceinline__ int sym_mod(int v, int p) {
+    int r = v % p;
+    if (r < 0) r += p;
+    return r > (p - 1) / 2 ? r - p : r;   // [-floor(p/2), ceil(p/2) - 1]
+}
+
+__device__ __forceinline__ uint16_t half_bits(int r) {   // fp16 of r in [-512, 511]
+    __half x = __hsub(__ushort_as_half((unsigned short)(0x6600 + r)), __float2half(1536.0f));
+    return __half_as_ushort(x);
+}
+
+// 4 threads per (row, 16 consecutive k), 4 entries each; residues of the
+// NP moduli pairs, one 8-byte store per plane and thread (a quad of lanes
+// writes one 32-byte sector).
+template <int NP>
+__global__ void __launch_bounds__(128) residue_kernel(
+    const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
+    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+    const unsigned long long *__restrict__ rmax, __half *__restrict__ R) {
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 4) + threadIdx.x / 4;
+    if (r >= rows_pad) return;
+    const int64_t l0 = (int64_t)blockIdx.y * 16 + 4 * (threadIdx.x & 3);
+    const int e = r < rows ? scale_exponent(rmax[r]) : 0;
+    const int shift = 8 * kDigits - e;
+    int dg[4][kDigits];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t l = l0 + q;
+        double hi = 0.0, lo = 0.0;
+        if (r < rows && l < k) {
+            const int64_t off = row_contig ? (r + l * ld) : (l + r * ld);
+            hi = Xh[off];
+            lo = Xl[off];
+        }
+        dd_digits<kDigits>(hi, lo, shift, dg[q]);
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        const int p0 = modulus(2 * j), p1 = modulus(2 * j + 1);
+        uint32_t w0[2], w1[2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int s = 0;
+#pragma unroll
+            for (int t = 0; t < kDigits; ++t) s += dg[q][t] * c_pair_weights.w[j][t];
+            const int rr = s % (p0 * p1);   // keeps the residues of both moduli
+            const uint32_t h0 = half_bits(sym_mod(rr, p0)), h1 = half_bits(sym_mod(rr, p1));
+            if (q & 1) {
+                w0[q / 2] |= h0 << 16;
+                w1[q / 2] |= h1 << 16;
+            } else {
+                w0[q / 2] = h0;
+                w1[q / 2] = h1;
+            }
+        }
+        uint2 v0 = make_uint2(w0[0], w0[1]), v1 = make_uint2(w1[0], w1[1]);
+        *reinterpret_cast<uint2 *>(R + ((int64_t)(2 * j) * rows_pad + r) * k_pad + l0) = v0;
+        *reinterpret_cast<uint2 *>(R + ((int64_t)(2 * j + 1) * rows_pad + r) * k_pad + l0) = v1;
+    }
+}
+
+// ------------------------------------------------------------------ CRT
+
+struct CrtArgs {
+    int N;
+    int64_t m, n, m_pad, n_pad;
+    const uint8_t *res;                   // [N][n_pad][m_pad] products mod p_i
+    const unsigned long long *rmax, *cmax;
+    mp_dd alpha, beta;
+    int alpha_one, beta_zero;
+    double *ch, *cl;
+    int64_t ldc;
+    int moduli[kMaxMod];
+    uint32_t P[kWords];                   // product of the moduli
+    uint32_t Phalf[kWords];               // floor(P / 2)
+    uint32_t w[kMaxMod][kWords];          // CRT weights
+    int ptop;                             // index of P's most significant word
+    float p_f;                            // P / 2^(32 ptop) (for quotient estimates)
+};
+
+// Word idx of a little-endian multiword value, without dynamic indexing
+// (which would move the array to local memory).
+__device__ __forceinline__ uint32_t word_at(const uint32_t (&v)[kWords], int idx) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int t = 0; t < kWords; ++t) r = (t == idx) ? v[t] : r;
+    return r;
+}
+
+// x 2^e for a binary64 x that is zero or normal, by exponent arithmetic when
+// the result stays normal (one DMUL otherwise).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    if (x == 0.0) return 0.0;
+    const long long bits = __double_as_longlong(x);
+    const int E = (int)((bits >> 52) & 0x7FF);
+    if (E + e >= 1 && E + e <= 2046) return __longlong_as_double(bits + ((long long)e << 52));
+    double r = x;
+    while (e > 1000) { r = __dmul_rn(r, 0x1p1000); e -= 1000; }
+    while (e < -1000) { r = __dmul_rn(r, 0x1p-1000); e += 1000; }
+    return __dmul_rn(r, __longlong_as_double((long long)(e + 1023) << 52));
+}
+
+// Round the magnitude v (little-endian 32-bit words) to the nearest binary64
+// (ties to even) times 2^scale.  rem receives the exact remainder v - RN(v)
+// as a magnitude, rem_neg its sign.
+__device__ __forceinline__ double round_words(const uint32_t (&v)[kWords], int scale,
+                                              uint32_t (&rem)[kWords], bool &rem_neg) {
+    int top = -1;
+#pragma unroll
+    for (int t = kWords - 1; t >= 0; --t)
+        if (top < 0 && v[t] != 0) top = t;
+    rem_neg = false;
+#pragma unroll
+    for (int t = 0; t < kWords; ++t) rem[t] = 0;
+    if (top < 0) return 0.0;
+    const int msb = 32 * top + (31 - __clz(word_at(v, top)));
+    if (msb <= 52) {
+        const uint64_t x = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
+        return scale_pow2(__ull2double_rn(x), scale);   // exact
+    }
+    const int q = msb - 52, w = q / 32, b = q % 32;
+    const uint64_t v0 = word_at(v, w), v1 = word_at(v, w + 1), v2 = word_at(v, w + 2);
+    uint64_t mant = b ? ((v0 >> b) | (v1 << (32 - b)) | (v2 << (64 - b))) : (v0 | (v1 << 32));
+    mant &= (1ull << 53) - 1;
+    // remainder below bit q, compared with 2^(q-1)
+    const int hw = (q - 1) / 32, hb = (q - 1) % 32;
+    bool gt = false, eq = true;
+#pragma unroll
+    for (int t = kWords - 1; t >= 0; --t) {
+        uint32_t word = v[t];
+        word = (t > w) ? 0u : (t == w ? (b ? (word & ((1u << b) - 1)) : 0u) : word);
+        rem[t] = word;
+        const uint32_t hwd = (t == hw) ? (1u << hb) : 0u;
+        if (eq && word != hwd) {
+            gt = word > hwd;
+            eq = false;
+        }
+    }
+    if (gt || (eq && (mant & 1))) {
+        ++mant;                       // rounded up: remainder becomes 2^q - rem, negative
+        rem_neg = true;
+        uint64_t borrow = 0;
+#pragma unroll
+        for (int t = 0; t < kWords; ++t) {
+            const uint64_t bit = (t == w) ? (1ull << b) : 0ull;
+            const uint64_t d = bit - (uint64_t)rem[t] - borrow;
+            rem[t] = (uint32_t)d;
+            borrow = (d >> 63) & 1;
+        }
+    }
+    return scale_pow2(__ull2double_rn(mant), q + scale);   // mant <= 2^53: exact
+}
+
+__global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
+    const int64_t total = p.m * p.n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx % p.m, j = idx / p.m;
+        // S = sum_b c_b w_b with 64-bit column sums, then carries
+        uint64_t acc[kWords];
+#pragma unroll
+        for (int t = 0; t < kWords; ++t) acc[t] = 0;
+        for (int b = 0; b < p.N; ++b) {
+            const uint32_t c = p.res[((int64_t)b * p.n_pad + j) * p.m_pad + i];
+#pragma unroll
+            for (int t = 0; t < kWords; ++t) acc[t] += (uint64_t)c * p.w[b][t];
+        }
+        uint32_t S[kWords];
+        uint64_t carry = 0;
+#pragma unroll
+        for (int t = 0; t < kWords; ++t) {
+            const uint64_t v = acc[t] + carry;
+            S[t] = (uint32_t)v;
+            carry = v >> 32;
+        }
+        // S mod P: quotient estimate (S < N 256 P < 2^14 P, so an fp32 ratio of
+        // the leading words is within one of the quotient; corrected below)
+        const float s_f = (float)word_at(S, p.ptop + 1) * 4294967296.0f +
+                          (float)word_at(S, p.ptop) + (float)word_at(S, p.ptop - 1) * 2.3283064e-10f;
+        int64_t qest = (int64_t)floorf(s_f / p.p_f);
+        if (qest < 0) qest = 0;
+        // S -= qest * P (two's complement over kWords words)
+        {
+            uint64_t borrow = 0, mc = 0;
+#pragma unroll
+            for (int t = 0; t < kWords; ++t) {
+                const uint64_t prod = (uint64_t)qest * p.P[t] + mc;
+                mc = prod >> 32;
+                const uint64_t d = (uint64_t)S[t] - (uint32_t)prod - borrow;
+                S[t] = (uint32_t)d;
+                borrow = (d >> 63) & 1;
+            }
+        }
+        // correct into [0, P): at most a couple of steps either way
+        for (int it = 0; it < 4; ++it) {
+            const bool neg = (S[kWords - 1] & 0x80000000u) != 0;
+            bool ge = false;
+            if (!neg) {
+                bool eq = true;
+#pragma unroll
+                for (int t = kWords - 1; t >= 0; --t)
+                    if (eq && S[t] != p.P[t]) {
+                        ge = S[t] > p.P[t];
+                        eq = false;
+                    }
+                if (eq) ge = true;
+            }
+            if (!neg && !ge) break;
+            uint64_t c2 = 0;
+#pragma unroll
+            for (int t = 0; t < kWords; ++t) {
+                uint64_t d = neg ? (uint64_t)S[t] + p.P[t] + c2
+                                 : (uint64_t)S[t] - p.P[t] - c2;
+                S[t] = (uint32_t)d;
+                c2 = neg ? (d >> 32) : ((d >> 63) & 1);
+            }
+        }
+        // symmetric range: S > P/2 -> S - P (store the magnitude, remember the sign)
+        bool gt_half = false;
+        {
+            bool eq = true;
+#pragma unroll
+            for (int t = kWords - 1; t >= 0; --t)
+                if (eq && S[t] != p.Phalf[t]) {
+                    gt_half = S[t] > p.Phalf[t];
+                    eq = false;
+                }
+        }
+        bool negative = false;
+        if (gt_half) {            // magnitude P - S
+            uint64_t b2 = 0;
+#pragma unroll
+            for (int t = 0; t < kWords; ++t) {
+                const uint64_t d = (uint64_t)p.P[t] - S[t] - b2;
+                S[t] = (uint32_t)d;
+                b2 = (d >> 63) & 1;
+            }
+            negative = true;
+        }
+        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * 8 * kDigits;
+        uint32_t rem[kWords], rem2[kWords];
+        bool rem_neg, unused;
+        double vh = round_words(S, sc, rem, rem_neg);
+        double vl = round_words(rem, sc, rem2, unused);
+        if (rem_neg) vl = -vl;
+        if (negative) {
+            vh = -vh;
+            vl = -vl;
+        }
+        dd v{vh, vl};
+        if (!p.alpha_one) v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
+        const int64_t off = i + j * p.ldc;
+        if (!p.beta_zero)
+            v = add_sloppy(v, mul(dd{p.beta.hi, p.beta.lo}, dd{p.ch[off], p.cl[off]}));
+        p.ch[off] = v.hi;
+        p.cl[off] = v.lo;
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+// Little-endian multiword helpers (host).
+using Big = std::vector<uint32_t>;
+
+Big big_mul_small(const Big &a, uint32_t s) {
+    Big r(a.size() + 1, 0);
+    uint64_t c = 0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        uint64_t v = (uint64_t)a[i] * s + c;
+        r[i] = (uint32_t)v;
+        c = v >> 32;
+    }
+    r[a.size()] = (uint32_t)c;
+    while (r.size() > 1 && r.back() == 0) r.pop_back();
+    return r;
+}
+
+Big big_div_small(const Big &a, uint32_t s, uint32_t *rem) {
+    Big r(a.size(), 0);
+    uint64_t c = 0;
+    for (size_t i = a.size(); i-- > 0;) {
+        uint64_t v = (c << 32) | a[i];
+        r[i] = (uint32_t)(v / s);
+        c = v % s;
+    }
+    if (rem) *rem = (uint32_t)c;
+    while (r.size() > 1 && r.back() == 0) r.pop_back();
+    return r;
+}
+
+int big_bits(const Big &a) {
+    for (size_t i = a.size(); i-- > 0;)
+        if (a[i]) return (int)(32 * i + 32 - __builtin_clz(a[i]));
+    return 0;
+}
+
+uint32_t inv_mod(uint32_t a, uint32_t p) {   // a^-1 mod p (gcd(a, p) = 1)
+    int64_t t = 0, nt = 1, r = p, nr = a % p;
+    while (nr) {
+        int64_t q = r / nr, tmp = t - q * nt;
+        t = nt;
+        nt = tmp;
+        tmp = r - q * nr;
+        r = nr;
+        nr = tmp;
+    }
+    if (t < 0) t += p;
+    return (uint32_t)t;
+}
+
+// Smallest moduli count with P > k 2^223 (= 2 max |A' B'|, |A'|, |B'| <= 2^111).
+int moduli_count(int64_t k) {
+    const int need = 223 + (int)std::ceil(std::log2((double)(k > 1 ? k : 1))) + 1;
+    Big P{1};
+    for (int N = 1; N <= kMaxMod; ++N) {
+        P = big_mul_small(P, modulus(N - 1));
+        if (big_bits(P) > need) return N % 2 ? N + 1 : N;   // residues come in pairs
+    }
+    return -1;
+}
+
+struct CrtLayout {
+    int N;
+    int64_t m_pad, n_pad, k_pad;
+    size_t off_rowmax, off_colmax, off_ra, off_rb, off_res, total;
+};
+
+size_t align1k(size_t x) { return (x + 1023) / 1024 * 1024; }
+
+CrtLayout crt_layout(int64_t m, int64_t n, int64_t k) {
+    CrtLayout L{};
+    L.N = moduli_count(k);
+    const int TN = band_tn(m, n);
+    L.m_pad = ceil_div(imax(m, 1), kBandTM) * kBandTM;
+    L.n_pad = ceil_div(imax(n, 1), TN) * TN;
+    L.k_pad = ceil_div(imax(k, 1), kBandTK) * kBandTK;
+    const size_t N = L.N > 0 ? (size_t)L.N : 0;
+    size_t o = 1024;
+    L.off_rowmax = o; o = align1k(o + 8 * (size_t)L.m_pad);
+    L.off_colmax = o; o = align1k(o + 8 * (size_t)L.n_pad);
+    L.off_ra = o; o = align1k(o + 2 * N * L.m_pad * L.k_pad);
+    L.off_rb = o; o = align1k(o + 2 * N * L.n_pad * L.k_pad);
+    L.off_res = o; o = align1k(o + N * L.n_pad * L.m_pad);
+    L.total = o;
+    return L;
+}
+
+template <int NP>
+void launch_residues_np(const double *Xh, const double *Xl, int64_t ld, int rc, int64_t rows,
+                        int64_t k, int64_t rows_pad, int64_t k_pad,
+                        const unsigned long long *rmax, __half *R, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(rows_pad, 32), (unsigned)(k_pad / 16));
+    residue_kernel<NP><<<grid, 128, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R);
+}
+
+int launch_residues(int N, const double *Xh, const double *Xl, int64_t ld, int rc,
+                    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+                    const unsigned long long *rmax, __half *R, cudaStream_t st) {
+    if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for residues");
+    switch (N / 2) {
+#define MPDD_RES_CASE(NP) \
+    case NP: launch_residues_np<NP>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R, st); break;
+        MPDD_RES_CASE(14) MPDD_RES_CASE(15) MPDD_RES_CASE(16) MPDD_RES_CASE(17)
+        MPDD_RES_CASE(18) MPDD_RES_CASE(19) MPDD_RES_CASE(20)
+#undef MPDD_RES_CASE
+        default:
+            return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [28, 40]", N);
+    }
+    return check_launch("residue_kernel");
+}
+
+}  // namespace
+
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k) {
+    return crt_layout(m, n, k).total;
+}
+
+int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *off, int *count) {
+    CrtLayout L = crt_layout(m, n, k);
+    off[0] = L.off_rowmax;
+    off[1] = L.off_colmax;
+    off[2] = L.off_ra;
+    off[3] = L.off_rb;
+    off[4] = L.off_res;
+    off[5] = (size_t)L.m_pad;
+    off[6] = (size_t)L.n_pad;
+    off[7] = (size_t)L.k_pad;
+    *count = L.N;
+    for (int i = 0; i < L.N && i < kMaxMod; ++i) off[8 + i] = (size_t)modulus(i);
+    return 0;
+}
+
+int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (p.k > ((int64_t)1 << 17) - 1)
+        return fail(MP_DD_ERR_TOO_LARGE, "k = %lld exceeds 131071 (int32 products)",
+                    (long long)p.k);
+    CrtLayout L = crt_layout(p.m, p.n, p.k);
+    if (L.N < 0 || L.N > kMaxMod) return fail(MP_DD_ERR_TOO_LARGE, "k too large for the moduli");
+    if (ws == nullptr || ws_bytes < L.total)
+        return fail(MP_DD_ERR_WORKSPACE, "CRT Rgemm needs %zu workspace bytes, got %zu",
+                    L.total, ws_bytes);
+    if ((int64_t)L.N * L.m_pad > 0x7fffffffLL || (int64_t)L.N * L.n_pad > 0x7fffffffLL)
+        return fail(MP_DD_ERR_TOO_LARGE, "matrix too large for the CRT path");
+    if (p.alpha_zero) return launch_gemm_plain(p, st);
+    const int TN = band_tn(p.m, p.n);
+
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    cudaError_t e = cudaMemsetAsync(w, 0, L.off_ra, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    auto *rmax = reinterpret_cast<unsigned long long *>(w + L.off_rowmax);
+    auto *cmax = reinterpret_cast<unsigned long long *>(w + L.off_colmax);
+    auto *RA = reinterpret_cast<__half *>(w + L.off_ra);
+    auto *RB = reinterpret_cast<__half *>(w + L.off_rb);
+    auto *RES = reinterpret_cast<uint8_t *>(w + L.off_res);
+    const int a_rc = p.ta ? 0 : 1, b_rc = p.tb ? 1 : 0;
+    int rc;
+    if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
+    if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
+    if ((rc = launch_residues(L.N, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
+                              RA, st)))
+        return rc;
+    if ((rc = launch_residues(L.N, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax,
+                              RB, st)))
+        return rc;
+
+    CUtensorMap tmA, tmB;
+    if ((rc = make_tmap(&tmA, RA, (int64_t)L.N * L.m_pad, L.k_pad, kBandTM))) return rc;
+    if ((rc = make_tmap(&tmB, RB, (int64_t)L.N * L.n_pad, L.k_pad, TN))) return rc;
+    BandArgs ba{};
+    ba.S = L.N;
+    ba.kb_count = (int)(L.k_pad / kBandTK);
+    ba.tiles_m = (int)(L.m_pad / kBandTM);
+    ba.tiles_n = (int)(L.n_pad / TN);
+    ba.m_pad = L.m_pad;
+    ba.n_pad = L.n_pad;
+    ba.P = nullptr;
+    ba.R = RES;
+    ba.status = reinterpret_cast<int *>(w);
+    ba.diag = 1;
+    for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
+    if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
+
+    // CRT constants
+    CrtArgs ca{};
+    ca.N = L.N;
+    ca.m = p.m; ca.n = p.n; ca.m_pad = L.m_pad; ca.n_pad = L.n_pad;
+    ca.res = RES; ca.rmax = rmax; ca.cmax = cmax;
+    ca.alpha = p.alpha; ca.beta = p.beta;
+    ca.alpha_one = p.alpha_one; ca.beta_zero = p.beta_zero;
+    ca.ch = p.ch; ca.cl = p.cl; ca.ldc = p.ldc;
+    Big P{1};
+    for (int i = 0; i < L.N; ++i) {
+        ca.moduli[i] = modulus(i);
+        P = big_mul_small(P, modulus(i));
+    }
+    if ((int)P.size() > kWords - 1) return fail(MP_DD_ERR_TOO_LARGE, "moduli product too wide");
+    for (int t = 0; t < kWords; ++t) ca.P[t] = t < (int)P.size() ? P[t] : 0;
+    Big half = big_div_small(P, 2, nullptr);
+    for (int t = 0; t < kWords; ++t) ca.Phalf[t] = t < (int)half.size() ? half[t] : 0;
+    for (int i = 0; i < L.N; ++i) {
+        uint32_t mi_mod = 0;
+        Big Mi = big_div_small(P, modulus(i), nullptr);
+        big_div_small(Mi, modulus(i), &mi_mod);
+        Big wi = big_mul_small(Mi, inv_mod(mi_mod, modulus(i)));
+        for (int t = 0; t < kWords; ++t) ca.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
+    }
+    ca.ptop = (int)P.size() - 1;
+    ca.p_f = (float)P.back() + (float)P[P.size() - 2] * 2.3283064e-10f;
+    const int64_t total = p.m * p.n;
+    int64_t blocks = ceil_div(total, 256);
+    if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
+    crt_kernel<<<(unsigned)blocks, 256, 0, st>>>(ca);
+    return check_launch("crt_kernel");
+}
+
+}  // namespace mpdd

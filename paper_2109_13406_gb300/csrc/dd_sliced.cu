@@ -38,6 +38,7 @@
 #include "common.cuh"
 #include "dd_arith.cuh"
 #include "kernels.cuh"
+#include "ozaki_common.cuh"
 #include "sm100.cuh"
 
 namespace mpdd {
@@ -64,11 +65,15 @@ struct BandCfg {
     static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024 + 256;
 };
 
+}  // namespace
+
 // Tile width used for an m x n product: the wide tile once there are enough
 // tiles to fill the GPU twice over.
 int band_tn(int64_t m, int64_t n) {
     return (ceil_div(m, TM) * ceil_div(n, 256) >= 304) ? 256 : 128;
 }
+
+namespace {
 
 // ------------------------------------------------------------------ layout
 
@@ -116,48 +121,6 @@ __global__ void absmax_kernel(const double *__restrict__ X, int64_t ld, int row_
     if (mx) atomicMax(out + r, mx);
 }
 
-// e with max |x| < 2^(e-1): from the biased exponent E of the maximum,
-// max in [2^(E-1023), 2^(E-1022)) -> e = E - 1021 (E = 0, subnormal: same).
-__device__ __forceinline__ int scale_exponent(unsigned long long maxbits) {
-    if (maxbits == 0) return 0;
-    return (int)(maxbits >> 52) - 1021;
-}
-
-// ------------------------------------------------------------------ step 2
-
-// RNE(v * 2^s) as a signed 128-bit integer, by integer operations on the
-// binary64 fields (|v 2^s| < 2^127 by construction).
-__device__ __forceinline__ __int128 scaled_round(double v, int s) {
-    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-    int E = (int)((bits >> 52) & 0x7FF);
-    unsigned long long mant = bits & ((1ull << 52) - 1);
-    int ex;
-    if (E == 0) {
-        ex = 1 - 1075;
-    } else {
-        mant |= 1ull << 52;
-        ex = E - 1075;
-    }
-    if (mant == 0) return 0;
-    int sh = ex + s;
-    __int128 r;
-    if (sh >= 0) {
-        r = (__int128)((unsigned __int128)mant << sh);
-    } else {
-        int rs = -sh;
-        if (rs > 54) {
-            r = 0;
-        } else {
-            unsigned long long q = mant >> rs;
-            unsigned long long rem = mant & ((1ull << rs) - 1);
-            unsigned long long half = 1ull << (rs - 1);
-            if (rem > half || (rem == half && (q & 1))) ++q;
-            r = (__int128)q;
-        }
-    }
-    return (bits >> 63) ? -r : r;
-}
-
 // Digits of 8 consecutive entries (l0 .. l0+7) of one row, written as S
 // planes of 8 fp16 values (16 bytes each).
 template <int S>
@@ -178,16 +141,7 @@ __device__ __forceinline__ void slice8(const double *__restrict__ Xh,
                 hi = Xh[off];
                 lo = Xl[off];
             }
-            __int128 X = scaled_round(hi, shift) + scaled_round(lo, shift);
-            unsigned __int128 u = (unsigned __int128)X;
-            int carry = 0;
-#pragma unroll
-            for (int t = S - 1; t >= 1; --t) {
-                int byte = (int)((unsigned)(u >> (8 * (S - 1 - t))) & 0xFFu) + carry;
-                carry = byte >= 128;
-                dg[h][t] = byte - (carry << 8);
-            }
-            dg[h][0] = (int)(X >> (8 * (S - 1))) + carry;
+            dd_digits<S>(hi, lo, shift, dg[h]);
         }
         // fp16 of a digit d in [-128, 128] without a conversion instruction:
         // the fp16 with bits 0x6600 + d is exactly 1536 + d (binade
@@ -229,12 +183,7 @@ __global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ X
 
 // ------------------------------------------------------------------ step 3
 
-struct BandArgs {
-    int S, kb_count, tiles_m, tiles_n;
-    int64_t m_pad, n_pad;
-    int32_t *P;   // [S][n_pad][m_pad]
-    int *status;
-};
+
 
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int &tm,
                                             int &tn) {
@@ -304,9 +253,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                 int tm, tn;
                 tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
                 for (int b = 0; b < S && ok; ++b)
-                    for (int t = 0; t <= b && ok; ++t) {
+                    for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
-                        const int yb = (int)((b - t) * p.n_pad) + tn * TN;
+                        const int yb = (int)((p.diag ? b : b - t) * p.n_pad) + tn * TN;
                         for (int kb = 0; kb < KB; ++kb, ++it) {
                             const int s = it % STAGES;
                             const uint32_t f = it / STAGES;
@@ -340,9 +289,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             bool ok = true;
             for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
                 for (int b = 0; b < S && ok; ++b) {
-                    const int steps = (b + 1) * KB;
+                    const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
-                    for (int t = 0; t <= b && ok; ++t)
+                    for (int t = p.diag ? b : 0; t <= b && ok; ++t)
                         for (int kb = 0; kb < KB; ++kb, ++it, ++sidx) {
                             const int s = it % STAGES;
                             const uint32_t f = it / STAGES;
@@ -399,7 +348,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                 int32_t acc[kEpiCols];
 #pragma unroll
                 for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
-                const int steps = (b + 1) * KB;
+                const int steps = (p.diag ? 1 : b + 1) * KB;
                 const int nchunks = (steps + CHUNK_KB - 1) / CHUNK_KB;
                 for (int c = 0; c < nchunks; ++c, ++chunk) {
                     const uint32_t buf = chunk & 1, use = chunk >> 1;
@@ -421,10 +370,21 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                     mbar_arrive(&acce[buf]);
                 }
                 if (!ok) break;
-                int32_t *dst = p.P + ((int64_t)b * p.n_pad + (int64_t)tn * TN + col0) * p.m_pad +
-                               (int64_t)tm * TM + row;
+                const int64_t off = ((int64_t)b * p.n_pad + (int64_t)tn * TN + col0) * p.m_pad +
+                                    (int64_t)tm * TM + row;
+                if (p.diag) {
+                    const int pm = p.moduli[b];
+                    uint8_t *dst = p.R + off;
 #pragma unroll
-                for (int j = 0; j < kEpiCols; ++j) dst[(int64_t)j * p.m_pad] = acc[j];
+                    for (int j = 0; j < kEpiCols; ++j) {
+                        int r = acc[j] % pm;
+                        dst[(int64_t)j * p.m_pad] = (uint8_t)(r < 0 ? r + pm : r);
+                    }
+                } else {
+                    int32_t *dst = p.P + off;
+#pragma unroll
+                    for (int j = 0; j < kEpiCols; ++j) dst[(int64_t)j * p.m_pad] = acc[j];
+                }
             }
         }
     }
@@ -567,6 +527,8 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+}  // namespace
+
 // Tensor map of a [rows][k_pad] fp16 digit array, box 64 (k) x box_rows.
 int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows) {
     EncodeTiledFn fn = encode_fn();
@@ -592,6 +554,8 @@ int launch_absmax(const double *X, int64_t ld, int row_contig, int64_t rows, int
     absmax_kernel<<<grid, 128, 0, st>>>(X, ld, row_contig, rows, k, lchunk, out);
     return check_launch("absmax_kernel");
 }
+
+namespace {
 
 template <int S>
 void launch_slice_s(const double *Xh, const double *Xl, int64_t ld, int row_contig,
@@ -729,23 +693,10 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     ba.m_pad = L.m_pad;
     ba.n_pad = L.n_pad;
     ba.P = P;
+    ba.R = nullptr;
+    ba.diag = 0;
     ba.status = status;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [] {
-        cudaFuncSetAttribute(band_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BandCfg<128>::SMEM);
-        cudaFuncSetAttribute(band_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BandCfg<256>::SMEM);
-    });
-    const int tiles = ba.tiles_m * ba.tiles_n;
-    const int grid = tiles < sm_count() ? tiles : sm_count();
-    if (TN == 256)
-        band_gemm_kernel<256><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(tmA, tmB,
-                                                                                      ba);
-    else
-        band_gemm_kernel<128><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(tmA, tmB,
-                                                                                      ba);
-    if ((rc = check_launch("band_gemm_kernel"))) return rc;
+    if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
     timer().mark(2, st);
 
     RecArgs ra{};
@@ -762,6 +713,26 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     rc = check_launch("recombine_kernel");
     timer().mark(3, st);
     return rc;
+}
+
+int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
+                cudaStream_t st) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        cudaFuncSetAttribute(band_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BandCfg<128>::SMEM);
+        cudaFuncSetAttribute(band_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BandCfg<256>::SMEM);
+    });
+    const int tiles = ba.tiles_m * ba.tiles_n;
+    const int grid = tiles < sm_count() ? tiles : sm_count();
+    if (TN == 256)
+        band_gemm_kernel<256><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(tmA, tmB,
+                                                                                      ba);
+    else
+        band_gemm_kernel<128><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(tmA, tmB,
+                                                                                      ba);
+    return check_launch("band_gemm_kernel");
 }
 
 int read_status(const void *ws, int *status) {

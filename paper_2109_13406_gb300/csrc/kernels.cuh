@@ -59,6 +59,11 @@ int launch_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *ds, cuda
 int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
                       cudaStream_t st);
 
+// Residue (CRT) form of the split-precision Rgemm.
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k);
+int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *offsets, int *count);
+int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t stream);
+
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();
 int run_sliced_noalloc(const GemmArgs &p, int slices, cudaStream_t stream);

@@ -1,0 +1,113 @@
+"""Parity of the residue (CRT) form of the split-precision Rgemm (GPU).
+
+Residue planes and the products reduced mod each modulus are integer work:
+bit-exact against the oracle (oracle/ozaki_ref.py).  The result is checked
+against the oracle's exact tier within the accuracy bound.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import datagen
+from oracle import ozaki_ref as oz
+from gpucase import check_against_exact, dev, host, sample_blocks
+
+pytestmark = pytest.mark.gpu
+
+
+def run_crt(mp, c):
+    A, B, C = dev(c.A), dev(c.B), dev(c.C)
+    ws = mp.workspace(mp.mp_dd_Rgemm_crt_workspace(c.m, c.n, c.k))
+    mp.mp_dd_Rgemm_crt(c.transa, c.transb, c.m, c.n, c.k, c.alpha, A, c.A[0].shape[0], B,
+                       c.B[0].shape[0], c.beta, C, c.C[0].shape[0], ws, ws.numel())
+    torch.cuda.synchronize()
+    assert mp.mp_dd_workspace_status(ws) == 0
+    return host(C, c.m, c.n), ws
+
+
+def view(ws, off, count, dtype):
+    return ws[off: off + count * np.dtype(dtype).itemsize].cpu().numpy().view(dtype)
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_crt_intermediates_bit_exact(cuda_lib, ta, tb):
+    m, n, k = 70, 50, 150
+    c = datagen.gemm_case(700 + "NT".index(ta) * 2 + "NT".index(tb), ta, tb, m, n, k, pad=1)
+    got, ws = run_crt(cuda_lib, c)
+    L = cuda_lib.mp_dd_crt_layout(m, n, k)
+    mods = L["moduli"]
+    assert mods == oz.crt_moduli(len(mods))
+    P = 1
+    for p in mods:
+        P *= p
+    assert P > k * 2 ** 223            # the reconstruction is exact
+    mp_, np_, kp = L["m_pad"], L["n_pad"], L["k_pad"]
+    RA, _ = oz.residue_planes(*oz.op_rows(c.A, ta == "T", m, k), mods)
+    RB, _ = oz.residue_planes(*oz.op_cols(c.B, tb == "T", k, n), mods)
+    N = len(mods)
+    ra = view(ws, L["residues_a"], N * mp_ * kp, np.float16).reshape(N, mp_, kp)
+    rb = view(ws, L["residues_b"], N * np_ * kp, np.float16).reshape(N, np_, kp)
+    assert np.array_equal(ra[:, :m, :k].astype(np.int64), RA)
+    assert np.array_equal(rb[:, :n, :k].astype(np.int64), RB)
+    assert not ra[:, m:, :].any() and not ra[:, :, k:].any()
+    prods = view(ws, L["products"], N * np_ * mp_, np.uint8).reshape(N, np_, mp_)
+    want = oz.crt_products(RA, RB, mods)
+    assert np.array_equal(prods[:, :n, :m].transpose(0, 2, 1).astype(np.int64), want)
+    assert check_against_exact(c, got) <= 1.0
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 5, 7), (129, 130, 65), (200, 64, 300)])
+def test_crt_ragged_shapes(cuda_lib, shape):
+    m, n, k = shape
+    c = datagen.gemm_case(710 + sum(shape), "N", "T", m, n, k, pad=1)
+    got, _ = run_crt(cuda_lib, c)
+    assert check_against_exact(c, got) <= 1.0
+
+
+def test_crt_beta_zero_and_limits(cuda_lib):
+    c = datagen.gemm_case(720, "N", "N", 90, 60, 70)
+    c.beta = (0.0, 0.0)
+    clean = datagen.gemm_case(720, "N", "N", 90, 60, 70)
+    clean.beta = (0.0, 0.0)
+    c.C = (np.full_like(c.C[0], np.nan), np.full_like(c.C[1], np.nan))
+    got, ws = run_crt(cuda_lib, c)
+    assert np.isfinite(got[0]).all() and check_against_exact(clean, got) <= 1.0
+    z = dev(c.C)
+    assert cuda_lib.mp_dd_Rgemm_crt("N", "N", 90, 60, 70, (1.0, 0.0), z, 90, z, 70, (0.0, 0.0),
+                                    z, 90, ws, 100, check=False) == 2003
+
+
+def test_crt_wide_tiles_and_ill_scaled(cuda_lib):
+    """4096 x 4096 (k = 256) uses the 128 x 256 tile kernel; sampled product
+    residues bit-exact, sampled results within the bound, with ill-scaled
+    (outer) inputs."""
+    m = n = 4096
+    k = 256
+    c = datagen.gemm_case(730, "N", "N", m, n, k, ill="outer")
+    got, ws = run_crt(cuda_lib, c)
+    L = cuda_lib.mp_dd_crt_layout(m, n, k)
+    mods = L["moduli"]
+    g = datagen.rng(731)
+    rows = np.concatenate([[0, m - 1], g.integers(0, m, 10)])
+    cols = np.concatenate([[0, 255, 256, n - 1], g.integers(0, n, 8)])
+    Ah, Al = oz.op_rows(c.A, False, m, k)
+    Bh, Bl = oz.op_cols(c.B, False, k, n)
+    RA, _ = oz.residue_planes(Ah[rows], Al[rows], mods)
+    RB, _ = oz.residue_planes(Bh[cols], Bl[cols], mods)
+    N, mp_, np_ = len(mods), L["m_pad"], L["n_pad"]
+    prods = view(ws, L["products"], N * np_ * mp_, np.uint8).reshape(N, np_, mp_)
+    sel = prods[:, cols][:, :, rows].transpose(0, 2, 1).astype(np.int64)
+    assert np.array_equal(sel, oz.crt_products(RA, RB, mods))
+    rr, cc = sample_blocks(m, n, bs=16, count=8)
+    assert check_against_exact(c, got, rr, cc) <= 1.0
+
+
+@pytest.mark.parametrize("ill", [None, "outer"])
+def test_crt_config2_2048(cuda_lib, ill):
+    n = 2048
+    c = datagen.gemm_case(2, "N", "N", n, n, n, ill=ill)
+    got, _ = run_crt(cuda_lib, c)
+    rr, cc = sample_blocks(n, n, bs=16, count=8)
+    assert check_against_exact(c, got, rr, cc) <= 1.0

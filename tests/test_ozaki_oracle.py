@@ -82,3 +82,53 @@ def test_truncation_error_within_documented_bound(ill):
     assert errs[14] < 0.25
     assert errs[10] > 1.0
     assert 30 < errs[10] / max(errs[11], 1e-300) < 2000
+
+
+# ---------------------------------------------------------------------------
+# residue (CRT) form
+# ---------------------------------------------------------------------------
+
+def test_crt_moduli_pairwise_coprime():
+    import math
+
+    mods = oz.crt_moduli()
+    assert len(mods) == 40 and mods == sorted(mods, reverse=True) and max(mods) == 256
+    for i in range(len(mods)):
+        for j in range(i):
+            assert math.gcd(mods[i], mods[j]) == 1
+    assert [oz.sym_residue(x, 256) for x in (127, 128, -128, 255)] == [127, -128, -128, -1]
+    assert [oz.sym_residue(x, 255) for x in (127, 128, -127)] == [127, -127, -127]
+
+
+def test_crt_reconstruction_equals_integer_product():
+    g = datagen.rng(7)
+    mods = oz.crt_moduli(32)
+    P = 1
+    for p in mods:
+        P *= p
+    k = 9
+    A = [[int(g.integers(-2 ** 62, 2 ** 62)) * 2 ** 49 + int(g.integers(0, 2 ** 49))
+          for _ in range(k)] for _ in range(3)]
+    B = [[int(g.integers(-2 ** 62, 2 ** 62)) * 2 ** 49 + int(g.integers(0, 2 ** 49))
+          for _ in range(k)] for _ in range(4)]
+    exact = [[sum(a * b for a, b in zip(ra, rb)) for rb in B] for ra in A]
+    assert P > 2 * max(abs(v) for r in exact for v in r)
+    RA = np.array([[[oz.sym_residue(x, p) for x in r] for r in A] for p in mods])
+    RB = np.array([[[oz.sym_residue(x, p) for x in r] for r in B] for p in mods])
+    assert np.abs(RA).max() <= 128 and np.abs(RB).max() <= 128
+    rec = oz.crt_reconstruct(oz.crt_products(RA, RB, mods), mods)
+    assert [[int(v) for v in r] for r in rec] == exact
+
+
+def test_crt_form_error_is_the_operand_rounding_only():
+    m, n, k = 3, 3, 40
+    c = datagen.gemm_case(8, "N", "N", m, n, k, alpha=(1.0, 0.0), beta=(0.0, 0.0))
+    mods = oz.crt_moduli(32)
+    RA, ea = oz.residue_planes(*oz.op_rows(c.A, False, m, k), mods)
+    RB, fb = oz.residue_planes(*oz.op_cols(c.B, False, k, n), mods)
+    rec = oz.crt_reconstruct(oz.crt_products(RA, RB, mods), mods)
+    exact = fr.gemm_exact("N", "N", m, n, k, (1.0, 0.0), c.A, c.B, (0.0, 0.0), c.C)
+    for i in range(m):
+        for j in range(n):
+            v = Fraction(int(rec[i, j])) * Fraction(2) ** (int(ea[i]) + int(fb[j]) - 224)
+            assert abs(v - exact[i][j]) <= k * Fraction(2) ** (int(ea[i]) + int(fb[j]) - 112)
