@@ -131,6 +131,55 @@ def _scale_rows_padded(M, exps):
     return M[0] * f[:, None], M[1] * f[:, None]
 
 
+@dataclass
+class TrsmCase:
+    side: str
+    uplo: str
+    transa: str
+    diag: str
+    m: int
+    n: int
+    alpha: tuple
+    A: tuple
+    B: tuple
+
+
+def triangular_dd(g: np.random.Generator, order: int, uplo: str, diag: str,
+                  ld: int | None = None):
+    """An order x order triangular dd matrix in column-major planes: the uplo
+    triangle U(-1, 1) off the diagonal, diagonal entries of magnitude
+    order * U(1, 2) with random sign (strictly diagonally dominant, so the
+    solve is well conditioned at every order).  The other triangle, padding
+    rows and -- for diag = 'U' -- the diagonal are NaN: only entries a solve
+    may read are finite."""
+    ld = max(1, order if ld is None else ld)
+    H, L = dd_matrix(g, order, order, ld)
+    d = order * g.uniform(1.0, 2.0, order) * g.choice([-1.0, 1.0], order)
+    dh, dl = dd_lo_for(d, g)
+    idx = np.arange(order)
+    H[idx, idx], L[idx, idx] = dh, dl
+    r, c = np.meshgrid(idx, idx, indexing="ij")
+    unused = (r > c) if uplo.upper() == "U" else (r < c)
+    if diag.upper() == "U":
+        unused |= r == c
+    H[:order, :order][unused] = np.nan
+    L[:order, :order][unused] = np.nan
+    return H, L
+
+
+def trsm_case(seed: int, side: str, uplo: str, transa: str, diag: str, m: int, n: int,
+              alpha=None, pad: int = 0) -> TrsmCase:
+    """Draw A (order m for side 'L', n for side 'R'; ``triangular_dd``), then
+    B (m x n, U(-1, 1) dd), then alpha (random dd in [0.5, 2] when None).
+    ``pad`` extra rows make both leading dimensions non-tight."""
+    g = rng(seed)
+    order = m if side.upper() == "L" else n
+    A = triangular_dd(g, order, uplo, diag, order + pad)
+    B = dd_matrix(g, m, n, m + pad)
+    al = dd_scalar(g) if alpha is None else alpha
+    return TrsmCase(side, uplo, transa, diag, m, n, al, A, B)
+
+
 def grouped_problems(seed: int, count: int = 4096, lo: int = 16, hi: int = 512):
     """m, n, k per problem, each round(exp(U(ln lo, ln hi)))."""
     g = rng(seed)

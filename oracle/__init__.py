@@ -13,9 +13,9 @@ Contents
       manual's description of the dd format (Sec. 5: a dd is hi + lo of two
       binary64 numbers, arithmetic from Knuth's and Dekker's error-free
       transformations);
-    - scalar dd Rgemm / Rsyrk / Rpotrf / Rpotrs: plain loops with DGEMM /
-      DSYRK / DPOTRF / DPOTRS argument semantics (Sec. 7.3 maps every MPBLAS
-      argument list onto the BLAS one);
+    - scalar dd Rgemm / Rsyrk / Rpotrf / Rpotrs / Rtrsm: plain loops with
+      DGEMM / DSYRK / DPOTRF / DPOTRS / DTRSM argument semantics (Sec. 7.3 maps
+      every MPBLAS argument list onto the BLAS one);
     - an exact tier: alpha*op(A)*op(B) + beta*C evaluated exactly in a
       superaccumulator and rounded once to the nearest dd.
 * ``fraction_ref.py`` -- the same definitions in pure Python ``fractions``,
@@ -27,7 +27,10 @@ Rsyrk -- the manual's worked examples (Sec. 7.3), the exact tier, Fraction
 brute force, closed forms and integer special cases; exact tier -- Fraction
 brute force and known exact sums; Rpotrf / Rpotrs -- exact integer factors,
 LAPACK test ratios (Sec. 8.2) and numpy's binary64 Cholesky on well
-conditioned matrices.
+conditioned matrices; Rtrsm -- exact integer solutions for all sixteen
+side/uplo/trans/diag variants, Fraction solves of tiny systems, the
+componentwise backward-error bound of substitution evaluated by the exact
+tier, and scipy's binary64 triangular solve.
 """
 from __future__ import annotations
 
@@ -97,6 +100,7 @@ def lib():
             L.oracle_dd_potrf.argtypes = [c, i64, _D, _D, i64]
             L.oracle_dd_potrf.restype = i64
             L.oracle_dd_potrs.argtypes = [c, i64, i64, _D, _D, i64, _D, _D, i64]
+            L.oracle_dd_trsm.argtypes = [c, c, c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64]
             L.oracle_exact_sum.argtypes = [i64, _D, _D, _D]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
@@ -262,6 +266,19 @@ def dd_potrs(uplo, F, B, n=None):
     nrhs = bh.shape[1]
     lib().oracle_dd_potrs(_ch(uplo), n, nrhs, _p(fh), _p(fl), _ld(fh), _p(bh), _p(bl),
                           _ld(bh))
+    return bh, bl
+
+
+def dd_trsm(side, uplo, transa, diag, alpha, A, B, m=None, n=None):
+    """Rtrsm (DTRSM semantics): returns X (hi, lo) with op(A) X = alpha B
+    (side 'L') or X op(A) = alpha B (side 'R'); B is m x n."""
+    ah, al = _f64(A[0]), _f64(A[1])
+    bh, bl = _f64(B[0]).copy(order="F"), _f64(B[1]).copy(order="F")
+    m = bh.shape[0] if m is None else m
+    n = bh.shape[1] if n is None else n
+    lib().oracle_dd_trsm(_ch(side), _ch(uplo), _ch(transa), _ch(diag), m, n,
+                         float(alpha[0]), float(alpha[1]), _p(ah), _p(al), _ld(ah), _p(bh),
+                         _p(bl), _ld(bh))
     return bh, bl
 
 

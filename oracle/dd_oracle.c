@@ -351,6 +351,66 @@ void oracle_dd_potrs(char uplo, int64_t n, int64_t nrhs, const double *ah, const
 #undef UF
 }
 
+/* Rtrsm: solve op(A) X = alpha B (side 'L') or X op(A) = alpha B (side 'R')
+ * for X, which overwrites the m x n matrix B; A is triangular (uplo), unit
+ * or not (diag), and only its uplo triangle is read.  DTRSM's semantics, the
+ * routine MPBLAS lists among its real routines (manual Sec. 6).  Plain
+ * substitution on one right-hand side at a time: for side 'L' the right-hand
+ * sides are the columns of B and the triangular matrix is T = op(A); for
+ * side 'R' they are the rows of B and T = op(A)^T, because x op(A) = b is
+ * op(A)^T x^T = b^T.  Each b is first scaled by alpha (a dd product), then
+ * x_i = (b_i - sum_c T(i, c) x_c) / T(i, i), the sum over the solved
+ * components in their natural order, and the division skipped for a unit
+ * diagonal.  alpha = 0 sets B to zero without reading A or B. */
+void oracle_dd_trsm(char side, char uplo, char transa, char diag, int64_t m, int64_t n,
+                    double alpha_hi, double alpha_lo, const double *ah, const double *al,
+                    int64_t lda, double *bh, double *bl, int64_t ldb) {
+    int right = (side == 'R' || side == 'r');
+    int upper = (uplo == 'U' || uplo == 'u');
+    int ta = is_trans(transa);
+    int unit = (diag == 'U' || diag == 'u');
+    odd alpha = {alpha_hi, alpha_lo};
+    if (m == 0 || n == 0) return;
+    if (alpha.hi == 0.0 && alpha.lo == 0.0) {
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = 0; i < m; ++i) bh[i + j * ldb] = bl[i + j * ldb] = 0.0;
+        return;
+    }
+    const int64_t order = right ? n : m;    /* order of T */
+    const int64_t count = right ? m : n;    /* right-hand sides */
+    /* T lower for (upper op(A) and side R) or (lower op(A) and side L) */
+    const int op_upper = upper ^ ta;
+    const int t_lower = right ? op_upper : !op_upper;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < count; ++q) {
+        /* element i of right-hand side q */
+#define BI(i) (right ? (q + (i) * ldb) : ((i) + q * ldb))
+        /* T(r, c) = op(A)(r, c) (side L) or op(A)(c, r) (side R);
+         * op(A)(r, c) = A(r, c), or A(c, r) when transposed */
+#define TIDX(r, c) ((right ^ ta) ? ((c) + (r) * lda) : ((r) + (c) * lda))
+        for (int64_t i = 0; i < order; ++i) {
+            odd b = {bh[BI(i)], bl[BI(i)]};
+            b = dd_mul(alpha, b);
+            bh[BI(i)] = b.hi;
+            bl[BI(i)] = b.lo;
+        }
+        for (int64_t s = 0; s < order; ++s) {
+            const int64_t i = t_lower ? s : order - 1 - s;
+            odd x = {bh[BI(i)], bl[BI(i)]};
+            const int64_t c0 = t_lower ? 0 : i + 1, c1 = t_lower ? i : order;
+            for (int64_t c = c0; c < c1; ++c) {
+                odd t = {ah[TIDX(i, c)], al[TIDX(i, c)]};
+                x = dd_sub(x, dd_mul(t, (odd){bh[BI(c)], bl[BI(c)]}));
+            }
+            if (!unit) x = dd_div(x, (odd){ah[TIDX(i, i)], al[TIDX(i, i)]});
+            bh[BI(i)] = x.hi;
+            bl[BI(i)] = x.lo;
+        }
+#undef TIDX
+#undef BI
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Tier 3: exact evaluation in a fixed-point superaccumulator                 */
 /* ------------------------------------------------------------------------- */

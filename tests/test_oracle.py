@@ -465,6 +465,155 @@ def test_potrf_matches_numpy_on_well_conditioned_spd():
 
 
 # ---------------------------------------------------------------------------
+# Rtrsm
+# ---------------------------------------------------------------------------
+
+TRSM_VARIANTS = [(s, u, t, d) for s in "LR" for u in "UL" for t in "NT" for d in "NU"]
+
+
+def op_triangle(A, uplo, transa, diag, order):
+    """op(A) as a dense float array: the uplo triangle of A (ones on a unit
+    diagonal, zeros elsewhere), transposed for transa = 'T'."""
+    T = np.triu(A[:order, :order]) if uplo == "U" else np.tril(A[:order, :order])
+    T = np.nan_to_num(T, nan=0.0)
+    if diag == "U":
+        np.fill_diagonal(T, 1.0)
+    return T.T if transa == "T" else T
+
+
+@pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS)
+def test_trsm_recovers_exact_integer_solution(side, uplo, transa, diag):
+    """Integer X, triangular integer A with power-of-two diagonal, alpha = 2:
+    B = op(A) X / 2 (or X op(A) / 2) is exact in binary64, and every step of
+    the substitution is exact in dd, so the solve must return X bit for bit.
+    The unused triangle (and a unit diagonal) hold NaN and must not be read."""
+    g = datagen.rng(70)
+    m, n = 9, 7
+    order = m if side == "L" else n
+    A = g.integers(-6, 7, (order, order)).astype(np.float64)
+    np.fill_diagonal(A, g.choice([-4.0, -2.0, -1.0, 1.0, 2.0, 4.0], order))
+    X = g.integers(-20, 21, (m, n)).astype(np.float64)
+    T = op_triangle(A, uplo, transa, diag, order)
+    Bx = (T @ X if side == "L" else X @ T) / 2.0
+    stored = A.copy()
+    r, c = np.meshgrid(np.arange(order), np.arange(order), indexing="ij")
+    unused = (r > c) if uplo == "U" else (r < c)
+    if diag == "U":
+        unused |= r == c
+    stored[unused] = np.nan
+    Ad = (np.asfortranarray(stored), np.zeros((order, order), order="F"))
+    xh, xl = oracle.dd_trsm(side, uplo, transa, diag, (2.0, 0.0), Ad,
+                            (np.asfortranarray(Bx), np.zeros((m, n), order="F")))
+    assert np.array_equal(xh, X) and not xl.any()
+
+
+@pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS[::3])
+def test_trsm_matches_fraction_solve(side, uplo, transa, diag):
+    """Tiny dd systems against the exact rational solution."""
+    c = datagen.trsm_case(71, side, uplo, transa, diag, 5, 4)
+    order = c.m if side == "L" else c.n
+    T = [[Fraction(0)] * order for _ in range(order)]
+    for i in range(order):
+        for j in range(order):
+            inside = (i <= j) if uplo == "U" else (i >= j)
+            if i == j and diag == "U":
+                v = Fraction(1)
+            elif inside:
+                v = F(c.A[0][i, j], c.A[1][i, j])
+            else:
+                v = Fraction(0)
+            if transa == "T":
+                T[j][i] = v
+            else:
+                T[i][j] = v
+    al = F(*c.alpha)
+    Bf = [[al * F(c.B[0][i, j], c.B[1][i, j]) for j in range(c.n)] for i in range(c.m)]
+    # side R: X T = B  <=>  T^T X^T = B^T
+    Ts = T if side == "L" else [list(r) for r in zip(*T)]
+    rhs = Bf if side == "L" else [list(r) for r in zip(*Bf)]
+    lower = all(Ts[i][j] == 0 for i in range(order) for j in range(i + 1, order))
+    cols = len(rhs[0])
+    Xs = [[Fraction(0)] * cols for _ in range(order)]
+    rows = range(order) if lower else range(order - 1, -1, -1)
+    for q in range(cols):
+        for i in rows:
+            s = rhs[i][q] - sum(Ts[i][k] * Xs[k][q] for k in range(order) if k != i)
+            Xs[i][q] = s / Ts[i][i]
+    X = Xs if side == "L" else [list(r) for r in zip(*Xs)]
+    xh, xl = oracle.dd_trsm(side, uplo, transa, diag, c.alpha, c.A, c.B)
+    for i in range(c.m):
+        for j in range(c.n):
+            err = abs(F(xh[i, j], xl[i, j]) - X[i][j])
+            assert err <= Fraction(2) ** -96 * abs(X[i][j]) + Fraction(2) ** -200
+
+
+def trsm_residual_over_bound(c, X):
+    """max_ij |op(A) X - alpha B|_ij / (4 (order + 2) 2^-104 (|op(A)||X| + |alpha B|)_ij),
+    the residual evaluated exactly by the superaccumulator tier (the
+    componentwise backward-error bound of substitution in dd arithmetic)."""
+    order = c.m if c.side == "L" else c.n
+    T = op_triangle(c.A[0], c.uplo, c.transa, c.diag, order)
+    Tl = op_triangle(c.A[1], c.uplo, c.transa, "N", order)
+    if c.diag == "U":
+        np.fill_diagonal(Tl, 0.0)
+    Td = (np.asfortranarray(T), np.asfortranarray(Tl))
+    Bd = (c.B[0][:c.m, :c.n], c.B[1][:c.m, :c.n])
+    rr, cc = np.meshgrid(np.arange(c.m), np.arange(c.n), indexing="ij")
+    neg = (-c.alpha[0], -c.alpha[1])
+    if c.side == "L":
+        R = oracle.exact_gemm_entries("N", "N", order, (1.0, 0.0), Td, X, neg, Bd,
+                                      rr.ravel(), cc.ravel())
+        scale = np.abs(T) @ np.abs(X[0])
+    else:
+        R = oracle.exact_gemm_entries("N", "N", order, (1.0, 0.0), X, Td, neg, Bd,
+                                      rr.ravel(), cc.ravel())
+        scale = np.abs(X[0]) @ np.abs(T)
+    scale = scale + abs(c.alpha[0]) * np.abs(Bd[0])
+    bound = 4 * (order + 2) * EPS_DD * scale.ravel() * (1 + 2.0 ** -40)
+    return (np.abs(R[0]) / bound).max()
+
+
+@pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS)
+def test_trsm_backward_error_within_bound(side, uplo, transa, diag):
+    c = datagen.trsm_case(72, side, uplo, transa, diag, 37, 29, pad=3)
+    X = oracle.dd_trsm(side, uplo, transa, diag, c.alpha, c.A, c.B, c.m, c.n)
+    X = (X[0][:c.m, :c.n], X[1][:c.m, :c.n])
+    assert trsm_residual_over_bound(c, X) <= 1.0
+    assert is_normalised(*X)
+
+
+@pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS[1::3])
+def test_trsm_matches_scipy_on_binary64_inputs(side, uplo, transa, diag):
+    """With lo planes zero the dd solve agrees with scipy's binary64 one to
+    binary64 accuracy (the matrices are diagonally dominant)."""
+    sla = pytest.importorskip("scipy.linalg")
+    c = datagen.trsm_case(73, side, uplo, transa, diag, 23, 31)
+    order = c.m if side == "L" else c.n
+    A0 = np.nan_to_num(c.A[0], nan=0.0)
+    B0 = c.B[0]
+    xh, _ = oracle.dd_trsm(side, uplo, transa, diag, (2.0, 0.0),
+                           (c.A[0], np.zeros_like(c.A[0])), (B0, np.zeros_like(B0)))
+    lower, trans = uplo == "L", 1 if transa == "T" else 0
+    if side == "L":
+        ref = sla.solve_triangular(A0, 2.0 * B0, trans=trans, lower=lower,
+                                   unit_diagonal=diag == "U")
+    else:   # X op(A) = 2B  <=>  op(A)^T X^T = 2B^T
+        ref = sla.solve_triangular(A0, 2.0 * B0.T, trans=1 - trans, lower=lower,
+                                   unit_diagonal=diag == "U").T
+    assert np.abs(xh - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_trsm_alpha_zero_and_empty():
+    c = datagen.trsm_case(74, "L", "U", "N", "N", 6, 5)
+    B = (c.B[0].copy(order="F"), c.B[1].copy(order="F"))
+    Anan = (np.full_like(c.A[0], np.nan), np.full_like(c.A[1], np.nan))
+    xh, xl = oracle.dd_trsm("L", "U", "N", "N", (0.0, 0.0), Anan, B)
+    assert not xh.any() and not xl.any()
+    xh, xl = oracle.dd_trsm("L", "U", "N", "N", c.alpha, c.A, B, 0, 5)
+    assert np.array_equal(xh, B[0]) and np.array_equal(xl, B[1])
+
+
+# ---------------------------------------------------------------------------
 # planted mistakes: every broken copy of the oracle must fail this file
 # ---------------------------------------------------------------------------
 
@@ -478,6 +627,13 @@ MUTANTS = {
     "no_sticky_rounding": ("if (round_bit && (sticky || (mant & 1))) mant += 1;",
                            "if (round_bit && (mant & 1)) mant += 1;"),
     "sqrt_without_newton": ("fast_two_sum(x, corr, &s, &e);", "fast_two_sum(x, 0.0, &s, &e);"),
+    "trsm_transposed_triangle": (
+        "#define TIDX(r, c) ((right ^ ta) ? ((c) + (r) * lda) : ((r) + (c) * lda))",
+        "#define TIDX(r, c) ((right ^ ta) ? ((r) + (c) * lda) : ((c) + (r) * lda))"),
+    "trsm_wrong_sweep": ("const int t_lower = right ? op_upper : !op_upper;",
+                         "const int t_lower = right ? !op_upper : op_upper;"),
+    "trsm_alpha_ignored": ("b = dd_mul(alpha, b);", "b = dd_add(b, (odd){0.0, 0.0});"),
+    "trsm_unit_diag_read": ("if (!unit) x = dd_div(", "x = dd_div("),
 }
 
 
