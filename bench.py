@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "sliced", "grouped", "served"])
+                    choices=["plain", "sliced", "crt", "grouped", "served"])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--groups", type=int, default=4096)
@@ -240,7 +240,12 @@ def run_ours(args):
         torch.cuda.empty_cache()
         sliced = {"vs_plain_2048": sliced_section(mp, torch, 2048, compare_plain=True),
                   "well_scaled": sliced_section(mp, torch, args.sliced_size),
-                  "ill_scaled_outer": sliced_section(mp, torch, args.sliced_size, ill="outer")}
+                  "ill_scaled_outer": sliced_section(mp, torch, args.sliced_size, ill="outer"),
+                  "crt_vs_plain_2048": sliced_section(mp, torch, 2048, compare_plain=True,
+                                                      form="crt"),
+                  "crt_well_scaled": sliced_section(mp, torch, args.sliced_size, form="crt"),
+                  "crt_ill_scaled_outer": sliced_section(mp, torch, args.sliced_size,
+                                                         ill="outer", form="crt")}
     if rank == 0:
         cpu = None if args.no_cpu or world > 1 else cpu_baseline(size, budget_s=15.0)
         line = {
@@ -282,18 +287,28 @@ def tensor_peak_tflops():
         return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
 
 
-def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=False):
-    """Time mp_dd_Rgemm_sliced (NN, m=n=k=size) with CUDA events on the
+def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=False,
+                   form="slices"):
+    """Time the split-precision Rgemm (NN, m=n=k=size) -- ``form`` "slices"
+    (mp_dd_Rgemm_sliced, 14 digits, 105 pair products) or "crt"
+    (mp_dd_Rgemm_crt, residues mod 32 moduli) -- with CUDA events on the
     launching stream; per-phase times from the library's own events."""
     c = datagen.gemm_case(2, "N", "N", size, size, size, ill=ill)
     dev = lambda pair: tuple(mp.to_device(x) for x in pair)
     A, B, C = dev(c.A), dev(c.B), dev(c.C)
-    ws = mp.workspace(mp.mp_dd_Rgemm_sliced_workspace(size, size, size, slices))
+    if form == "crt":
+        ws = mp.workspace(mp.mp_dd_Rgemm_crt_workspace(size, size, size))
+    else:
+        ws = mp.workspace(mp.mp_dd_Rgemm_sliced_workspace(size, size, size, slices))
     st = torch.cuda.current_stream()
 
     def call(Cout):
-        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta,
-                              Cout, size, slices, ws, ws.numel())
+        if form == "crt":
+            mp.mp_dd_Rgemm_crt("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta,
+                               Cout, size, ws, ws.numel())
+        else:
+            mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, A, size, B, size,
+                                  c.beta, Cout, size, slices, ws, ws.numel())
 
     C0 = tuple(x.clone() for x in C)
     call(C0)
@@ -312,13 +327,19 @@ def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=F
     phases = mp.mp_dd_sliced_phase_ms()
     mp.mp_dd_sliced_timing(False)
     total_ms = sum(phases)
-    L = mp.mp_dd_sliced_layout(size, size, size, slices)
-    pairs = slices * (slices + 1) // 2
+    if form == "crt":
+        L = mp.mp_dd_crt_layout(size, size, size)
+        pairs = len(L["moduli"])
+    else:
+        L = mp.mp_dd_sliced_layout(size, size, size, slices)
+        pairs = slices * (slices + 1) // 2
     band_flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * pairs
     peak, src = tensor_peak_tflops()
     achieved = band_flops / (phases[1] * 1e-3) / 1e12
+    what = (f"CRT form, {pairs} moduli" if form == "crt"
+            else f"sliced form, {slices} slices ({pairs} pair products)")
     out = {
-        "workload": f"sliced dd Rgemm NN m=n=k={size}, {slices} slices, "
+        "workload": f"split-precision dd Rgemm NN m=n=k={size}, {what}, "
                     f"{'well-scaled' if ill is None else ill + ' ill-scaled'}",
         "ms": total_ms, "dd_GFlops": 2.0 * size ** 3 / (total_ms * 1e-3) / 1e9,
         "phase_ms": {"scale_and_slice": phases[0], "band_products": phases[1],
@@ -475,15 +496,24 @@ def run_sliced_workload(args):
     import paper_2109_13406_gb300 as mp
 
     size, S = args.sliced_size, 14
+    crt = args.workload == "crt"
     c = datagen.gemm_case(2, "N", "N", size, size, size)
     dev = lambda pair: tuple(mp.to_device(x) for x in pair)
     A, B, C = dev(c.A), dev(c.B), dev(c.C)
-    ws = mp.workspace(mp.mp_dd_Rgemm_sliced_workspace(size, size, size, S))
+    ws = mp.workspace(mp.mp_dd_Rgemm_crt_workspace(size, size, size) if crt else
+                      mp.mp_dd_Rgemm_sliced_workspace(size, size, size, S))
     st = torch.cuda.current_stream()
 
+    def gemm(Ax, Bx, Cx):
+        if crt:
+            mp.mp_dd_Rgemm_crt("N", "N", size, size, size, c.alpha, Ax, size, Bx, size, c.beta,
+                               Cx, size, ws, ws.numel())
+        else:
+            mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, Ax, size, Bx, size,
+                                  c.beta, Cx, size, S, ws, ws.numel())
+
     def step():
-        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, A, size, B, size, c.beta, C,
-                              size, S, ws, ws.numel())
+        gemm(A, B, C)
 
     for _ in range(args.warmup):
         step()
@@ -503,9 +533,14 @@ def run_sliced_workload(args):
     clocks = clk.stop()
     ms = t0.elapsed_time(t1)
     value = 2.0 * size ** 3 * args.steps / (ms * 1e-3) / 1e9
-    L = mp.mp_dd_sliced_layout(size, size, size, S)
+    if crt:
+        L = mp.mp_dd_crt_layout(size, size, size)
+        products = len(L["moduli"])
+    else:
+        L = mp.mp_dd_sliced_layout(size, size, size, S)
+        products = S * (S + 1) // 2
     band_ms = sum(b[1] for b in band) / len(band)
-    flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * S * (S + 1) // 2
+    flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * products
     peak, src = tensor_peak_tflops()
     ach = flops / (band_ms * 1e-3) / 1e12
     # e2e: pinned host inputs -> device -> sliced Rgemm -> host result
@@ -520,9 +555,7 @@ def run_sliced_workload(args):
     def e2e_step():
         for d, h in zip(dA + dB + dC, hA + hB + hC):
             d.copy_(h, non_blocking=True)
-        mp.mp_dd_Rgemm_sliced("N", "N", size, size, size, c.alpha, (dA[0], dA[1]), size,
-                              (dB[0], dB[1]), size, c.beta, (dC[0], dC[1]), size, S, ws,
-                              ws.numel())
+        gemm((dA[0], dA[1]), (dB[0], dB[1]), (dC[0], dC[1]))
         for h, d in zip(hOut, dC):
             h.copy_(d, non_blocking=True)
 
@@ -541,17 +574,20 @@ def run_sliced_workload(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor (exact integer slices) + i64",
         "data": "synthetic (seeded PCG64; dd entries hi~U(-1,1), lo=hi*2^-53*U(-1,1) "
                 "renormalised; alpha,beta random dd in [0.5,2])",
-        "config": {"workload": f"sliced dd Rgemm NN m=n=k={size}, {S} slices, well-scaled",
-                   "m": size, "n": size, "k": size, "slices": S,
+        "config": {"workload": (f"split-precision dd Rgemm NN m=n=k={size}, " +
+                                (f"CRT form, {products} moduli" if crt else
+                                 f"sliced form, {S} slices") + ", well-scaled"),
+                   "m": size, "n": size, "k": size, "products": products,
                    "l2": f"inputs {3 * mat / 1e6:.0f} MB > 129 MB L2, no flush"},
         "roofline": {"bound": "tensor", "kernel": "band_gemm_kernel", "achieved": ach,
                      "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
                      "traffic": None},
-        "phase_ms": {"scale_and_slice": band[-1][0], "band_products": band[-1][1],
+        "phase_ms": {"scale_and_split": band[-1][0], "tensor_products": band[-1][1],
                      "recombine_epilogue": band[-1][2]},
         "e2e": {"value": 2.0 * size ** 3 * n_e2e / dt / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 3 * mat, "d2h_bytes_per_step": mat,
-                "api": "Python binding mp_dd_Rgemm_sliced, pinned host buffers"},
+                "api": "Python binding mp_dd_Rgemm_" + ("crt" if crt else "sliced") +
+                       ", pinned host buffers"},
         "gpu_launches": 7 * args.steps, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -769,7 +805,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "sliced":
+    elif args.workload in ("sliced", "crt"):
         run_sliced_workload(args)
     elif args.workload == "grouped":
         run_grouped_workload(args)

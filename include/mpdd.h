@@ -144,6 +144,30 @@ int mp_dd_Rgemm_host(const char *transa, const char *transb, int64_t m, int64_t 
 int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
                      mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
 
+/* Rtrsm (MPBLAS routine table, Sec. 6; DTRSM semantics): solve
+ *
+ *     op(A) X = alpha B   (side 'L', A m x m), or
+ *     X op(A) = alpha B   (side 'R', A n x n),
+ *
+ * for X, which overwrites the m x n B (column-major dd planes, ldb).  A is
+ * upper (uplo 'U') or lower ('L') triangular and only that triangle is
+ * read; diag 'U' takes its diagonal as one without reading it, 'N' divides
+ * by it.  op(A) = A ('N') or A^T ('T'; 'C' is 'T' for real data).  Flags are
+ * case-insensitive.  alpha = 0 sets B to zero without reading A or B; m = 0
+ * or n = 0 returns at once.  Arithmetic: substitution on 64 x 64 diagonal
+ * blocks (dd division by the diagonal) and dd Rgemm updates of the
+ * off-diagonal blocks, split recursively in halves so that the updates are
+ * large products.  Accuracy: the componentwise backward error of
+ * substitution, |op(A) X - alpha B| <= 4 (n_A + 2) 2^-104 (|op(A)||X| +
+ * |alpha B|), n_A the order of A; a zero diagonal entry gives Inf/NaN as
+ * DTRSM does (no check).  Asynchronous on the current stream.
+ * Errors: -1 side, -2 uplo, -3 transa, -4 diag, -5 m < 0, -6 n < 0,
+ * -8 A planes NULL, -9 lda < max(1, order of A), -10 B planes NULL,
+ * -11 ldb < max(1, m) (DTRSM's numbering). */
+int mp_dd_Rtrsm(const char *side, const char *uplo, const char *transa, const char *diag,
+                int64_t m, int64_t n, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_mat B,
+                int64_t ldb);
+
 /* ------------------------------------------------------------------------ */
 /* MPLAPACK: dd Cholesky factorisation and solve                             */
 /* ------------------------------------------------------------------------ */
@@ -186,7 +210,8 @@ typedef struct {
 /* Solve U^T X = B (trans 1) or U X = B (trans 0) in place, U the n x n
  * (n <= 64) upper factor block at u_hi/u_lo (lower_u: read it from 'L'
  * storage), B n x nrhs at b_hi/b_lo (lower_b: B is stored transposed, as
- * the panel of an 'L' factor is). */
+ * the panel of an 'L' factor is).  unit_diag != 0 takes U's diagonal as
+ * one without reading it. */
 typedef struct {
     const double *u_hi, *u_lo;
     int64_t ldu;
@@ -194,7 +219,7 @@ typedef struct {
     int64_t ldb;
     int64_t n, nrhs;
     const int64_t *info;
-    int32_t trans, lower_u, lower_b, reserved;
+    int32_t trans, lower_u, lower_b, unit_diag;
 } mp_dd_trsm_desc;
 
 /* One launch: one CTA per diagonal block.  Errors: -1 count, -2 descs. */
@@ -358,12 +383,13 @@ int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offs
 /* Read the device status word of a workspace (synchronous copy). */
 int mp_dd_workspace_status(const void *workspace, int *status);
 
-/* Per-phase timing of sliced calls (no counterpart in the manual).  With
- * enable != 0, later mp_dd_Rgemm_sliced calls from this thread record CUDA
- * events around their three phases on the current stream;
- * mp_dd_sliced_phase_ms waits for the last timed call and writes the
- * milliseconds of (0) scaling and slicing, (1) band products on the tensor
- * cores, (2) recombination and epilogue.  Returns 2002 if no call was timed. */
+/* Per-phase timing of split-precision calls (no counterpart in the manual).
+ * With enable != 0, later mp_dd_Rgemm_sliced and mp_dd_Rgemm_crt calls from
+ * this thread record CUDA events around their three phases on the current
+ * stream; mp_dd_sliced_phase_ms waits for the last timed call and writes the
+ * milliseconds of (0) scaling and slicing (or residues), (1) the tensor-core
+ * products, (2) recombination (or CRT reconstruction) and epilogue.  Returns
+ * 2002 if no call was timed. */
 int mp_dd_sliced_timing(int enable);
 int mp_dd_sliced_phase_ms(float ms[3]);
 

@@ -484,6 +484,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     auto *RES = reinterpret_cast<uint8_t *>(w + L.off_res);
     const int a_rc = p.ta ? 0 : 1, b_rc = p.tb ? 1 : 0;
     int rc;
+    sliced_timing_mark(0, st);
     if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
     if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
     if ((rc = launch_residues(L.N, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
@@ -493,6 +494,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
                               RB, st)))
         return rc;
 
+    sliced_timing_mark(1, st);
     CUtensorMap tmA, tmB;
     if ((rc = make_tmap(&tmA, RA, (int64_t)L.N * L.m_pad, L.k_pad, kBandTM))) return rc;
     if ((rc = make_tmap(&tmB, RB, (int64_t)L.N * L.n_pad, L.k_pad, TN))) return rc;
@@ -509,6 +511,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ba.diag = 1;
     for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
     if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
+    sliced_timing_mark(2, st);
 
     // CRT constants
     CrtArgs ca{};
@@ -540,7 +543,9 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
     crt_kernel<<<(unsigned)blocks, 256, 0, st>>>(ca);
-    return check_launch("crt_kernel");
+    rc = check_launch("crt_kernel");
+    sliced_timing_mark(3, st);
+    return rc;
 }
 
 }  // namespace mpdd

@@ -41,6 +41,7 @@ int sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
 int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t stream);
 int read_status(const void *ws, int *status);
 void sliced_timing_enable(int on);
+void sliced_timing_mark(int phase, cudaStream_t stream);  // phases 0..3 of a timed call
 int sliced_timing_read(float *ms);
 
 // Grouped dd Rgemm (one persistent launch over many problems).
@@ -55,6 +56,10 @@ int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t
 int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double *al,
               int64_t lda, double *bh, double *bl, int64_t ldb, const int64_t *info,
               cudaStream_t stream);
+// dd Rtrsm (every side / uplo / trans / diag variant), alpha != 0, m, n > 0.
+int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp_dd alpha,
+             const double *ah, const double *al, int64_t lda, double *bh, double *bl,
+             int64_t ldb, cudaStream_t stream);
 int launch_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *ds, cudaStream_t st);
 int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
                       cudaStream_t st);

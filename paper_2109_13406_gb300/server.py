@@ -4,8 +4,9 @@ Each request brings G (n x 2n) and B (n x nrhs) as dd matrices.  Its work is
 a fixed list of operations on its own device buffers:
 
   * F := G G^T: for n >= ``sliced_min_n`` one split-precision Rgemm on the
-    tensor cores (``mp_dd_Rgemm_sliced``, both triangles written, within the
-    same accuracy bound); for smaller n as 2n/nb chunked Rsyrk updates
+    tensor cores (``mp_dd_Rgemm_crt``, the residue form; both triangles
+    written, within the same accuracy bound); for smaller n as 2n/nb chunked
+    Rsyrk updates
     F += G_c G_c^T over column chunks G_c of G (so no single FP64 operation
     is large enough to hold a scheduler step hostage);
   * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
@@ -32,8 +33,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rgemm_sliced,
-               mp_dd_Rgemm_sliced_workspace, mp_dd_trsm_batch, to_device, to_numpy, workspace)
+from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rgemm_crt, mp_dd_Rgemm_crt_workspace,
+               mp_dd_trsm_batch, to_device, to_numpy, workspace)
 from . import grouped as gr
 
 
@@ -59,7 +60,7 @@ class Request:
     def nrhs(self) -> int:
         return int(self.B[0].shape[1]) if self.B is not None else self.nrhs_
 
-    sliced_ws: int = 0    # workspace bytes of the sliced Rsyrk (0 = FP64 path)
+    sliced_ws: int = 0    # workspace bytes of the tensor-core Rsyrk (0 = FP64 path)
 
     def footprint(self) -> int:
         """Device bytes while admitted: G, F, X planes, the info word and the
@@ -107,7 +108,7 @@ class SpdServer:
 
     def _size(self, r: Request) -> None:
         if r.n >= self.sliced_min_n and r.sliced_ws == 0:
-            r.sliced_ws = mp_dd_Rgemm_sliced_workspace(r.n, r.n, 2 * r.n, 0)
+            r.sliced_ws = mp_dd_Rgemm_crt_workspace(r.n, r.n, 2 * r.n)
 
     def admit(self, r: Request, now: float) -> None:
         self._size(r)
@@ -180,8 +181,8 @@ class SpdServer:
                 G, F = args
                 n = r.n
                 ws = workspace(r.sliced_ws)
-                mp_dd_Rgemm_sliced("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F,
-                                   n, 0, ws, ws.numel())
+                mp_dd_Rgemm_crt("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F, n,
+                                ws, ws.numel())
                 self.launches += 1
             elif kind == "gemm":
                 ta, tb, m, n, k, al, A, B, be, C, uplo = args
