@@ -246,6 +246,10 @@ def run_ours(args):
                   "crt_well_scaled": sliced_section(mp, torch, args.sliced_size, form="crt"),
                   "crt_ill_scaled_outer": sliced_section(mp, torch, args.sliced_size,
                                                          ill="outer", form="crt")}
+    trsm = None
+    if not args.no_sliced:
+        trsm = {f"{s}{u}{t}N_{size}": trsm_section(mp, torch, size, s, u, t)
+                for (s, u, t) in (("L", "U", "N"), ("R", "L", "T"))}
     if rank == 0:
         cpu = None if args.no_cpu or world > 1 else cpu_baseline(size, budget_s=15.0)
         line = {
@@ -263,12 +267,51 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "sliced": sliced,
+            "rtrsm": trsm,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def trsm_section(mp, torch, size, side, uplo, transa, reps=2):
+    """Time mp_dd_Rtrsm (m = n = size, diag 'N') with CUDA events on the
+    launching stream.  dd-flops: m^2 n (side L) or m n^2 (side R), the LAPACK
+    count; FP64 work: the m^2 n / 2 multiply-adds of the off-diagonal blocks
+    at the plain kernel's instructions per multiply-add."""
+    c = datagen.trsm_case(3, side, uplo, transa, "N", size, size)
+    A = tuple(mp.to_device(x) for x in c.A)
+    B0 = tuple(mp.to_device(x) for x in c.B)
+    B = tuple(x.clone() for x in B0)
+    st = torch.cuda.current_stream()
+
+    def call():
+        mp.mp_dd_Rtrsm(side, uplo, transa, "N", size, size, c.alpha, A, size, B, size)
+
+    call()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        for x, y in zip(B, B0):
+            x.copy_(y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        call()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = sum(ts) / len(ts)
+    flops = float(size) ** 3
+    instr = FP64_OPS_PER_MAC * flops / 2 / (ms * 1e-3) / 1e9
+    return {"workload": f"dd Rtrsm side={side} uplo={uplo} transa={transa} diag=N, "
+                        f"m=n={size}, diagonally dominant A", "ms": ms,
+            "dd_GFlops": flops / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "alu", "achieved": instr, "peak": NOMINAL_FP64_INSTR / 1e9,
+                         "unit": "GFP64instr/s", "frac": instr / (NOMINAL_FP64_INSTR / 1e9),
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FP64 "
+                                        "instr/s (derived)"}}
 
 
 # ----------------------------------------------------------------------------

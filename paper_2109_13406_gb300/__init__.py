@@ -26,8 +26,9 @@ __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
-    "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status", "Rgemm",
-    "Rsyrk", "Rgemm_sliced", "workspace", "dd_empty", "to_device", "to_numpy", "lib",
+    "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
+    "mp_dd_Rtrsm", "mp_dd_Rpotrf", "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
+    "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
 
 _LIB = _abi.load()
@@ -238,6 +239,13 @@ def mp_dd_Rpotrf(uplo, n, A, lda, info, check=True):
     return _check(rc, "mp_dd_Rpotrf") if check else rc
 
 
+def mp_dd_Rtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rtrsm(_flag(side), _flag(uplo), _flag(transa), _flag(diag), m, n,
+                          _dd(alpha), _cm(A), lda, _m(B), ldb)
+    return _check(rc, "mp_dd_Rtrsm") if check else rc
+
+
 def mp_dd_Rpotrs(uplo, n, nrhs, A, lda, B, ldb, factor_info=None, check=True):
     _sync_stream()
     rc = _LIB.mp_dd_Rpotrs(_flag(uplo), n, nrhs, _cm(A), lda, _m(B), ldb, _ptr(factor_info))
@@ -313,6 +321,13 @@ def Rgemm(transa, transb, alpha, A, B, beta, C, m=None, n=None, k=None):
         n = B[0].shape[0] if tb else B[0].shape[1]
     return mp_dd_Rgemm(transa, transb, m, n, k, alpha, A, _ld(A[0]), B, _ld(B[0]), beta, C,
                        _ld(C[0]))
+
+
+def Rtrsm(side, uplo, transa, diag, alpha, A, B, m=None, n=None):
+    """mp_dd_Rtrsm on (hi, lo) device tensors; B (m x n) is overwritten by X."""
+    m = B[0].shape[0] if m is None else m
+    n = B[0].shape[1] if n is None else n
+    return mp_dd_Rtrsm(side, uplo, transa, diag, m, n, alpha, A, _ld(A[0]), B, _ld(B[0]))
 
 
 def Rsyrk(uplo, trans, alpha, A, beta, C, n=None, k=None):

@@ -56,7 +56,7 @@ class MpDDTrsmDesc(ctypes.Structure):
                 ("b_hi", ctypes.c_void_p), ("b_lo", ctypes.c_void_p), ("ldb", ctypes.c_int64),
                 ("n", ctypes.c_int64), ("nrhs", ctypes.c_int64), ("info", ctypes.c_void_p),
                 ("trans", ctypes.c_int32), ("lower_u", ctypes.c_int32),
-                ("lower_b", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lower_b", ctypes.c_int32), ("unit_diag", ctypes.c_int32)]
 
 _c = ctypes.c_char_p
 _i64 = ctypes.c_int64
@@ -95,6 +95,7 @@ SIGNATURES = {
     "mp_dd_Rpotrs": (_int, [_c, _i64, _i64, MpDDCMat, _i64, MpDDMat, _i64, _vp]),
     "mp_dd_potrf_diag_batch": (_int, [_i64, _vp]),
     "mp_dd_trsm_batch": (_int, [_i64, _vp, _i64]),
+    "mp_dd_Rtrsm": (_int, [_c, _c, _c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDMat, _i64]),
     "mp_dd_Rgemm_grouped_workspace": (_sz, [_i64, ctypes.POINTER(MpDDGemmDesc)]),
     "mp_dd_Rgemm_grouped_prepare": (_int, [_i64, ctypes.POINTER(MpDDGemmDesc), _vp, _sz]),
     "mp_dd_Rgemm_grouped_run": (_int, [_vp]),

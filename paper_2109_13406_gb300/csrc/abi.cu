@@ -390,6 +390,43 @@ int mp_dd_Rpotrs(const char *uplo, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_
                      tls().stream);
 }
 
+int mp_dd_Rtrsm(const char *side, const char *uplo, const char *transa, const char *diag,
+                int64_t m, int64_t n, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_mat B,
+                int64_t ldb) {
+    clear_error();
+    const int right = flag_is(side, 'R') ? 1 : flag_is(side, 'L') ? 0 : -1;
+    if (right < 0) return fail(-1, "Rtrsm: illegal side");
+    const int ul = uplo_flag(uplo);
+    if (ul < 0) return fail(-2, "Rtrsm: illegal uplo");
+    const int ta = trans_flag(transa);
+    if (ta < 0) return fail(-3, "Rtrsm: illegal transa");
+    const int unit = flag_is(diag, 'U') ? 1 : flag_is(diag, 'N') ? 0 : -1;
+    if (unit < 0) return fail(-4, "Rtrsm: illegal diag");
+    if (m < 0) return fail(-5, "Rtrsm: m < 0");
+    if (n < 0) return fail(-6, "Rtrsm: n < 0");
+    const int64_t order = right ? n : m;
+    const bool work = m > 0 && n > 0;
+    if (work && !dd_is_zero(alpha) && (A.hi == nullptr || A.lo == nullptr))
+        return fail(-8, "Rtrsm: A is NULL");
+    if (lda < imax(1, order)) return fail(-9, "Rtrsm: lda < max(1, order of A)");
+    if (work && (B.hi == nullptr || B.lo == nullptr)) return fail(-10, "Rtrsm: B is NULL");
+    if (ldb < imax(1, m)) return fail(-11, "Rtrsm: ldb < max(1, m)");
+    if (!work) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    cudaStream_t st = tls().stream;
+    if (dd_is_zero(alpha)) {
+        for (double *plane : {B.hi, B.lo}) {
+            cudaError_t e = cudaMemset2DAsync(plane, (size_t)ldb * sizeof(double), 0,
+                                              (size_t)m * sizeof(double), (size_t)n, st);
+            if (e != cudaSuccess) return cuda_fail(e, "Rtrsm: zero B");
+        }
+        return 0;
+    }
+    return run_trsm(right, ul == 2, ta, unit, m, n, alpha, A.hi, A.lo, lda, B.hi, B.lo, ldb,
+                    st);
+}
+
 int mp_dd_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *descs) {
     clear_error();
     if (count < 0) return fail(-1, "potrf_diag_batch: count < 0");

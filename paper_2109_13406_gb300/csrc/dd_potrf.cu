@@ -1,12 +1,14 @@
 // dd Cholesky factorisation and solve (Rpotrf / Rpotrs, MPLAPACK routine
 // table of the manual's Sec. 6; the Rpotrf benchmark of Sec. 10.5), built as
-// the LAPACK blocked right-looking algorithm on three kernels:
+// the LAPACK blocked right-looking algorithm on three kernels, and the
+// triangular solve Rtrsm (MPBLAS, Sec. 6) on the same two of them:
 //
 //  * diag:  unblocked Cholesky of one nb x nb diagonal block (nb <= 64), in
 //           shared memory, one CTA per block;
 //  * trsm:  triangular solve with one nb x nb factor block for up to 32
 //           right-hand-side columns per CTA (forward with U^T, backward
-//           with U);
+//           with U), optionally scaling the right-hand sides by alpha and
+//           taking the diagonal as unit;
 //  * the trailing updates are the dd Rsyrk / Rgemm kernels.
 //
 // Storage follows LAPACK: uplo 'U' factors A = U^T U in the upper triangle,
@@ -116,17 +118,25 @@ struct TrsmSmem {
     double bh[NB][TC + 1], bl[NB][TC + 1];
 };
 
+// B := alpha B before the solve when scale != 0.
+struct TrsmScale {
+    dd alpha;
+    int scale;
+};
+
 // Solve U^T X = B (trans = 1) or U X = B (trans = 0) for the columns
-// [c0, c0 + TC) of B, in place.  U is the n x n upper factor block.
-__device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s) {
+// [c0, c0 + TC) of B, in place.  U is the n x n upper factor block; with
+// d.unit_diag its diagonal is taken as one and never read.
+__device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, TrsmScale sc) {
     const int n = (int)d.n;
     const int tid = threadIdx.x;
     if (d.info != nullptr && *d.info != 0) return;
     const int64_t ncol = d.nrhs - c0 < TC ? d.nrhs - c0 : TC;
     if (ncol <= 0) return;
+    const int unit = d.unit_diag != 0;
     for (int e = tid; e < n * n; e += NT) {
         int r = e % n, c = e / n;
-        if (r <= c) {
+        if (r < c || (r == c && !unit)) {
             int64_t o = uidx(d.lower_u, r, c, d.ldu);
             s.uh[r][c] = d.u_hi[o];
             s.ul[r][c] = d.u_lo[o];
@@ -136,14 +146,16 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s) {
         int r = e % n, c = e / n;
         if (c < ncol) {
             int64_t o = uidx(d.lower_b, r, c0 + c, d.ldb);
-            s.bh[r][c] = d.b_hi[o];
-            s.bl[r][c] = d.b_lo[o];
+            dd b{d.b_hi[o], d.b_lo[o]};
+            if (sc.scale) b = mul(sc.alpha, b);
+            s.bh[r][c] = b.hi;
+            s.bl[r][c] = b.lo;
         }
     }
     __syncthreads();
     for (int step = 0; step < n; ++step) {
         const int i = d.trans ? step : n - 1 - step;
-        if (tid < ncol) {
+        if (tid < ncol && !unit) {
             dd x = div(dd{s.bh[i][tid], s.bl[i][tid]}, dd{s.uh[i][i], s.ul[i][i]});
             s.bh[i][tid] = x.hi;
             s.bl[i][tid] = x.lo;
@@ -175,13 +187,17 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s) {
 
 __global__ void __launch_bounds__(NT) trsm_batch_kernel(const mp_dd_trsm_desc *ds) {
     extern __shared__ double smem_t[];
-    trsm_one(ds[blockIdx.x], (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t));
+    trsm_one(ds[blockIdx.x], (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t),
+             TrsmScale{dd{1.0, 0.0}, 0});
 }
 
-__global__ void __launch_bounds__(NT) trsm_single_kernel(const mp_dd_trsm_desc d) {
+__global__ void __launch_bounds__(NT) trsm_single_kernel(const mp_dd_trsm_desc d,
+                                                         TrsmScale sc) {
     extern __shared__ double smem_t[];
-    trsm_one(d, (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t));
+    trsm_one(d, (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t), sc);
 }
+
+constexpr TrsmScale kNoScale{dd{1.0, 0.0}, 0};
 
 bool g_attr_done = false;
 
@@ -255,7 +271,7 @@ int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t
         tr.n = nb; tr.nrhs = rest; tr.trans = 1; tr.lower_u = lower; tr.lower_b = lower;
         tr.info = info;
         dim3 grid(1, (unsigned)ceil_div(rest, TC));
-        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr);
+        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr, kNoScale);
         if ((rc = check_launch("trsm_single_kernel"))) return rc;
         // trailing: A(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) on the stored triangle
         GemmArgs p{};
@@ -294,7 +310,7 @@ int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double
         tr.n = nb; tr.nrhs = nrhs; tr.trans = trans; tr.lower_u = lower; tr.lower_b = 0;
         tr.info = info;
         dim3 grid(1, (unsigned)ceil_div(nrhs, TC));
-        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr);
+        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr, kNoScale);
         return check_launch("trsm_single_kernel");
     };
     auto update = [&](int64_t j, int forward) -> int {
@@ -333,6 +349,116 @@ int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double
         if ((rc = update(b * NB, 0))) return rc;
     }
     return 0;
+}
+
+// ------------------------------------------------------------------ Rtrsm
+//
+// Every DTRSM variant is one triangular system T Y = B' with several
+// right-hand sides: for side 'L' T = op(A) and B' = B; for side 'R'
+// X op(A) = B is op(A)^T X^T = B^T, so T = op(A)^T and B' = B^T (read
+// through the transposed accessor).  T is then either U^T (lower: forward
+// substitution) or U (upper: backward substitution) for the upper-stored
+// view U(r, c) = A[uidx(lower_a, r, c)] of A's triangle.  The solve splits
+// T recursively into halves (at multiples of 64): solve the first half,
+// update the second half's right-hand sides with one dd Rgemm of the whole
+// off-diagonal block, solve the second half.  The leaves are 64 x 64
+// diagonal blocks in shared memory.  alpha is applied where each row block
+// of B' is first touched: by the leaf kernel (the first block) or as the
+// beta of its first Rgemm update.
+
+namespace {
+
+struct TrsmPlan {
+    int lower_a;   // A's triangle is 'L' (read through the transposed accessor)
+    int forward;   // T is lower: forward substitution
+    int right;     // B' = B^T
+    int unit;
+    const double *ah, *al;
+    int64_t lda;
+    double *bh, *bl;
+    int64_t ldb;
+    int64_t nrhs;  // columns of B'
+    mp_dd alpha;
+    int alpha_one;
+    cudaStream_t st;
+};
+
+int trsm_leaf(const TrsmPlan &P, int64_t j0, int64_t nt, bool first) {
+    mp_dd_trsm_desc tr{};
+    const int64_t o = uidx(P.lower_a, j0, j0, P.lda);
+    tr.u_hi = P.ah + o; tr.u_lo = P.al + o; tr.ldu = P.lda;
+    const int64_t ob = uidx(P.right, j0, 0, P.ldb);
+    tr.b_hi = P.bh + ob; tr.b_lo = P.bl + ob; tr.ldb = P.ldb;
+    tr.n = nt; tr.nrhs = P.nrhs; tr.trans = P.forward; tr.lower_u = P.lower_a;
+    tr.lower_b = P.right; tr.unit_diag = P.unit; tr.info = nullptr;
+    const TrsmScale sc{dd{P.alpha.hi, P.alpha.lo}, first && !P.alpha_one};
+    const int64_t gy = ceil_div(P.nrhs, TC);
+    if (gy > 65535) return fail(MP_DD_ERR_TOO_LARGE, "Rtrsm: too many right-hand sides");
+    trsm_single_kernel<<<dim3(1, (unsigned)gy), NT, sizeof(TrsmSmem), P.st>>>(tr, sc);
+    return check_launch("trsm_single_kernel");
+}
+
+// B'(rows r0 .. r0+mr) -= T(rows, cols c0 .. c0+kc) B'(cols), with beta = alpha
+// when these rows are touched for the first time.
+int trsm_update(const TrsmPlan &P, int64_t r0, int64_t mr, int64_t c0, int64_t kc,
+                bool first) {
+    // T(r, c) off the diagonal is A[uidx(tl, r, c)]: as stored (tl = 0) or
+    // transposed (tl = 1); the block starts at uidx(tl, r0, c0)
+    const int tl = P.lower_a ^ P.forward;
+    const int64_t ot = uidx(tl, r0, c0, P.lda);
+    GemmArgs p{};
+    p.alpha = mp_dd{-1.0, 0.0};
+    p.beta = first ? P.alpha : mp_dd{1.0, 0.0};
+    p.alpha_zero = 0; p.alpha_one = 0; p.beta_zero = 0; p.tri = 0; p.info = nullptr;
+    if (!P.right) {
+        // B(r0:, :) -= T_sub B(c0:, :)
+        p.m = mr; p.n = P.nrhs; p.k = kc;
+        p.ah = P.ah + ot; p.al = P.al + ot; p.lda = P.lda; p.ta = tl;
+        p.bh = P.bh + c0; p.bl = P.bl + c0; p.ldb = P.ldb; p.tb = 0;
+        p.ch = P.bh + r0; p.cl = P.bl + r0; p.ldc = P.ldb;
+    } else {
+        // B(:, r0:) -= B(:, c0:) T_sub^T
+        p.m = P.nrhs; p.n = mr; p.k = kc;
+        p.ah = P.bh + c0 * P.ldb; p.al = P.bl + c0 * P.ldb; p.lda = P.ldb; p.ta = 0;
+        p.bh = P.ah + ot; p.bl = P.al + ot; p.ldb = P.lda; p.tb = !tl;
+        p.ch = P.bh + r0 * P.ldb; p.cl = P.bl + r0 * P.ldb; p.ldc = P.ldb;
+    }
+    return launch_gemm_plain(p, P.st);
+}
+
+int trsm_rec(const TrsmPlan &P, int64_t j0, int64_t nt, bool first) {
+    if (nt <= NB) return trsm_leaf(P, j0, nt, first);
+    const int64_t h = ceil_div(nt / 2, (int64_t)NB) * NB;   // 64 <= h < nt
+    int rc;
+    if (P.forward) {
+        if ((rc = trsm_rec(P, j0, h, first))) return rc;
+        if ((rc = trsm_update(P, j0 + h, nt - h, j0, h, first))) return rc;
+        return trsm_rec(P, j0 + h, nt - h, false);
+    }
+    if ((rc = trsm_rec(P, j0 + h, nt - h, first))) return rc;
+    if ((rc = trsm_update(P, j0, h, j0 + h, nt - h, first))) return rc;
+    return trsm_rec(P, j0, h, false);
+}
+
+}  // namespace
+
+int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp_dd alpha,
+             const double *ah, const double *al, int64_t lda, double *bh, double *bl,
+             int64_t ldb, cudaStream_t st) {
+    int rc = set_attrs();
+    if (rc) return rc;
+    TrsmPlan P{};
+    P.lower_a = lower;
+    P.forward = lower ^ trans ^ right;
+    P.right = right;
+    P.unit = unit;
+    P.ah = ah; P.al = al; P.lda = lda;
+    P.bh = bh; P.bl = bl; P.ldb = ldb;
+    P.nrhs = right ? m : n;
+    P.alpha = alpha;
+    P.alpha_one = alpha.hi == 1.0 && alpha.lo == 0.0;
+    P.st = st;
+    return trsm_rec(P, 0, right ? n : m, true);
 }
 
 }  // namespace mpdd

@@ -22,6 +22,7 @@ import datagen
 import oracle
 from oracle import fraction_ref as fr
 from ddcheck import EPS_DD, U, err_over_bound, gemm_bound, is_normalised
+from trsmcheck import TRSM_VARIANTS, op_triangle, trsm_residual_over_bound
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN = os.path.join(HERE, "golden")
@@ -468,17 +469,6 @@ def test_potrf_matches_numpy_on_well_conditioned_spd():
 # Rtrsm
 # ---------------------------------------------------------------------------
 
-TRSM_VARIANTS = [(s, u, t, d) for s in "LR" for u in "UL" for t in "NT" for d in "NU"]
-
-
-def op_triangle(A, uplo, transa, diag, order):
-    """op(A) as a dense float array: the uplo triangle of A (ones on a unit
-    diagonal, zeros elsewhere), transposed for transa = 'T'."""
-    T = np.triu(A[:order, :order]) if uplo == "U" else np.tril(A[:order, :order])
-    T = np.nan_to_num(T, nan=0.0)
-    if diag == "U":
-        np.fill_diagonal(T, 1.0)
-    return T.T if transa == "T" else T
 
 
 @pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS)
@@ -545,32 +535,6 @@ def test_trsm_matches_fraction_solve(side, uplo, transa, diag):
         for j in range(c.n):
             err = abs(F(xh[i, j], xl[i, j]) - X[i][j])
             assert err <= Fraction(2) ** -96 * abs(X[i][j]) + Fraction(2) ** -200
-
-
-def trsm_residual_over_bound(c, X):
-    """max_ij |op(A) X - alpha B|_ij / (4 (order + 2) 2^-104 (|op(A)||X| + |alpha B|)_ij),
-    the residual evaluated exactly by the superaccumulator tier (the
-    componentwise backward-error bound of substitution in dd arithmetic)."""
-    order = c.m if c.side == "L" else c.n
-    T = op_triangle(c.A[0], c.uplo, c.transa, c.diag, order)
-    Tl = op_triangle(c.A[1], c.uplo, c.transa, "N", order)
-    if c.diag == "U":
-        np.fill_diagonal(Tl, 0.0)
-    Td = (np.asfortranarray(T), np.asfortranarray(Tl))
-    Bd = (c.B[0][:c.m, :c.n], c.B[1][:c.m, :c.n])
-    rr, cc = np.meshgrid(np.arange(c.m), np.arange(c.n), indexing="ij")
-    neg = (-c.alpha[0], -c.alpha[1])
-    if c.side == "L":
-        R = oracle.exact_gemm_entries("N", "N", order, (1.0, 0.0), Td, X, neg, Bd,
-                                      rr.ravel(), cc.ravel())
-        scale = np.abs(T) @ np.abs(X[0])
-    else:
-        R = oracle.exact_gemm_entries("N", "N", order, (1.0, 0.0), X, Td, neg, Bd,
-                                      rr.ravel(), cc.ravel())
-        scale = np.abs(X[0]) @ np.abs(T)
-    scale = scale + abs(c.alpha[0]) * np.abs(Bd[0])
-    bound = 4 * (order + 2) * EPS_DD * scale.ravel() * (1 + 2.0 ** -40)
-    return (np.abs(R[0]) / bound).max()
 
 
 @pytest.mark.parametrize("side,uplo,transa,diag", TRSM_VARIANTS)
