@@ -13,9 +13,10 @@ Contents
       manual's description of the dd format (Sec. 5: a dd is hi + lo of two
       binary64 numbers, arithmetic from Knuth's and Dekker's error-free
       transformations);
-    - scalar dd Rgemm / Rsyrk / Rpotrf / Rpotrs / Rtrsm: plain loops with
-      DGEMM / DSYRK / DPOTRF / DPOTRS / DTRSM argument semantics (Sec. 7.3 maps
-      every MPBLAS argument list onto the BLAS one);
+    - scalar dd Rgemm / Rsyrk / Rsyr2k / Rsymm / Rpotrf / Rpotrs / Rtrsm:
+      plain loops with the DGEMM / DSYRK / DSYR2K / DSYMM / DPOTRF / DPOTRS /
+      DTRSM argument semantics (Sec. 7.3 maps every MPBLAS argument list onto
+      the BLAS one);
     - an exact tier: alpha*op(A)*op(B) + beta*C evaluated exactly in a
       superaccumulator and rounded once to the nearest dd.
 * ``fraction_ref.py`` -- the same definitions in pure Python ``fractions``,
@@ -30,7 +31,10 @@ LAPACK test ratios (Sec. 8.2) and numpy's binary64 Cholesky on well
 conditioned matrices; Rtrsm -- exact integer solutions for all sixteen
 side/uplo/trans/diag variants, Fraction solves of tiny systems, the
 componentwise backward-error bound of substitution evaluated by the exact
-tier, and scipy's binary64 triangular solve.
+tier, and scipy's binary64 triangular solve; Rsyr2k / Rsymm -- the exact
+tier on the equivalent Rgemm of concatenated or symmetrised operands,
+integer inputs against binary64 matmul, Fraction brute force, and the
+closed form Rsyr2k(A, A) = Rsyrk(A) with 2 alpha.
 """
 from __future__ import annotations
 
@@ -101,6 +105,10 @@ def lib():
             L.oracle_dd_potrf.restype = i64
             L.oracle_dd_potrs.argtypes = [c, i64, i64, _D, _D, i64, _D, _D, i64]
             L.oracle_dd_trsm.argtypes = [c, c, c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64]
+            L.oracle_dd_syr2k.argtypes = [c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64, d, d,
+                                          _D, _D, i64]
+            L.oracle_dd_symm.argtypes = [c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64, d, d,
+                                         _D, _D, i64]
             L.oracle_exact_sum.argtypes = [i64, _D, _D, _D]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
@@ -267,6 +275,32 @@ def dd_potrs(uplo, F, B, n=None):
     lib().oracle_dd_potrs(_ch(uplo), n, nrhs, _p(fh), _p(fl), _ld(fh), _p(bh), _p(bl),
                           _ld(bh))
     return bh, bl
+
+
+def dd_syr2k(uplo, trans, alpha, A, B, beta, C, n=None, k=None):
+    """Rsyr2k (DSYR2K semantics): returns C (hi, lo); only the uplo triangle
+    changes."""
+    ah, al, bh_, bl_ = _f64(A[0]), _f64(A[1]), _f64(B[0]), _f64(B[1])
+    ch, cl = _f64(C[0]).copy(order="F"), _f64(C[1]).copy(order="F")
+    t = trans.upper() in "TC"
+    n = (ah.shape[1] if t else ah.shape[0]) if n is None else n
+    k = (ah.shape[0] if t else ah.shape[1]) if k is None else k
+    lib().oracle_dd_syr2k(_ch(uplo), _ch(trans), n, k, float(alpha[0]), float(alpha[1]),
+                          _p(ah), _p(al), _ld(ah), _p(bh_), _p(bl_), _ld(bh_),
+                          float(beta[0]), float(beta[1]), _p(ch), _p(cl), _ld(ch))
+    return ch, cl
+
+
+def dd_symm(side, uplo, alpha, A, B, beta, C, m=None, n=None):
+    """Rsymm (DSYMM semantics): returns C (hi, lo)."""
+    ah, al, bh_, bl_ = _f64(A[0]), _f64(A[1]), _f64(B[0]), _f64(B[1])
+    ch, cl = _f64(C[0]).copy(order="F"), _f64(C[1]).copy(order="F")
+    m = ch.shape[0] if m is None else m
+    n = ch.shape[1] if n is None else n
+    lib().oracle_dd_symm(_ch(side), _ch(uplo), m, n, float(alpha[0]), float(alpha[1]),
+                         _p(ah), _p(al), _ld(ah), _p(bh_), _p(bl_), _ld(bh_), float(beta[0]),
+                         float(beta[1]), _p(ch), _p(cl), _ld(ch))
+    return ch, cl
 
 
 def dd_trsm(side, uplo, transa, diag, alpha, A, B, m=None, n=None):

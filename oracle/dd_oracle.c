@@ -277,6 +277,88 @@ void oracle_dd_syrk(char uplo, char trans, int64_t n, int64_t k, double alpha_hi
     }
 }
 
+/* Rsyr2k: C := alpha*(A*B^T + B*A^T) + beta*C (trans = 'N', A and B n x k) or
+ * C := alpha*(A^T*B + B^T*A) + beta*C (trans = 'T', A and B k x n); only the
+ * uplo triangle of C is referenced (DSYR2K semantics).  Each entry sums the
+ * 2k products a_il b_jl (l = 0..k-1) and then b_il a_jl in that order. */
+void oracle_dd_syr2k(char uplo, char trans, int64_t n, int64_t k, double alpha_hi,
+                     double alpha_lo, const double *ah, const double *al, int64_t lda,
+                     const double *bh, const double *bl, int64_t ldb, double beta_hi,
+                     double beta_lo, double *ch, double *cl, int64_t ldc) {
+    odd alpha = {alpha_hi, alpha_lo}, beta = {beta_hi, beta_lo};
+    int upper = (uplo == 'U' || uplo == 'u');
+    int t = is_trans(trans);
+    int alpha_zero = (alpha.hi == 0.0 && alpha.lo == 0.0);
+    int beta_zero = (beta.hi == 0.0 && beta.lo == 0.0);
+    if (n == 0) return;
+    if ((alpha_zero || k == 0) && beta.hi == 1.0 && beta.lo == 0.0) return;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t i0 = upper ? 0 : j, i1 = upper ? j + 1 : n;
+        for (int64_t i = i0; i < i1; ++i) {
+            odd acc = {0.0, 0.0};
+            if (!alpha_zero) {
+                /* row i of op(A) is A(i, :) (N) or A(:, i) (T) */
+                for (int64_t l = 0; l < k; ++l)
+                    acc = dd_add(acc, dd_mul(op_elem(ah, al, lda, t, i, l),
+                                             op_elem(bh, bl, ldb, t, j, l)));
+                for (int64_t l = 0; l < k; ++l)
+                    acc = dd_add(acc, dd_mul(op_elem(bh, bl, ldb, t, i, l),
+                                             op_elem(ah, al, lda, t, j, l)));
+                acc = dd_mul(alpha, acc);
+            }
+            if (!beta_zero)
+                acc = dd_add(acc, dd_mul(beta, (odd){ch[i + j * ldc], cl[i + j * ldc]}));
+            ch[i + j * ldc] = acc.hi;
+            cl[i + j * ldc] = acc.lo;
+        }
+    }
+}
+
+/* Rsymm: C := alpha*A*B + beta*C (side = 'L', A m x m) or alpha*B*A + beta*C
+ * (side = 'R', A n x n), A symmetric with only its uplo triangle read, B and
+ * C m x n (DSYMM semantics).  A(r, c) outside the stored triangle is read
+ * as A(c, r).  Products in the natural order of the inner index. */
+void oracle_dd_symm(char side, char uplo, int64_t m, int64_t n, double alpha_hi,
+                    double alpha_lo, const double *ah, const double *al, int64_t lda,
+                    const double *bh, const double *bl, int64_t ldb, double beta_hi,
+                    double beta_lo, double *ch, double *cl, int64_t ldc) {
+    odd alpha = {alpha_hi, alpha_lo}, beta = {beta_hi, beta_lo};
+    int left = !(side == 'R' || side == 'r');
+    int upper = (uplo == 'U' || uplo == 'u');
+    int alpha_zero = (alpha.hi == 0.0 && alpha.lo == 0.0);
+    int beta_zero = (beta.hi == 0.0 && beta.lo == 0.0);
+    if (m == 0 || n == 0) return;
+    if (alpha_zero && beta.hi == 1.0 && beta.lo == 0.0) return;
+    const int64_t k = left ? m : n;
+#define SYM(r, c) ((upper ? (r) <= (c) : (r) >= (c)) ? ((r) + (c) * lda) : ((c) + (r) * lda))
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) {
+            odd acc = {0.0, 0.0};
+            if (!alpha_zero) {
+                for (int64_t l = 0; l < k; ++l) {
+                    odd a, b;
+                    if (left) {
+                        a = (odd){ah[SYM(i, l)], al[SYM(i, l)]};
+                        b = (odd){bh[l + j * ldb], bl[l + j * ldb]};
+                    } else {
+                        a = (odd){bh[i + l * ldb], bl[i + l * ldb]};
+                        b = (odd){ah[SYM(l, j)], al[SYM(l, j)]};
+                    }
+                    acc = dd_add(acc, dd_mul(a, b));
+                }
+                acc = dd_mul(alpha, acc);
+            }
+            if (!beta_zero)
+                acc = dd_add(acc, dd_mul(beta, (odd){ch[i + j * ldc], cl[i + j * ldc]}));
+            ch[i + j * ldc] = acc.hi;
+            cl[i + j * ldc] = acc.lo;
+        }
+    }
+#undef SYM
+}
+
 /* Rpotrf: Cholesky factorisation A = U^T U (uplo = 'U') or A = L L^T
  * (uplo = 'L'), unblocked, column by column (the LAPACK dpotf2 order).
  * Returns info: 0 on success, j > 0 if the leading minor of order j is not

@@ -23,6 +23,7 @@ import oracle
 from oracle import fraction_ref as fr
 from ddcheck import EPS_DD, U, err_over_bound, gemm_bound, is_normalised
 from trsmcheck import TRSM_VARIANTS, op_triangle, trsm_residual_over_bound
+import blas3check as b3
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN = os.path.join(HERE, "golden")
@@ -466,6 +467,96 @@ def test_potrf_matches_numpy_on_well_conditioned_spd():
 
 
 # ---------------------------------------------------------------------------
+# Rsyr2k / Rsymm
+# ---------------------------------------------------------------------------
+
+def syr2k_case(seed, trans, n, k, pad=2):
+    g = datagen.rng(seed)
+    ar, ac = (n, k) if trans == "N" else (k, n)
+    A = datagen.dd_matrix(g, ar, ac, ar + pad)
+    B = datagen.dd_matrix(g, ar, ac, ar + pad)
+    C = datagen.dd_matrix(g, n, n, n + pad)
+    return A, B, C, datagen.dd_scalar(g), datagen.dd_scalar(g)
+
+
+@pytest.mark.parametrize("uplo", ["U", "L"])
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_syr2k_within_bound_of_exact_concatenated_gemm(uplo, trans):
+    n, k = 11, 9
+    A, B, C, al, be = syr2k_case(90, trans, n, k)
+    got = oracle.dd_syr2k(uplo, trans, al, A, B, be, C, n, k)
+    rows, cols = b3.triangle_entries(n, uplo)
+    ex, bound = b3.exact_and_bound(b3.syr2k_as_gemm(trans, n, k, A, B), n, n, al, be, C,
+                                   rows, cols)
+    g = (got[0][rows, cols], got[1][rows, cols])
+    assert err_over_bound(g, ex, bound) <= 1.0
+    # the other triangle and the padding are untouched
+    other = np.ones((n + 2, n), bool)
+    other[rows, cols] = False
+    assert np.array_equal(got[0][other], C[0][other], equal_nan=True)
+
+
+def test_syr2k_integer_inputs_match_binary64():
+    g = datagen.rng(91)
+    n, k = 10, 6
+    A = g.integers(-9, 10, (k, n)).astype(np.float64)
+    B = g.integers(-9, 10, (k, n)).astype(np.float64)
+    C = g.integers(-9, 10, (n, n)).astype(np.float64)
+    z = np.zeros((k, n))
+    got = oracle.dd_syr2k("L", "T", (3.0, 0.0), (A, z), (B, z), (-2.0, 0.0), (C, np.zeros((n, n))))
+    ref = 3.0 * (A.T @ B + B.T @ A) - 2.0 * C
+    rows, cols = b3.triangle_entries(n, "L")
+    assert np.array_equal(got[0][rows, cols], ref[rows, cols]) and not got[1].any()
+
+
+def test_syr2k_fraction_brute_force():
+    n, k = 4, 3
+    A, B, C, al, be = syr2k_case(92, "N", n, k, pad=0)
+    got = oracle.dd_syr2k("U", "N", al, A, B, be, C)
+    for j in range(n):
+        for i in range(j + 1):
+            v = F(*al) * sum(F(A[0][i, l], A[1][i, l]) * F(B[0][j, l], B[1][j, l]) +
+                             F(B[0][i, l], B[1][i, l]) * F(A[0][j, l], A[1][j, l])
+                             for l in range(k)) + F(*be) * F(C[0][i, j], C[1][i, j])
+            assert abs(F(got[0][i, j], got[1][i, j]) - v) <= Fraction(2) ** -100 * abs(v)
+
+
+@pytest.mark.parametrize("side", ["L", "R"])
+@pytest.mark.parametrize("uplo", ["U", "L"])
+def test_symm_within_bound_of_exact_symmetrised_gemm(side, uplo):
+    m, n = 9, 7
+    g = datagen.rng(93)
+    order = m if side == "L" else n
+    A = datagen.dd_matrix(g, order, order, order + 2)
+    r, c = np.meshgrid(np.arange(order), np.arange(order), indexing="ij")
+    unused = (r > c) if uplo == "U" else (r < c)
+    for P in A:
+        P[:order][unused] = np.nan                 # must never be read
+    B = datagen.dd_matrix(g, m, n, m + 1)
+    C = datagen.dd_matrix(g, m, n, m + 3)
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    got = oracle.dd_symm(side, uplo, al, A, B, be, C, m, n)
+    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    rows, cols = rr.ravel(), cc.ravel()
+    ex, bound = b3.exact_and_bound(b3.symm_as_gemm(side, uplo, m, n, A, B), m, n, al, be, C,
+                                   rows, cols)
+    assert err_over_bound((got[0][rows, cols], got[1][rows, cols]), ex, bound) <= 1.0
+
+
+def test_symm_integer_inputs_match_binary64():
+    g = datagen.rng(94)
+    m, n = 8, 11
+    S = g.integers(-9, 10, (n, n)).astype(np.float64)
+    S = np.triu(S) + np.triu(S, 1).T
+    B = g.integers(-9, 10, (m, n)).astype(np.float64)
+    C = g.integers(-9, 10, (m, n)).astype(np.float64)
+    stored = np.where(np.tril(np.ones((n, n))) > 0, S, np.nan)
+    got = oracle.dd_symm("R", "L", (2.0, 0.0), (stored, np.zeros((n, n))), (B, np.zeros((m, n))),
+                         (1.0, 0.0), (C, np.zeros((m, n))))
+    assert np.array_equal(got[0], 2.0 * B @ S + C) and not got[1].any()
+
+
+# ---------------------------------------------------------------------------
 # Rtrsm
 # ---------------------------------------------------------------------------
 
@@ -598,6 +689,12 @@ MUTANTS = {
                          "const int t_lower = right ? !op_upper : op_upper;"),
     "trsm_alpha_ignored": ("b = dd_mul(alpha, b);", "b = dd_add(b, (odd){0.0, 0.0});"),
     "trsm_unit_diag_read": ("if (!unit) x = dd_div(", "x = dd_div("),
+    "syr2k_second_product_sign": (
+        "acc = dd_add(acc, dd_mul(op_elem(bh, bl, ldb, t, i, l),",
+        "acc = dd_sub(acc, dd_mul(op_elem(bh, bl, ldb, t, i, l),"),
+    "symm_wrong_triangle": (
+        "#define SYM(r, c) ((upper ? (r) <= (c) : (r) >= (c))",
+        "#define SYM(r, c) ((upper ? (r) >= (c) : (r) <= (c))"),
 }
 
 
