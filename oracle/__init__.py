@@ -13,10 +13,10 @@ Contents
       manual's description of the dd format (Sec. 5: a dd is hi + lo of two
       binary64 numbers, arithmetic from Knuth's and Dekker's error-free
       transformations);
-    - scalar dd Rgemm / Rsyrk / Rsyr2k / Rsymm / Rpotrf / Rpotrs / Rtrsm:
-      plain loops with the DGEMM / DSYRK / DSYR2K / DSYMM / DPOTRF / DPOTRS /
-      DTRSM argument semantics (Sec. 7.3 maps every MPBLAS argument list onto
-      the BLAS one);
+    - scalar dd Rgemm / Rsyrk / Rsyr2k / Rsymm / Rtrsm / Rpotrf / Rpotrs /
+      Rgetrf / Rgetrs: plain loops with the argument semantics of the BLAS /
+      LAPACK routine of the same name (Sec. 7.3 maps every MPBLAS argument
+      list onto the BLAS one);
     - an exact tier: alpha*op(A)*op(B) + beta*C evaluated exactly in a
       superaccumulator and rounded once to the nearest dd.
 * ``fraction_ref.py`` -- the same definitions in pure Python ``fractions``,
@@ -33,8 +33,10 @@ side/uplo/trans/diag variants, Fraction solves of tiny systems, the
 componentwise backward-error bound of substitution evaluated by the exact
 tier, and scipy's binary64 triangular solve; Rsyr2k / Rsymm -- the exact
 tier on the equivalent Rgemm of concatenated or symmetrised operands,
-integer inputs against binary64 matmul, Fraction brute force, and the
-closed form Rsyr2k(A, A) = Rsyrk(A) with 2 alpha.
+integer inputs against binary64 matmul and Fraction brute force; Rgetrf / Rgetrs -- exact
+recovery of a dyadic L U factorisation with a known permutation, LAPACK test
+ratios with exact-tier residuals, scipy's binary64 LU (same pivots) and
+LAPACK's info on singular input.
 """
 from __future__ import annotations
 
@@ -107,6 +109,9 @@ def lib():
             L.oracle_dd_trsm.argtypes = [c, c, c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64]
             L.oracle_dd_syr2k.argtypes = [c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64, d, d,
                                           _D, _D, i64]
+            L.oracle_dd_getrf.argtypes = [i64, i64, _D, _D, i64, _I64]
+            L.oracle_dd_getrf.restype = i64
+            L.oracle_dd_getrs.argtypes = [c, i64, i64, _D, _D, i64, _I64, _D, _D, i64]
             L.oracle_dd_symm.argtypes = [c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64, d, d,
                                          _D, _D, i64]
             L.oracle_exact_sum.argtypes = [i64, _D, _D, _D]
@@ -301,6 +306,28 @@ def dd_symm(side, uplo, alpha, A, B, beta, C, m=None, n=None):
                          _p(ah), _p(al), _ld(ah), _p(bh_), _p(bl_), _ld(bh_), float(beta[0]),
                          float(beta[1]), _p(ch), _p(cl), _ld(ch))
     return ch, cl
+
+
+def dd_getrf(A, m=None, n=None):
+    """Rgetrf (DGETRF semantics): returns (hi, lo, ipiv, info); ipiv one-based."""
+    ah, al = _f64(A[0]).copy(order="F"), _f64(A[1]).copy(order="F")
+    m = ah.shape[0] if m is None else m
+    n = ah.shape[1] if n is None else n
+    ipiv = np.zeros(max(1, min(m, n)), dtype=np.int64)
+    info = lib().oracle_dd_getrf(m, n, _p(ah), _p(al), _ld(ah),
+                                 ipiv.ctypes.data_as(_I64))
+    return ah, al, ipiv[:min(m, n)], int(info)
+
+
+def dd_getrs(trans, LU, ipiv, B, n=None):
+    """Rgetrs (DGETRS semantics): X (hi, lo) with A X = B or A^T X = B."""
+    ah, al = _f64(LU[0]), _f64(LU[1])
+    bh, bl = _f64(B[0]).copy(order="F"), _f64(B[1]).copy(order="F")
+    n = ah.shape[1] if n is None else n
+    piv = np.ascontiguousarray(ipiv, dtype=np.int64)
+    lib().oracle_dd_getrs(_ch(trans), n, bh.shape[1], _p(ah), _p(al), _ld(ah),
+                          piv.ctypes.data_as(_I64), _p(bh), _p(bl), _ld(bh))
+    return bh, bl
 
 
 def dd_trsm(side, uplo, transa, diag, alpha, A, B, m=None, n=None):

@@ -493,6 +493,124 @@ void oracle_dd_trsm(char side, char uplo, char transa, char diag, int64_t m, int
     }
 }
 
+/* |a| > |b| for normalised dd values (compares hi, then lo, of the absolute
+ * values). */
+static int dd_abs_greater(odd a, odd b) {
+    if (a.hi < 0.0 || (a.hi == 0.0 && a.lo < 0.0)) a = dd_neg(a);
+    if (b.hi < 0.0 || (b.hi == 0.0 && b.lo < 0.0)) b = dd_neg(b);
+    return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+
+/* Rgetrf: LU factorisation with partial pivoting, P A = L U, of the m x n A
+ * (DGETRF semantics; MPLAPACK routine table, Sec. 6).  Unblocked, column by
+ * column (the LAPACK dgetf2 order): the pivot of column j is the first row
+ * p >= j of largest |A(p, j)|; rows j and p are interchanged across all n
+ * columns (ipiv[j] = p + 1, one-based); the entries below the diagonal are
+ * divided by the pivot (the multipliers, L's strict lower part); the
+ * trailing (m-j-1) x (n-j-1) block receives the rank-one update
+ * A(i, c) -= L(i, j) U(j, c).  A zero pivot sets info = j + 1 (the first
+ * one), skips the division and the factorisation continues.  Returns info. */
+int64_t oracle_dd_getrf(int64_t m, int64_t n, double *ah, double *al, int64_t lda,
+                        int64_t *ipiv) {
+    int64_t info = 0;
+    const int64_t mn = m < n ? m : n;
+    for (int64_t j = 0; j < mn; ++j) {
+        int64_t p = j;
+        for (int64_t i = j + 1; i < m; ++i)
+            if (dd_abs_greater((odd){ah[i + j * lda], al[i + j * lda]},
+                               (odd){ah[p + j * lda], al[p + j * lda]}))
+                p = i;
+        ipiv[j] = p + 1;
+        const odd piv = {ah[p + j * lda], al[p + j * lda]};
+        if (piv.hi == 0.0 && piv.lo == 0.0) {
+            if (info == 0) info = j + 1;
+            continue;
+        }
+        if (p != j)
+            for (int64_t c = 0; c < n; ++c) {
+                double th = ah[j + c * lda], tl = al[j + c * lda];
+                ah[j + c * lda] = ah[p + c * lda];
+                al[j + c * lda] = al[p + c * lda];
+                ah[p + c * lda] = th;
+                al[p + c * lda] = tl;
+            }
+        for (int64_t i = j + 1; i < m; ++i) {
+            odd v = dd_div((odd){ah[i + j * lda], al[i + j * lda]}, piv);
+            ah[i + j * lda] = v.hi;
+            al[i + j * lda] = v.lo;
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t c = j + 1; c < n; ++c) {
+            const odd u = {ah[j + c * lda], al[j + c * lda]};
+            for (int64_t i = j + 1; i < m; ++i) {
+                odd x = {ah[i + c * lda], al[i + c * lda]};
+                x = dd_sub(x, dd_mul((odd){ah[i + j * lda], al[i + j * lda]}, u));
+                ah[i + c * lda] = x.hi;
+                al[i + c * lda] = x.lo;
+            }
+        }
+    }
+    return info;
+}
+
+/* Rgetrs: solve A X = B (trans 'N') or A^T X = B ('T') with the factors and
+ * pivots of oracle_dd_getrf (n x n), B n x nrhs overwritten by X (DGETRS
+ * semantics).  'N': interchange B's rows as ipiv says (in order), solve
+ * L Y = B (unit diagonal) forward, then U X = Y backward.  'T': solve
+ * U^T Y = B forward, L^T Z = Y (unit) backward, then undo the interchanges
+ * in reverse order. */
+void oracle_dd_getrs(char trans, int64_t n, int64_t nrhs, const double *ah, const double *al,
+                     int64_t lda, const int64_t *ipiv, double *bh, double *bl, int64_t ldb) {
+    const int t = is_trans(trans);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < nrhs; ++q) {
+        double *xh = bh + q * ldb, *xl = bl + q * ldb;
+#define SWAPROW(a, b)                                                   \
+        do {                                                            \
+            double th = xh[a], tl = xl[a];                              \
+            xh[a] = xh[b]; xl[a] = xl[b]; xh[b] = th; xl[b] = tl;       \
+        } while (0)
+        if (!t) {
+            for (int64_t j = 0; j < n; ++j)
+                if (ipiv[j] - 1 != j) SWAPROW(j, ipiv[j] - 1);
+            for (int64_t i = 0; i < n; ++i) {          /* L y = b */
+                odd s = {xh[i], xl[i]};
+                for (int64_t c = 0; c < i; ++c)
+                    s = dd_sub(s, dd_mul((odd){ah[i + c * lda], al[i + c * lda]},
+                                         (odd){xh[c], xl[c]}));
+                xh[i] = s.hi; xl[i] = s.lo;
+            }
+            for (int64_t i = n - 1; i >= 0; --i) {     /* U x = y */
+                odd s = {xh[i], xl[i]};
+                for (int64_t c = i + 1; c < n; ++c)
+                    s = dd_sub(s, dd_mul((odd){ah[i + c * lda], al[i + c * lda]},
+                                         (odd){xh[c], xl[c]}));
+                s = dd_div(s, (odd){ah[i + i * lda], al[i + i * lda]});
+                xh[i] = s.hi; xl[i] = s.lo;
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i) {          /* U^T y = b */
+                odd s = {xh[i], xl[i]};
+                for (int64_t c = 0; c < i; ++c)
+                    s = dd_sub(s, dd_mul((odd){ah[c + i * lda], al[c + i * lda]},
+                                         (odd){xh[c], xl[c]}));
+                s = dd_div(s, (odd){ah[i + i * lda], al[i + i * lda]});
+                xh[i] = s.hi; xl[i] = s.lo;
+            }
+            for (int64_t i = n - 1; i >= 0; --i) {     /* L^T z = y */
+                odd s = {xh[i], xl[i]};
+                for (int64_t c = i + 1; c < n; ++c)
+                    s = dd_sub(s, dd_mul((odd){ah[c + i * lda], al[c + i * lda]},
+                                         (odd){xh[c], xl[c]}));
+                xh[i] = s.hi; xl[i] = s.lo;
+            }
+            for (int64_t j = n - 1; j >= 0; --j)
+                if (ipiv[j] - 1 != j) SWAPROW(j, ipiv[j] - 1);
+        }
+#undef SWAPROW
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Tier 3: exact evaluation in a fixed-point superaccumulator                 */
 /* ------------------------------------------------------------------------- */

@@ -557,6 +557,113 @@ def test_symm_integer_inputs_match_binary64():
 
 
 # ---------------------------------------------------------------------------
+# Rgetrf / Rgetrs
+# ---------------------------------------------------------------------------
+
+def dyadic_lu_case(seed, m, n):
+    """A = (rows of L U placed at rows sigma) with L unit lower, |L| <= 1/2
+    below the diagonal in quarters, U integer with a power-of-two diagonal:
+    partial pivoting must find sigma, L and U exactly.  Returns A, L, U and
+    the expected one-based ipiv."""
+    g = datagen.rng(seed)
+    mn = min(m, n)
+    L = np.tril(g.choice([-0.5, -0.25, 0.0, 0.25, 0.5], (m, mn)), -1)
+    L[np.arange(mn), np.arange(mn)] = 1.0
+    U = np.triu(g.integers(-5, 6, (mn, n)).astype(np.float64))
+    U[np.arange(mn), np.arange(mn)] = g.choice([-4.0, -2.0, -1.0, 1.0, 2.0, 4.0], mn)
+    sigma = g.permutation(m)
+    A = np.zeros((m, n))
+    A[sigma, :] = L @ U
+    cur = list(range(m))
+    ipiv = []
+    for j in range(mn):
+        p = cur.index(sigma[j])
+        ipiv.append(p + 1)
+        cur[j], cur[p] = cur[p], cur[j]
+    # P A = L' U with L' the rows of L in the final order of A's rows
+    inv = np.argsort(sigma)
+    return np.asfortranarray(A), L[inv[cur]], U, np.array(ipiv)
+
+
+def apply_ipiv(X, ipiv):
+    """Rows of X interchanged as ipiv says (in order): P X."""
+    X = X.copy()
+    for j, p in enumerate(ipiv):
+        X[[j, p - 1]] = X[[p - 1, j]]
+    return X
+
+
+@pytest.mark.parametrize("m,n", [(12, 12), (15, 9), (8, 13)])
+def test_getrf_recovers_dyadic_factorisation(m, n):
+    A, L, U, ipiv = dyadic_lu_case(100 + m, m, n)
+    lh, ll, piv, info = oracle.dd_getrf((A, np.zeros_like(A)))
+    assert info == 0 and np.array_equal(piv, ipiv) and not ll.any()
+    mn = min(m, n)
+    assert np.array_equal(np.tril(lh[:, :mn], -1), np.tril(L, -1))
+    assert np.array_equal(np.triu(lh[:mn, :]), U)
+
+
+def lu_residual_ratio(A, LU, ipiv, m, n):
+    """||P A - L U||_1 / (n ||A||_1 eps_dd), the product evaluated exactly."""
+    mn = min(m, n)
+    L = [np.tril(P[:, :mn], -1) for P in LU]
+    L[0][np.arange(mn), np.arange(mn)] = 1.0
+    U = [np.triu(P[:mn, :]) for P in LU]
+    PA = tuple(np.asfortranarray(apply_ipiv(P, ipiv)) for P in A)
+    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    R = oracle.exact_gemm_entries("N", "N", mn, (1.0, 0.0), tuple(np.asfortranarray(x) for x in L),
+                                  tuple(np.asfortranarray(x) for x in U), (-1.0, 0.0), PA,
+                                  rr.ravel(), cc.ravel())
+    Rn = np.abs(R[0].reshape(m, n)).sum(axis=0).max()
+    return Rn / (n * np.abs(A[0]).sum(axis=0).max() * EPS_DD)
+
+
+@pytest.mark.parametrize("m,n", [(40, 40), (47, 31), (29, 44)])
+def test_getrf_lapack_ratio(m, n):
+    g = datagen.rng(110 + m)
+    A = datagen.dd_matrix(g, m, n)
+    lh, ll, piv, info = oracle.dd_getrf(A)
+    assert info == 0
+    assert lu_residual_ratio(A, (lh, ll), piv, m, n) < 30
+
+
+def test_getrf_matches_scipy_on_binary64_input():
+    sla = pytest.importorskip("scipy.linalg")
+    g = datagen.rng(120)
+    A = g.standard_normal((30, 30))
+    lh, _, piv, info = oracle.dd_getrf((np.asfortranarray(A), np.zeros((30, 30), order="F")))
+    lu, p = sla.lu_factor(A)
+    assert info == 0 and np.array_equal(piv, p + 1)
+    assert np.abs(lh - lu).max() <= 1e-12 * np.abs(lu).max()
+
+
+def test_getrf_info_on_singular_input():
+    A = np.array([[1.0, 2.0, 0.0, 3.0], [2.0, 1.0, 0.0, 1.0], [0.0, 1.0, 0.0, 5.0],
+                  [1.0, 1.0, 0.0, 2.0]])
+    z = np.zeros_like(A)
+    assert oracle.dd_getrf((np.asfortranarray(A), z))[3] == 3
+    B = np.array([[1.0, 2.0], [1.0, 2.0]])
+    assert oracle.dd_getrf((np.asfortranarray(B), np.zeros((2, 2))))[3] == 2
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_getrs_lapack_ratio(trans):
+    n = 36
+    g = datagen.rng(130)
+    A = datagen.dd_matrix(g, n, n)
+    B = datagen.dd_matrix(g, n, 4)
+    lh, ll, piv, info = oracle.dd_getrf(A)
+    X = oracle.dd_getrs(trans, (lh, ll), piv, B)
+    rr, cc = np.meshgrid(np.arange(n), np.arange(4), indexing="ij")
+    R = oracle.exact_gemm_entries(trans, "N", n, (-1.0, 0.0), A, X, (1.0, 0.0), B, rr.ravel(),
+                                  cc.ravel())
+    An = np.abs(A[0]).sum(axis=0).max()
+    Xn = np.abs(X[0]).sum(axis=0).max()
+    ratio = np.abs(R[0]).reshape(n, 4).sum(axis=0).max() / (An * Xn * EPS_DD)
+    assert ratio < 30
+
+
+# ---------------------------------------------------------------------------
 # Rtrsm
 # ---------------------------------------------------------------------------
 
@@ -692,6 +799,12 @@ MUTANTS = {
     "syr2k_second_product_sign": (
         "acc = dd_add(acc, dd_mul(op_elem(bh, bl, ldb, t, i, l),",
         "acc = dd_sub(acc, dd_mul(op_elem(bh, bl, ldb, t, i, l),"),
+    "getrf_wrong_pivot": ("            if (dd_abs_greater((odd){ah[i + j * lda], al[i + j * lda]},",
+                          "            if (!dd_abs_greater((odd){ah[i + j * lda], al[i + j * lda]},"),
+    "getrf_left_columns_not_swapped": ("        if (p != j)\n            for (int64_t c = 0; c < n; ++c) {",
+                                       "        if (p != j)\n            for (int64_t c = j; c < n; ++c) {"),
+    "getrs_no_unpivot": ("            for (int64_t j = n - 1; j >= 0; --j)\n                if (ipiv[j] - 1 != j) SWAPROW(j, ipiv[j] - 1);",
+                         ""),
     "symm_wrong_triangle": (
         "#define SYM(r, c) ((upper ? (r) <= (c) : (r) >= (c))",
         "#define SYM(r, c) ((upper ? (r) >= (c) : (r) <= (c))"),
