@@ -130,7 +130,39 @@ int mp_dd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, in
 int mp_dd_Rsyrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
                 mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc);
 
-/* Host-buffer forms of the two calls above, as the manual's CUDA MPBLAS is
+/* Rsyr2k (MPBLAS routine table, Sec. 6; DSYR2K semantics):
+ *
+ *     C := alpha (A B^T + B A^T) + beta C   (trans N, A and B n x k), or
+ *     C := alpha (A^T B + B^T A) + beta C   (trans T/C, A and B k x n),
+ *
+ * updating only the uplo triangle of the n x n C.  Each entry accumulates
+ * the k products of the first term and then the k of the second in one dd
+ * accumulator (the plain kernel's multiply-add), then applies alpha and
+ * beta once.  Accuracy: |C - C_exact| <= 4 (2k) 2^-104 (|alpha| (|A||B^T| +
+ * |B||A^T|) + |beta||C|) componentwise (trans N; transposed for T).
+ * Quick return and beta = 0 as mp_dd_Rsyrk.  Errors: -1 uplo, -2 trans,
+ * -3 n < 0, -4 k < 0, -6 A NULL, -7 lda < max(1, n (N) or k (T)), -8 B NULL,
+ * -9 ldb < max(1, n (N) or k (T)), -11 C NULL, -12 ldc < max(1, n)
+ * (DSYR2K's numbering). */
+int mp_dd_Rsyr2k(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                 mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
+                 mp_dd_mat C, int64_t ldc);
+
+/* Rsymm (MPBLAS routine table, Sec. 6; DSYMM semantics):
+ *
+ *     C := alpha A B + beta C   (side L, A m x m), or
+ *     C := alpha B A + beta C   (side R, A n x n),
+ *
+ * A symmetric with only its uplo triangle read (A(i, l) outside it is read
+ * as A(l, i)), B and C m x n.  Arithmetic, accuracy (k = order of A) and
+ * beta / alpha semantics as mp_dd_Rgemm.  Errors: -1 side, -2 uplo,
+ * -3 m < 0, -4 n < 0, -6 A NULL, -7 lda < max(1, order of A), -8 B NULL,
+ * -9 ldb < max(1, m), -11 C NULL, -12 ldc < max(1, m) (DSYMM's numbering). */
+int mp_dd_Rsymm(const char *side, const char *uplo, int64_t m, int64_t n, mp_dd alpha,
+                mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta, mp_dd_mat C,
+                int64_t ldc);
+
+/* Host-buffer forms of mp_dd_Rgemm and mp_dd_Rsyrk, as the manual's CUDA MPBLAS is
  * used (Sec. 7.3: the caller passes host arrays; the library moves them to
  * the GPU and back -- the "with host-GPU transfer" figures of Sec. 10).
  * All matrix pointers are HOST memory (pinned memory gives the fastest
@@ -167,6 +199,34 @@ int mp_dd_Rsyrk_host(const char *uplo, const char *trans, int64_t n, int64_t k, 
 int mp_dd_Rtrsm(const char *side, const char *uplo, const char *transa, const char *diag,
                 int64_t m, int64_t n, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_mat B,
                 int64_t ldb);
+
+/* ------------------------------------------------------------------------ */
+/* MPLAPACK: dd LU factorisation and solve                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Rgetrf (MPLAPACK routine table, Sec. 6; DGETRF semantics): P A = L U with
+ * partial pivoting of the m x n A; L (unit lower, not stored diagonal) and
+ * U overwrite A.  ipiv (DEVICE int64[min(m, n)]) receives the one-based row
+ * interchanged with row j at step j.  The pivot of a column is the first row
+ * of largest dd magnitude.  *info (DEVICE int64, required) receives 0 or
+ * j > 0 when U(j, j) is exactly zero (the factorisation completes, as in
+ * LAPACK).  Recursive column splitting (LAPACK's dgetrf2): the updates are
+ * dd Rtrsm and dd Rgemm products, the single-column leaves one CTA each.
+ * Accuracy: the backward error of Gaussian elimination in dd arithmetic
+ * (LAPACK test ratio ||P A - L U|| / (n ||A|| 2^-104) < 30).  Asynchronous.
+ * Errors: -1 m < 0, -2 n < 0, -3 A NULL, -4 lda < max(1, m), -5 ipiv NULL,
+ * -6 info NULL. */
+int mp_dd_Rgetrf(int64_t m, int64_t n, mp_dd_mat A, int64_t lda, int64_t *ipiv,
+                 int64_t *info);
+
+/* Rgetrs (DGETRS semantics): solve A X = B (trans 'N') or A^T X = B ('T';
+ * 'C' is 'T') with the factors and ipiv (device) of mp_dd_Rgetrf on the
+ * n x n A; B (n x nrhs) is overwritten by X.  Row interchanges, then unit
+ * lower and upper dd Rtrsm (reverse order for 'T').  Asynchronous.
+ * Errors: -1 trans, -2 n < 0, -3 nrhs < 0, -4 A NULL, -5 lda < max(1, n),
+ * -6 ipiv NULL, -7 B NULL, -8 ldb < max(1, n). */
+int mp_dd_Rgetrs(const char *trans, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_t lda,
+                 const int64_t *ipiv, mp_dd_mat B, int64_t ldb);
 
 /* ------------------------------------------------------------------------ */
 /* MPLAPACK: dd Cholesky factorisation and solve                             */

@@ -27,7 +27,8 @@ __all__ = [
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
-    "mp_dd_Rtrsm", "mp_dd_Rpotrf", "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
+    "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf",
+    "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
     "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
 
@@ -237,6 +238,32 @@ def mp_dd_Rpotrf(uplo, n, A, lda, info, check=True):
     _sync_stream()
     rc = _LIB.mp_dd_Rpotrf(_flag(uplo), n, _m(A), lda, _ptr(info))
     return _check(rc, "mp_dd_Rpotrf") if check else rc
+
+
+def mp_dd_Rgetrf(m, n, A, lda, ipiv, info, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgetrf(m, n, _m(A), lda, _ptr(ipiv), _ptr(info))
+    return _check(rc, "mp_dd_Rgetrf") if check else rc
+
+
+def mp_dd_Rgetrs(trans, n, nrhs, A, lda, ipiv, B, ldb, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rgetrs(_flag(trans), n, nrhs, _cm(A), lda, _ptr(ipiv), _m(B), ldb)
+    return _check(rc, "mp_dd_Rgetrs") if check else rc
+
+
+def mp_dd_Rsyr2k(uplo, trans, n, k, alpha, A, lda, B, ldb, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rsyr2k(_flag(uplo), _flag(trans), n, k, _dd(alpha), _cm(A), lda, _cm(B),
+                           ldb, _dd(beta), _m(C), ldc)
+    return _check(rc, "mp_dd_Rsyr2k") if check else rc
+
+
+def mp_dd_Rsymm(side, uplo, m, n, alpha, A, lda, B, ldb, beta, C, ldc, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rsymm(_flag(side), _flag(uplo), m, n, _dd(alpha), _cm(A), lda, _cm(B), ldb,
+                          _dd(beta), _m(C), ldc)
+    return _check(rc, "mp_dd_Rsymm") if check else rc
 
 
 def mp_dd_Rtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, check=True):

@@ -96,6 +96,12 @@ SIGNATURES = {
     "mp_dd_potrf_diag_batch": (_int, [_i64, _vp]),
     "mp_dd_trsm_batch": (_int, [_i64, _vp, _i64]),
     "mp_dd_Rtrsm": (_int, [_c, _c, _c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDMat, _i64]),
+    "mp_dd_Rgetrf": (_int, [_i64, _i64, MpDDMat, _i64, _vp, _vp]),
+    "mp_dd_Rgetrs": (_int, [_c, _i64, _i64, MpDDCMat, _i64, _vp, MpDDMat, _i64]),
+    "mp_dd_Rsyr2k": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64, MpDD,
+                            MpDDMat, _i64]),
+    "mp_dd_Rsymm": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64, MpDD,
+                           MpDDMat, _i64]),
     "mp_dd_Rgemm_grouped_workspace": (_sz, [_i64, ctypes.POINTER(MpDDGemmDesc)]),
     "mp_dd_Rgemm_grouped_prepare": (_int, [_i64, ctypes.POINTER(MpDDGemmDesc), _vp, _sz]),
     "mp_dd_Rgemm_grouped_run": (_int, [_vp]),

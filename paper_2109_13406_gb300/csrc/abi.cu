@@ -252,6 +252,82 @@ int mp_dd_Rsyrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd
     return launch_gemm_plain(p, tls().stream);
 }
 
+int mp_dd_Rsyr2k(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                 mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
+                 mp_dd_mat C, int64_t ldc) {
+    clear_error();
+    const int ul = uplo_flag(uplo), t = trans_flag(trans);
+    if (ul < 0) return fail(-1, "Rsyr2k: illegal uplo");
+    if (t < 0) return fail(-2, "Rsyr2k: illegal trans");
+    if (n < 0) return fail(-3, "Rsyr2k: n < 0");
+    if (k < 0) return fail(-4, "Rsyr2k: k < 0");
+    const int64_t nrow = t ? k : n;
+    const bool need_ab = n > 0 && k > 0 && !dd_is_zero(alpha);
+    if (need_ab && (A.hi == nullptr || A.lo == nullptr)) return fail(-6, "Rsyr2k: A is NULL");
+    if (lda < imax(1, nrow)) return fail(-7, "Rsyr2k: lda < max(1, %lld)", (long long)nrow);
+    if (need_ab && (B.hi == nullptr || B.lo == nullptr)) return fail(-8, "Rsyr2k: B is NULL");
+    if (ldb < imax(1, nrow)) return fail(-9, "Rsyr2k: ldb < max(1, %lld)", (long long)nrow);
+    if (n > 0 && (C.hi == nullptr || C.lo == nullptr)) return fail(-11, "Rsyr2k: C is NULL");
+    if (ldc < imax(1, n)) return fail(-12, "Rsyr2k: ldc < max(1, n)");
+    GemmArgs p{};
+    p.m = n; p.n = n; p.k = k;
+    p.alpha = alpha; p.beta = beta;
+    // entry (i, j): row i of op(A) times row j of op(B), then B with A
+    p.ah = A.hi; p.al = A.lo; p.lda = lda;
+    p.bh = B.hi; p.bl = B.lo; p.ldb = ldb;
+    p.a2h = B.hi; p.a2l = B.lo; p.lda2 = ldb;
+    p.b2h = A.hi; p.b2l = A.lo; p.ldb2 = lda;
+    p.ch = C.hi; p.cl = C.lo; p.ldc = ldc;
+    p.ta = t; p.tb = 1 - t; p.tri = ul;
+    p.alpha_zero = dd_is_zero(alpha) || k == 0;
+    p.alpha_one = dd_is_one(alpha);
+    p.beta_zero = dd_is_zero(beta);
+    if (quick_return(p)) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    return launch_gemm_plain(p, tls().stream);
+}
+
+int mp_dd_Rsymm(const char *side, const char *uplo, int64_t m, int64_t n, mp_dd alpha,
+                mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta, mp_dd_mat C,
+                int64_t ldc) {
+    clear_error();
+    const int right = flag_is(side, 'R') ? 1 : flag_is(side, 'L') ? 0 : -1;
+    if (right < 0) return fail(-1, "Rsymm: illegal side");
+    const int ul = uplo_flag(uplo);
+    if (ul < 0) return fail(-2, "Rsymm: illegal uplo");
+    if (m < 0) return fail(-3, "Rsymm: m < 0");
+    if (n < 0) return fail(-4, "Rsymm: n < 0");
+    const int64_t order = right ? n : m;
+    const bool need_ab = m > 0 && n > 0 && !dd_is_zero(alpha);
+    if (need_ab && (A.hi == nullptr || A.lo == nullptr)) return fail(-6, "Rsymm: A is NULL");
+    if (lda < imax(1, order)) return fail(-7, "Rsymm: lda < max(1, order of A)");
+    if (need_ab && (B.hi == nullptr || B.lo == nullptr)) return fail(-8, "Rsymm: B is NULL");
+    if (ldb < imax(1, m)) return fail(-9, "Rsymm: ldb < max(1, m)");
+    if (m > 0 && n > 0 && (C.hi == nullptr || C.lo == nullptr))
+        return fail(-11, "Rsymm: C is NULL");
+    if (ldc < imax(1, m)) return fail(-12, "Rsymm: ldc < max(1, m)");
+    GemmArgs p{};
+    p.m = m; p.n = n; p.k = order;
+    p.alpha = alpha; p.beta = beta;
+    if (!right) {
+        p.ah = A.hi; p.al = A.lo; p.lda = lda; p.sym_a = ul;
+        p.bh = B.hi; p.bl = B.lo; p.ldb = ldb;
+    } else {
+        p.ah = B.hi; p.al = B.lo; p.lda = ldb;
+        p.bh = A.hi; p.bl = A.lo; p.ldb = lda; p.sym_b = ul;
+    }
+    p.ch = C.hi; p.cl = C.lo; p.ldc = ldc;
+    p.ta = 0; p.tb = 0; p.tri = 0;
+    p.alpha_zero = dd_is_zero(alpha) || order == 0;
+    p.alpha_one = dd_is_one(alpha);
+    p.beta_zero = dd_is_zero(beta);
+    if (quick_return(p)) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    return launch_gemm_plain(p, tls().stream);
+}
+
 int mp_dd_Rgemm_host(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
                      mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
                      mp_dd beta, mp_dd_mat C, int64_t ldc) {
@@ -425,6 +501,45 @@ int mp_dd_Rtrsm(const char *side, const char *uplo, const char *transa, const ch
     }
     return run_trsm(right, ul == 2, ta, unit, m, n, alpha, A.hi, A.lo, lda, B.hi, B.lo, ldb,
                     st);
+}
+
+int mp_dd_Rgetrf(int64_t m, int64_t n, mp_dd_mat A, int64_t lda, int64_t *ipiv,
+                 int64_t *info) {
+    clear_error();
+    if (m < 0) return fail(-1, "Rgetrf: m < 0");
+    if (n < 0) return fail(-2, "Rgetrf: n < 0");
+    if (m > 0 && n > 0 && (A.hi == nullptr || A.lo == nullptr))
+        return fail(-3, "Rgetrf: A is NULL");
+    if (lda < imax(1, m)) return fail(-4, "Rgetrf: lda < max(1, m)");
+    if (m > 0 && n > 0 && ipiv == nullptr) return fail(-5, "Rgetrf: ipiv is NULL");
+    if (info == nullptr) return fail(-6, "Rgetrf: info is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    cudaStream_t st = tls().stream;
+    if (m == 0 || n == 0) {
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), st);
+        return e == cudaSuccess ? 0 : cuda_fail(e, "info reset");
+    }
+    return run_getrf(m, n, A.hi, A.lo, lda, ipiv, info, st);
+}
+
+int mp_dd_Rgetrs(const char *trans, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_t lda,
+                 const int64_t *ipiv, mp_dd_mat B, int64_t ldb) {
+    clear_error();
+    const int t = trans_flag(trans);
+    if (t < 0) return fail(-1, "Rgetrs: illegal trans");
+    if (n < 0) return fail(-2, "Rgetrs: n < 0");
+    if (nrhs < 0) return fail(-3, "Rgetrs: nrhs < 0");
+    const bool work = n > 0 && nrhs > 0;
+    if (work && (A.hi == nullptr || A.lo == nullptr)) return fail(-4, "Rgetrs: A is NULL");
+    if (lda < imax(1, n)) return fail(-5, "Rgetrs: lda < max(1, n)");
+    if (work && ipiv == nullptr) return fail(-6, "Rgetrs: ipiv is NULL");
+    if (work && (B.hi == nullptr || B.lo == nullptr)) return fail(-7, "Rgetrs: B is NULL");
+    if (ldb < imax(1, n)) return fail(-8, "Rgetrs: ldb < max(1, n)");
+    if (!work) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    return run_getrs(t, n, nrhs, A.hi, A.lo, lda, ipiv, B.hi, B.lo, ldb, tls().stream);
 }
 
 int mp_dd_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *descs) {

@@ -1,19 +1,25 @@
 // Plain double-double Rgemm / Rsyrk kernel for sm_103a (FP64 DFMA path).
 //
-// Computes C := alpha op(A) op(B) + beta C (Rgemm) or one triangle of
-// alpha A A^T + beta C (Rsyrk), MPBLAS semantics (manual Sec. 7.3 and the
-// routine table of Sec. 6).  Every multiply-add is dd arithmetic: the exact
-// product of the hi parts by FMA, the two cross products, TwoSum into the
-// accumulator, and a FastTwoSum renormalisation every 4 steps of k
-// (dd_arith.cuh).
+// Computes C := alpha op(A) op(B) + beta C (Rgemm), one triangle of
+// alpha A A^T + beta C (Rsyrk) or of alpha (A B^T + B A^T) + beta C (Rsyr2k:
+// the second product continues the same k loop), and alpha S B + beta C or
+// alpha B S + beta C with S symmetric and one triangle stored (Rsymm: the
+// operand is read through the stored triangle); MPBLAS semantics (manual
+// Sec. 7.3 and the routine table of Sec. 6).  Every multiply-add is dd
+// arithmetic: the exact product of the hi parts by FMA, the two cross
+// products, TwoSum into the accumulator, and a FastTwoSum renormalisation
+// every 4 steps of k (dd_arith.cuh).
 //
 // On GB300 the FP64 pipe is the bottleneck by a wide margin (12.75 FP64
 // instructions per dd multiply-add), so the kernel is organised to keep that
-// pipe busy and nothing else: each CTA owns a 64 x 64 tile of C, each thread
-// a 4 x 4 block of dd accumulators (16 independent dependency chains), and
-// the hi/lo planes of the op(A) and op(B) panels are staged through shared
-// memory 16 columns of k at a time with a register prefetch of the next
-// panel.  Loads are zero-filled outside the matrices; a zero product leaves
+// pipe busy and nothing else: each CTA owns a 16R x 16R tile of C (R = 4, 2
+// or 1), each thread an R x R block of dd accumulators, and the hi/lo planes
+// of the op(A) and op(B) panels are staged through shared memory 16 columns
+// of k at a time with a register prefetch of the next panel.  One SM's FP64
+// pipe issues only 2 lanes per clock, so a few warps keep it busy whatever R
+// is; the launch picks R so that the tiles fill all SMs (large products:
+// 64 x 64, the fewest operand loads per multiply-add; thin ones: smaller
+// tiles, more CTAs).  Loads are zero-filled outside the matrices; a zero product leaves
 // a normalised accumulator bitwise unchanged, so the per-entry operation
 // sequence (l = 0, 1, ..., k-1) and hence the result are independent of the
 // tiling.  Rsyrk uses the same instantiation as Rgemm(N, T) / (T, N) over
@@ -25,11 +31,13 @@
 namespace mpdd {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 
+template <int R>
 struct PlainSmem {
-    double ah[BK][BM + 1], al[BK][BM + 1];  // op(A) panel, [l][i]
-    double bh[BK][BN + 1], bl[BK][BN + 1];  // op(B) panel, [l][j]
+    static constexpr int B = 16 * R;
+    double ah[BK][B + 1], al[BK][B + 1];  // op(A) panel, [l][i]
+    double bh[BK][B + 1], bl[BK][B + 1];  // op(B) panel, [l][j]
 };
 
 constexpr int GROUP_N = 8;  // tile columns per rasterisation group
@@ -40,6 +48,7 @@ constexpr int GROUP_N = 8;  // tile columns per rasterisation group
 // (a plain column-by-column order re-reads all of A for every tile column).
 // Rsyrk: a 1-D grid over the tiles of one triangle, t -> (row, col) with
 // row <= col (upper) or row >= col (lower).
+template <int BM, int BN>
 __device__ __forceinline__ void tile_coords(const GemmArgs &p, int64_t &bi, int64_t &bj) {
     if (p.tri == 0) {
         const int64_t tm = (p.m + BM - 1) / BM, tn = (p.n + BN - 1) / BN;
@@ -66,23 +75,27 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &p, int64_t &bi, int6
     }
 }
 
-template <int TA, int TB>
-__global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
-    __shared__ PlainSmem s;
+template <int TA, int TB, int R>
+__device__ __forceinline__ void plain_body(const GemmArgs &p, PlainSmem<R> &s) {
+    constexpr int BM = 16 * R, BN = 16 * R;
     if (p.info != nullptr && *p.info != 0) return;  // an earlier step failed
     int64_t bi, bj;
-    tile_coords(p, bi, bj);
+    tile_coords<BM, BN>(p, bi, bj);
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
     const int64_t i0 = bi * BM, j0 = bj * BN;
-    const int64_t kk = p.alpha_zero ? 0 : p.k;
+    // the k loop: [0, k) over (A, B), then for Rsyr2k [k1, k1 + k) over
+    // (A2, B2), k1 = k rounded up to whole panels (zero products between)
+    const int64_t k1 = (p.k + BK - 1) / BK * BK;
+    const int64_t kk = p.alpha_zero ? 0 : (p.a2h != nullptr ? k1 + p.k : p.k);
 
-    dd acc[4][4];
+    dd acc[R][R];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = dd{0.0, 0.0};
+        for (int c = 0; c < R; ++c) acc[r][c] = dd{0.0, 0.0};
 
-    double rah[4], ral[4], rbh[4], rbl[4];
+    // a panel holds 16R x 16 entries of op(A) and of op(B): R per thread
+    double rah[R], ral[R], rbh[R], rbl[R];
     // Element q of this thread's share of a panel: (row-in-panel, l).
     auto a_pos = [&](int q, int &ii, int &ll) {
         int idx = t + NT * q;
@@ -95,28 +108,41 @@ __global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
         else     { jj = idx % BN; ll = idx / BN; }   // contiguous in j
     };
     auto load = [&](int64_t l0) {
+        const bool second = p.a2h != nullptr && l0 >= k1;
+        const double *Ah = second ? p.a2h : p.ah, *Al = second ? p.a2l : p.al;
+        const double *Bh = second ? p.b2h : p.bh, *Bl = second ? p.b2l : p.bl;
+        const int64_t lda = second ? p.lda2 : p.lda, ldb = second ? p.ldb2 : p.ldb;
+        const int64_t lb = second ? l0 - k1 : l0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             int ii, ll;
             a_pos(q, ii, ll);
-            int64_t gi = i0 + ii, gl = l0 + ll;
-            bool ok = gi < p.m && gl < kk;
-            int64_t off = TA ? (gl + gi * p.lda) : (gi + gl * p.lda);
-            rah[q] = ok ? p.ah[off] : 0.0;
-            ral[q] = ok ? p.al[off] : 0.0;
+            int64_t gi = i0 + ii, gl = lb + ll;
+            bool ok = gi < p.m && gl < p.k;
+            int64_t off = TA ? (gl + gi * lda) : (gi + gl * lda);
+            if (p.sym_a) {
+                const bool direct = p.sym_a == 1 ? gi <= gl : gi >= gl;
+                off = direct ? gi + gl * lda : gl + gi * lda;
+            }
+            rah[q] = ok ? Ah[off] : 0.0;
+            ral[q] = ok ? Al[off] : 0.0;
             int jj;
             b_pos(q, jj, ll);
             int64_t gj = j0 + jj;
-            gl = l0 + ll;
-            ok = gj < p.n && gl < kk;
-            off = TB ? (gj + gl * p.ldb) : (gl + gj * p.ldb);
-            rbh[q] = ok ? p.bh[off] : 0.0;
-            rbl[q] = ok ? p.bl[off] : 0.0;
+            gl = lb + ll;
+            ok = gj < p.n && gl < p.k;
+            off = TB ? (gj + gl * ldb) : (gl + gj * ldb);
+            if (p.sym_b) {
+                const bool direct = p.sym_b == 1 ? gl <= gj : gl >= gj;
+                off = direct ? gl + gj * ldb : gj + gl * ldb;
+            }
+            rbh[q] = ok ? Bh[off] : 0.0;
+            rbl[q] = ok ? Bl[off] : 0.0;
         }
     };
     auto stage = [&]() {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < R; ++q) {
             int ii, jj, ll;
             a_pos(q, ii, ll);
             s.ah[ll][ii] = rah[q];
@@ -138,31 +164,31 @@ __global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
             for (int l4 = 0; l4 < BK; l4 += kRenormEvery) {
 #pragma unroll
                 for (int l = l4; l < l4 + kRenormEvery; ++l) {
-                    dd a[4], b[4];
+                    dd a[R], b[R];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < R; ++r)
                         a[r] = dd{s.ah[l][tx + 16 * r], s.al[l][tx + 16 * r]};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
+                    for (int c = 0; c < R; ++c)
                         b[c] = dd{s.bh[l][ty + 16 * c], s.bl[l][ty + 16 * c]};
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < R; ++r)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) mac_deferred(acc[r][c], a[r], b[c]);
+                        for (int c = 0; c < R; ++c) mac_deferred(acc[r][c], a[r], b[c]);
                 }
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < R; ++r)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) renorm(acc[r][c]);
+                    for (int c = 0; c < R; ++c) renorm(acc[r][c]);
             }
         }
     }
 
     const dd alpha{p.alpha.hi, p.alpha.lo}, beta{p.beta.hi, p.beta.lo};
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < R; ++c) {
             int64_t i = i0 + tx + 16 * r, j = j0 + ty + 16 * c;
             if (i >= p.m || j >= p.n) continue;
             if ((p.tri == 1 && i > j) || (p.tri == 2 && i < j)) continue;
@@ -174,25 +200,72 @@ __global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
         }
 }
 
+// 64 x 64 tiles (one CTA per SM by registers) and the smaller tiles (two or
+// more CTAs per SM, registers capped accordingly).
+template <int TA, int TB>
+__global__ void __launch_bounds__(NT) dd_gemm_plain_kernel(const GemmArgs p) {
+    __shared__ PlainSmem<4> s;
+    plain_body<TA, TB, 4>(p, s);
+}
+
+template <int TA, int TB, int R>
+__global__ void __launch_bounds__(NT, 2) dd_gemm_plain_small_kernel(const GemmArgs p) {
+    __shared__ PlainSmem<R> s;
+    plain_body<TA, TB, R>(p, s);
+}
+
 }  // namespace
 
-int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream) {
-    dim3 block(NT);
-    dim3 grid;
-    int64_t tm = ceil_div(p.m, BM), tn = ceil_div(p.n, BN);
-    if (p.tri == 0) {
-        if (tm * tn > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "m x n too large");
-        grid = dim3((unsigned)(tm * tn));
-    } else {
-        int64_t tiles = tm * (tm + 1) / 2;
-        if (tiles > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "n too large");
-        grid = dim3((unsigned)tiles);
-    }
-    if (p.ta == 0 && p.tb == 0) dd_gemm_plain_kernel<0, 0><<<grid, block, 0, stream>>>(p);
-    else if (p.ta == 1 && p.tb == 0) dd_gemm_plain_kernel<1, 0><<<grid, block, 0, stream>>>(p);
-    else if (p.ta == 0 && p.tb == 1) dd_gemm_plain_kernel<0, 1><<<grid, block, 0, stream>>>(p);
-    else dd_gemm_plain_kernel<1, 1><<<grid, block, 0, stream>>>(p);
+namespace {
+
+int64_t tile_count(const GemmArgs &p, int b) {
+    const int64_t tm = ceil_div(p.m, b), tn = ceil_div(p.n, b);
+    return p.tri == 0 ? tm * tn : tm * (tm + 1) / 2;
+}
+
+template <int TA, int TB, int R>
+void launch_one(dim3 grid, const GemmArgs &p, cudaStream_t stream) {
+    if constexpr (R == 4)
+        dd_gemm_plain_kernel<TA, TB><<<grid, NT, 0, stream>>>(p);
+    else
+        dd_gemm_plain_small_kernel<TA, TB, R><<<grid, NT, 0, stream>>>(p);
+}
+
+template <int R>
+int launch_r(const GemmArgs &p, cudaStream_t stream) {
+    const int64_t tiles = tile_count(p, 16 * R);
+    if (tiles > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "m x n too large");
+    const dim3 grid((unsigned)tiles);
+    if (p.ta == 0 && p.tb == 0) launch_one<0, 0, R>(grid, p, stream);
+    else if (p.ta == 1 && p.tb == 0) launch_one<1, 0, R>(grid, p, stream);
+    else if (p.ta == 0 && p.tb == 1) launch_one<0, 1, R>(grid, p, stream);
+    else launch_one<1, 1, R>(grid, p, stream);
     return check_launch("dd_gemm_plain_kernel");
+}
+
+}  // namespace
+
+// Tile size: the time of a launch is about (tiles per SM, rounded up) x
+// (work per tile), i.e. ceil(tiles_R / SMs) R^2 in units of a 16 x 16 tile;
+// the largest R with the least such time wins (the per-entry operation
+// sequence, and hence the result, does not depend on R).
+int plain_tile_r(const GemmArgs &p) {
+    const int64_t sms = sm_count() > 0 ? sm_count() : 152;
+    int best = 4;
+    int64_t best_t = -1;
+    for (int r = 4; r >= 1; r /= 2) {
+        const int64_t t = ceil_div(tile_count(p, 16 * r), sms) * r * r;
+        if (best_t < 0 || t < best_t) { best_t = t; best = r; }
+    }
+    return best;
+}
+
+int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream) {
+    switch (plain_tile_r(p)) {
+        case 1: return launch_r<1>(p, stream);
+        case 2: return launch_r<2>(p, stream);
+        default: return launch_r<4>(p, stream);
+    }
 }
 
 }  // namespace mpdd

@@ -461,4 +461,246 @@ int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp
     return trsm_rec(P, 0, right ? n : m, true);
 }
 
+// ------------------------------------------------------------------ Rgetrf
+//
+// LU factorisation with partial pivoting, P A = L U (DGETRF semantics), by
+// the recursive column splitting of LAPACK's dgetrf2: factor the left half
+// of the columns (recursively), solve L11 U12 = A12 (the Rtrsm above, unit
+// lower), update A22 -= L21 U12 (the plain dd Rgemm kernel, or a
+// one-thread-per-entry kernel when k or n is small), factor A22
+// (recursively).  A single column is a leaf: one CTA finds the pivot (the
+// first row of largest |A(i, j)|, compared as dd values), records it,
+// interchanges the two rows across the whole matrix and forms the
+// multipliers.  dgetrf2 applies each half's interchanges to the other half
+// as a block afterwards; swapping whole rows at the leaf gives the same
+// matrix, because nothing reads or writes the other half in between, and
+// needs no sequential interchange passes.  The top-level updates are large
+// products; the leaves and the thin updates near them are latency-bound.
+
+namespace {
+
+constexpr int LT = 256;   // threads of the pivot-column kernel
+
+// Pivot candidates: |x| of a normalised dd x orders by |hi| first (compared
+// as the integer bit pattern, off the FP64 pipe), then by lo taken with the
+// sign of hi; ties go to the lower row (the first maximum, as idamax).
+struct PivotKey {
+    uint64_t mag;   // |hi| bits
+    double lo;      // lo * sign(hi)
+    int64_t row;    // -1: none
+};
+
+__device__ __forceinline__ PivotKey pivot_key(double hi, double lo, int64_t row) {
+    const uint64_t b = (uint64_t)__double_as_longlong(hi);
+    return PivotKey{b & 0x7fffffffffffffffull, (b >> 63) ? -lo : lo, row};
+}
+
+// b is the better pivot than a
+__device__ __forceinline__ bool better(const PivotKey &b, const PivotKey &a) {
+    if (b.row < 0) return false;
+    if (a.row < 0) return true;
+    if (b.mag != a.mag) return b.mag > a.mag;
+    if (b.lo != a.lo) return b.lo > a.lo;
+    return b.row < a.row;
+}
+
+// Column j (global) of A, rows [j, m): pivot search, interchange of rows j
+// and p across all n columns of A, and the multipliers below the diagonal
+// (as LAPACK's dgetf2: one dd reciprocal of the pivot, then a product per
+// entry; a division per entry when the pivot is below 2^-1021, where the
+// reciprocal could overflow).
+__global__ void __launch_bounds__(LT) getrf_column_kernel(double *ah, double *al, int64_t lda,
+                                                          int64_t m, int64_t n, int64_t j,
+                                                          int64_t *ipiv, int64_t *info) {
+    __shared__ PivotKey wk[LT / 32];
+    __shared__ int64_t piv_row;
+    __shared__ double ph, pl, rh, rl;
+    const double *ch = ah + j * lda, *cl = al + j * lda;
+    PivotKey best{0, 0.0, -1};
+    for (int64_t i = j + threadIdx.x; i < m; i += LT) {
+        const PivotKey c = pivot_key(ch[i], cl[i], i);
+        if (better(c, best)) best = c;
+    }
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (int off = 16; off > 0; off /= 2) {
+        PivotKey o{__shfl_down_sync(0xffffffffu, best.mag, off),
+                   __shfl_down_sync(0xffffffffu, best.lo, off),
+                   __shfl_down_sync(0xffffffffu, best.row, off)};
+        if (better(o, best)) best = o;
+    }
+    if (lane == 0) wk[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < LT / 32; ++w)
+            if (better(wk[w], best)) best = wk[w];
+        const int64_t p = best.row;
+        ipiv[j] = p + 1;
+        piv_row = p;
+        ph = ch[p];
+        pl = cl[p];
+        if (ph == 0.0 && pl == 0.0) {
+            atomicCAS(reinterpret_cast<unsigned long long *>(info), 0ull,
+                      (unsigned long long)(j + 1));
+        } else if (fabs(ph) >= 0x1p-1021) {
+            const dd r = div(dd{1.0, 0.0}, dd{ph, pl});
+            rh = r.hi;
+            rl = r.lo;
+        }
+    }
+    __syncthreads();
+    if (ph == 0.0 && pl == 0.0) return;   // LAPACK: no interchange, no scaling
+    const int64_t p = piv_row;
+    if (p != j) {
+        for (int64_t c = threadIdx.x; c < n; c += LT) {
+            const int64_t oj = j + c * lda, op = p + c * lda;
+            const double th = ah[oj], tl = al[oj];
+            ah[oj] = ah[op]; al[oj] = al[op];
+            ah[op] = th; al[op] = tl;
+        }
+    }
+    __syncthreads();
+    double *wh = ah + j * lda, *wl = al + j * lda;
+    if (fabs(ph) >= 0x1p-1021) {
+        const dd r{rh, rl};
+        for (int64_t i = j + 1 + threadIdx.x; i < m; i += LT) {
+            dd v = mul(dd{wh[i], wl[i]}, r);
+            wh[i] = v.hi; wl[i] = v.lo;
+        }
+    } else {
+        const dd pv{ph, pl};
+        for (int64_t i = j + 1 + threadIdx.x; i < m; i += LT) {
+            dd v = div(dd{wh[i], wl[i]}, pv);
+            wh[i] = v.hi; wl[i] = v.lo;
+        }
+    }
+}
+
+// Row interchanges ipiv[k0 .. k1) (one-based global rows, applied in order)
+// on columns [c0, c1) of A: one thread per column.
+__global__ void laswp_kernel(double *ah, double *al, int64_t lda, int64_t c0, int64_t c1,
+                             const int64_t *ipiv, int64_t k0, int64_t k1, int reverse) {
+    const int64_t c = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    double *ch = ah + c * lda, *cl = al + c * lda;
+    for (int64_t t = 0; t < k1 - k0; ++t) {
+        const int64_t k = reverse ? k1 - 1 - t : k0 + t;
+        const int64_t p = ipiv[k] - 1;
+        if (p != k) {
+            double th = ch[k], tl = cl[k];
+            ch[k] = ch[p]; cl[k] = cl[p];
+            ch[p] = th; cl[p] = tl;
+        }
+    }
+}
+
+// C(m x n) -= A(m x k) B(k x n), all column-major, for small k or n: one
+// thread per entry of C, multiply-adds l = 0 .. k-1 straight into C's value.
+// (The 64 x 64 tiles of the Rgemm kernel would compute zero-padded products
+// worth up to 16 / k and 64 / n times the useful ones.)
+__global__ void __launch_bounds__(256) small_update_kernel(
+    int64_t m, int64_t n, int64_t k, const double *__restrict__ ah,
+    const double *__restrict__ al, int64_t lda, const double *__restrict__ bh,
+    const double *__restrict__ bl, int64_t ldb, double *ch, double *cl, int64_t ldc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * n) return;
+    const int64_t i = e % m, j = e / m;
+    dd acc{ch[i + j * ldc], cl[i + j * ldc]};
+    for (int64_t l = 0; l < k; ++l)
+        mac(acc, dd{-ah[i + l * lda], -al[i + l * lda]}, dd{bh[l + j * ldb], bl[l + j * ldb]});
+    ch[i + j * ldc] = acc.hi;
+    cl[i + j * ldc] = acc.lo;
+}
+
+constexpr int64_t kSmallUpdate = 16;   // k or n at or below this: small_update_kernel
+
+struct LuPlan {
+    double *ah, *al;
+    int64_t lda, m, n;     // the whole matrix
+    int64_t *ipiv, *info;
+    cudaStream_t st;
+};
+
+int laswp(const LuPlan &P, double *bh, double *bl, int64_t ldb, int64_t c0, int64_t c1,
+          int64_t k0, int64_t k1, int reverse) {
+    if (c1 <= c0 || k1 <= k0) return 0;
+    const int64_t cols = c1 - c0;
+    laswp_kernel<<<(unsigned)ceil_div(cols, 128), 128, 0, P.st>>>(bh, bl, ldb, c0, c1, P.ipiv,
+                                                                  k0, k1, reverse);
+    return check_launch("laswp_kernel");
+}
+
+// Factor the block of rows [j0, m) and columns [j0, j0 + n) (the rows above
+// j0 are already final).
+int getrf_rec(const LuPlan &P, int64_t j0, int64_t n) {
+    const int64_t rows = P.m - j0;
+    if (n <= 0 || rows <= 0) return 0;
+    int rc;
+    if (n == 1) {
+        getrf_column_kernel<<<1, LT, 0, P.st>>>(P.ah, P.al, P.lda, P.m, P.n, j0, P.ipiv,
+                                                P.info);
+        return check_launch("getrf_column_kernel");
+    }
+    const int64_t mn = rows < n ? rows : n;
+    const int64_t n1 = mn / 2 > 0 ? mn / 2 : 1, n2 = n - n1;
+    if ((rc = getrf_rec(P, j0, n1))) return rc;
+    // A12 := L11^-1 A12 (n1 x n2), A22 -= A21 A12
+    const int64_t o11 = j0 + j0 * P.lda, o12 = j0 + (j0 + n1) * P.lda;
+    if (n1 > 1 &&   // a unit 1 x 1 L11 leaves A12 as it is
+        (rc = run_trsm(0, 1, 0, 1, n1, n2, mp_dd{1.0, 0.0}, P.ah + o11, P.al + o11, P.lda,
+                       P.ah + o12, P.al + o12, P.lda, P.st)))
+        return rc;
+    const int64_t m2 = rows - n1;
+    if (m2 > 0 && (n1 <= kSmallUpdate || n2 <= kSmallUpdate)) {
+        const int64_t o21 = (j0 + n1) + j0 * P.lda, o22 = (j0 + n1) + (j0 + n1) * P.lda;
+        const int64_t count = m2 * n2;
+        small_update_kernel<<<(unsigned)ceil_div(count, 256), 256, 0, P.st>>>(
+            m2, n2, n1, P.ah + o21, P.al + o21, P.lda, P.ah + o12, P.al + o12, P.lda,
+            P.ah + o22, P.al + o22, P.lda);
+        if ((rc = check_launch("small_update_kernel"))) return rc;
+        if ((rc = getrf_rec(P, j0 + n1, n2))) return rc;
+    } else if (m2 > 0) {
+        GemmArgs g{};
+        g.m = m2; g.n = n2; g.k = n1;
+        g.alpha = mp_dd{-1.0, 0.0}; g.beta = mp_dd{1.0, 0.0};
+        const int64_t o21 = (j0 + n1) + j0 * P.lda, o22 = (j0 + n1) + (j0 + n1) * P.lda;
+        g.ah = P.ah + o21; g.al = P.al + o21; g.lda = P.lda;
+        g.bh = P.ah + o12; g.bl = P.al + o12; g.ldb = P.lda;
+        g.ch = P.ah + o22; g.cl = P.al + o22; g.ldc = P.lda;
+        g.ta = 0; g.tb = 0; g.tri = 0;
+        g.alpha_zero = 0; g.alpha_one = 0; g.beta_zero = 0;
+        if ((rc = launch_gemm_plain(g, P.st))) return rc;
+        if ((rc = getrf_rec(P, j0 + n1, n2))) return rc;
+    }
+    return 0;
+}
+
+}  // namespace
+
+int run_getrf(int64_t m, int64_t n, double *ah, double *al, int64_t lda, int64_t *ipiv,
+              int64_t *info, cudaStream_t st) {
+    int rc = set_attrs();
+    if (rc) return rc;
+    cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "info reset");
+    LuPlan P{ah, al, lda, m, n, ipiv, info, st};
+    return getrf_rec(P, 0, n);
+}
+
+int run_getrs(int trans, int64_t n, int64_t nrhs, const double *ah, const double *al,
+              int64_t lda, const int64_t *ipiv, double *bh, double *bl, int64_t ldb,
+              cudaStream_t st) {
+    LuPlan P{const_cast<double *>(ah), const_cast<double *>(al), lda, n, n,
+             const_cast<int64_t *>(ipiv), nullptr, st};
+    int rc;
+    const mp_dd one{1.0, 0.0};
+    if (!trans) {
+        if ((rc = laswp(P, bh, bl, ldb, 0, nrhs, 0, n, 0))) return rc;
+        if ((rc = run_trsm(0, 1, 0, 1, n, nrhs, one, ah, al, lda, bh, bl, ldb, st))) return rc;
+        return run_trsm(0, 0, 0, 0, n, nrhs, one, ah, al, lda, bh, bl, ldb, st);
+    }
+    if ((rc = run_trsm(0, 0, 1, 0, n, nrhs, one, ah, al, lda, bh, bl, ldb, st))) return rc;
+    if ((rc = run_trsm(0, 1, 1, 1, n, nrhs, one, ah, al, lda, bh, bl, ldb, st))) return rc;
+    return laswp(P, bh, bl, ldb, 0, nrhs, 0, n, 1);
+}
+
 }  // namespace mpdd

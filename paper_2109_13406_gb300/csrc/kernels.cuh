@@ -25,6 +25,13 @@ struct GemmArgs {
     int alpha_one;   // alpha == 1: the product is stored without scaling
     int beta_zero;   // beta == 0: C is write-only
     const int64_t *info = nullptr;  // optional device word: non-zero -> leave C as is
+    // Rsyr2k: a second product op(A2) op(B2) (same transposes and k) summed
+    // into the same accumulators after the first; a2h == nullptr: none.
+    const double *a2h = nullptr, *a2l = nullptr, *b2h = nullptr, *b2l = nullptr;
+    int64_t lda2 = 0, ldb2 = 0;
+    // Rsymm: op(A) (sym_a) or op(B) (sym_b) is symmetric with one triangle
+    // stored: 0 = no, 1 = upper stored, 2 = lower stored (transpose flag 0).
+    int sym_a = 0, sym_b = 0;
 };
 
 // Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).
@@ -60,6 +67,13 @@ int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double
 int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp_dd alpha,
              const double *ah, const double *al, int64_t lda, double *bh, double *bl,
              int64_t ldb, cudaStream_t stream);
+// dd Rgetrf / Rgetrs (recursive LU with partial pivoting); ipiv one-based,
+// device memory; info device int64 (LAPACK convention).
+int run_getrf(int64_t m, int64_t n, double *ah, double *al, int64_t lda, int64_t *ipiv,
+              int64_t *info, cudaStream_t stream);
+int run_getrs(int trans, int64_t n, int64_t nrhs, const double *ah, const double *al,
+              int64_t lda, const int64_t *ipiv, double *bh, double *bl, int64_t ldb,
+              cudaStream_t stream);
 int launch_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *ds, cudaStream_t st);
 int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
                       cudaStream_t st);

@@ -24,6 +24,7 @@ from oracle import fraction_ref as fr
 from ddcheck import EPS_DD, U, err_over_bound, gemm_bound, is_normalised
 from trsmcheck import TRSM_VARIANTS, op_triangle, trsm_residual_over_bound
 import blas3check as b3
+from lucheck import dyadic_lu_case, lu_residual_ratio
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN = os.path.join(HERE, "golden")
@@ -560,39 +561,6 @@ def test_symm_integer_inputs_match_binary64():
 # Rgetrf / Rgetrs
 # ---------------------------------------------------------------------------
 
-def dyadic_lu_case(seed, m, n):
-    """A = (rows of L U placed at rows sigma) with L unit lower, |L| <= 1/2
-    below the diagonal in quarters, U integer with a power-of-two diagonal:
-    partial pivoting must find sigma, L and U exactly.  Returns A, L, U and
-    the expected one-based ipiv."""
-    g = datagen.rng(seed)
-    mn = min(m, n)
-    L = np.tril(g.choice([-0.5, -0.25, 0.0, 0.25, 0.5], (m, mn)), -1)
-    L[np.arange(mn), np.arange(mn)] = 1.0
-    U = np.triu(g.integers(-5, 6, (mn, n)).astype(np.float64))
-    U[np.arange(mn), np.arange(mn)] = g.choice([-4.0, -2.0, -1.0, 1.0, 2.0, 4.0], mn)
-    sigma = g.permutation(m)
-    A = np.zeros((m, n))
-    A[sigma, :] = L @ U
-    cur = list(range(m))
-    ipiv = []
-    for j in range(mn):
-        p = cur.index(sigma[j])
-        ipiv.append(p + 1)
-        cur[j], cur[p] = cur[p], cur[j]
-    # P A = L' U with L' the rows of L in the final order of A's rows
-    inv = np.argsort(sigma)
-    return np.asfortranarray(A), L[inv[cur]], U, np.array(ipiv)
-
-
-def apply_ipiv(X, ipiv):
-    """Rows of X interchanged as ipiv says (in order): P X."""
-    X = X.copy()
-    for j, p in enumerate(ipiv):
-        X[[j, p - 1]] = X[[p - 1, j]]
-    return X
-
-
 @pytest.mark.parametrize("m,n", [(12, 12), (15, 9), (8, 13)])
 def test_getrf_recovers_dyadic_factorisation(m, n):
     A, L, U, ipiv = dyadic_lu_case(100 + m, m, n)
@@ -601,21 +569,6 @@ def test_getrf_recovers_dyadic_factorisation(m, n):
     mn = min(m, n)
     assert np.array_equal(np.tril(lh[:, :mn], -1), np.tril(L, -1))
     assert np.array_equal(np.triu(lh[:mn, :]), U)
-
-
-def lu_residual_ratio(A, LU, ipiv, m, n):
-    """||P A - L U||_1 / (n ||A||_1 eps_dd), the product evaluated exactly."""
-    mn = min(m, n)
-    L = [np.tril(P[:, :mn], -1) for P in LU]
-    L[0][np.arange(mn), np.arange(mn)] = 1.0
-    U = [np.triu(P[:mn, :]) for P in LU]
-    PA = tuple(np.asfortranarray(apply_ipiv(P, ipiv)) for P in A)
-    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
-    R = oracle.exact_gemm_entries("N", "N", mn, (1.0, 0.0), tuple(np.asfortranarray(x) for x in L),
-                                  tuple(np.asfortranarray(x) for x in U), (-1.0, 0.0), PA,
-                                  rr.ravel(), cc.ravel())
-    Rn = np.abs(R[0].reshape(m, n)).sum(axis=0).max()
-    return Rn / (n * np.abs(A[0]).sum(axis=0).max() * EPS_DD)
 
 
 @pytest.mark.parametrize("m,n", [(40, 40), (47, 31), (29, 44)])
