@@ -44,6 +44,39 @@ def dd_lo_for(hi: np.ndarray, g: np.random.Generator):
     return _renormalise(hi, lo)
 
 
+def qd_tail_for(x0: np.ndarray, g: np.random.Generator):
+    """Four components (x0', x1, x2, x3) with x_{t+1} drawn as x_t 2^-53
+    U(-1, 1) and the four renormalised (each component within half an ulp
+    of the one above)."""
+    x = [np.asarray(x0, dtype=np.float64)]
+    for _ in range(3):
+        x.append(x[-1] * 2.0 ** -53 * g.uniform(-1.0, 1.0, size=x[-1].shape))
+    for t in (0, 1, 2):   # top-down, twice: |x_{t+1}| <= ulp(x_t) / 2
+        x[t], x[t + 1] = _renormalise(x[t], x[t + 1])
+    for t in (0, 1, 2):
+        x[t], x[t + 1] = _renormalise(x[t], x[t + 1])
+    return tuple(x)
+
+
+def qd_matrix(g: np.random.Generator, rows: int, cols: int, ld: int | None = None,
+              low: float = -1.0, high: float = 1.0):
+    """A rows x cols quad-double matrix: four column-major planes of leading
+    dimension ld (padding rows NaN), x0 ~ U(low, high) and the lower
+    components as ``qd_tail_for``."""
+    ld = max(1, rows if ld is None else ld)
+    comps = qd_tail_for(g.uniform(low, high, size=(rows, cols)), g)
+    out = []
+    for c in comps:
+        P = np.full((ld, cols), np.nan, order="F")
+        P[:rows, :] = c
+        out.append(P)
+    return tuple(out)
+
+
+def qd_scalar(g: np.random.Generator, low: float = 0.5, high: float = 2.0):
+    return tuple(float(c[0]) for c in qd_tail_for(np.array([g.uniform(low, high)]), g))
+
+
 def dd_matrix(g: np.random.Generator, rows: int, cols: int, ld: int | None = None,
               low: float = -1.0, high: float = 1.0):
     """A rows x cols dd matrix in column-major planes of leading dimension ld.

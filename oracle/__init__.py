@@ -115,6 +115,9 @@ def lib():
             L.oracle_dd_symm.argtypes = [c, c, i64, i64, d, d, _D, _D, i64, _D, _D, i64, d, d,
                                          _D, _D, i64]
             L.oracle_exact_sum.argtypes = [i64, _D, _D, _D]
+            _P4 = ctypes.POINTER(_D)
+            L.oracle_exact_qd_gemm_entries.argtypes = [c, c, i64, _D, _P4, i64, _P4, i64, _D,
+                                                       _P4, i64, i64, _I64, _I64, _P4]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
@@ -341,6 +344,35 @@ def dd_trsm(side, uplo, transa, diag, alpha, A, B, m=None, n=None):
                          float(alpha[0]), float(alpha[1]), _p(ah), _p(al), _ld(ah), _p(bh),
                          _p(bl), _ld(bh))
     return bh, bl
+
+
+def _planes4(X):
+    """Four float64 column-major planes and a C array of their pointers."""
+    planes = [_f64(P) for P in X]
+    arr = (_D * 4)(*[_p(P) for P in planes])
+    return planes, arr
+
+
+def exact_qd_gemm_entries(transa, transb, k, alpha, A, B, beta, C, rows, cols):
+    """Selected entries of RN_qd(alpha op(A) op(B) + beta C), exactly: a tuple
+    of four component arrays.  alpha, beta: 4-tuples; A, B, C: 4 planes each."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    count = rows.size
+    al = np.ascontiguousarray(alpha, dtype=np.float64)
+    be = np.ascontiguousarray(beta, dtype=np.float64)
+    pa, aa = _planes4(A)
+    pb, ab = _planes4(B)
+    if C is None:
+        C = [np.zeros((1, 1), order="F")] * 4
+    pc, ac = _planes4(C)
+    out = [np.zeros(count) for _ in range(4)]
+    ao = (_D * 4)(*[_p(o) for o in out])
+    lib().oracle_exact_qd_gemm_entries(_ch(transa), _ch(transb), k, _p(al), aa, _ld(pa[0]),
+                                       ab, _ld(pb[0]), _p(be), ac, _ld(pc[0]), count,
+                                       rows.ctypes.data_as(_I64), cols.ctypes.data_as(_I64),
+                                       ao)
+    return tuple(out)
 
 
 def exact_sum(x):

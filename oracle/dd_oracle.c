@@ -769,6 +769,61 @@ void oracle_exact_gemm_entries(char transa, char transb, int64_t k, double alpha
     }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Quad-double (qd): a value is x0 + x1 + x2 + x3 of four binary64 numbers    */
+/* (the manual's quad-double format, Sec. 5, from the QD library)             */
+/* ------------------------------------------------------------------------- */
+
+/* Round the accumulator to qd: x0 = RN(S), x1 = RN(S - x0), x2 = RN(S - x0 -
+ * x1), x3 = RN(S - x0 - x1 - x2); every subtraction is exact in the
+ * accumulator, so |S - (x0 + x1 + x2 + x3)| <= ulp(x3) / 2. */
+static void sa_round_qd(superacc *s, double out[4]) {
+    for (int t = 0; t < 4; ++t) {
+        sa_normalise(s);
+        out[t] = sa_round(s);
+        sa_add(s, -out[t]);
+    }
+}
+
+/* Exact qd Rgemm entries: out[t][q] = component t of RN_qd(alpha*sum_l
+ * op(A)(i,l)*op(B)(l,j) + beta*C(i,j)) for (i, j) = (rows[q], cols[q]).
+ * alpha, beta: 4 components each; A, B, C, out: 4 column-major planes each
+ * (A and B with leading dimensions lda, ldb; C with ldc, read only if beta
+ * != 0).  Every one of the 64 triple products alpha_t a_u b_v per l is
+ * accumulated exactly. */
+void oracle_exact_qd_gemm_entries(char transa, char transb, int64_t k, const double *alpha,
+                                  const double *const *A, int64_t lda, const double *const *B,
+                                  int64_t ldb, const double *beta, const double *const *C,
+                                  int64_t ldc, int64_t count, const int64_t *rows,
+                                  const int64_t *cols, double *const *out) {
+    int ta = is_trans(transa), tb = is_trans(transb);
+    int beta_zero = beta[0] == 0.0 && beta[1] == 0.0 && beta[2] == 0.0 && beta[3] == 0.0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < count; ++q) {
+        superacc *s = (superacc *)malloc(sizeof(superacc));
+        sa_clear(s);
+        int64_t i = rows[q], j = cols[q];
+        for (int64_t l = 0; l < k; ++l) {
+            int64_t ia = ta ? (l + i * lda) : (i + l * lda);
+            int64_t ib = tb ? (j + l * ldb) : (l + j * ldb);
+            for (int x = 0; x < 4; ++x)
+                for (int y = 0; y < 4; ++y)
+                    for (int z = 0; z < 4; ++z)
+                        if (alpha[x] != 0.0 && A[y][ia] != 0.0 && B[z][ib] != 0.0)
+                            sa_add_prod3(s, alpha[x], A[y][ia], B[z][ib]);
+        }
+        if (!beta_zero)
+            for (int x = 0; x < 4; ++x)
+                for (int y = 0; y < 4; ++y)
+                    if (beta[x] != 0.0 && C[y][i + j * ldc] != 0.0)
+                        sa_add_prod2(s, beta[x], C[y][i + j * ldc]);
+        double r[4];
+        sa_round_qd(s, r);
+        for (int t = 0; t < 4; ++t) out[t][q] = r[t];
+        free(s);
+    }
+}
+
 /* Exact sum of an array of binary64 values, rounded to dd (pins the
  * superaccumulator itself against known sums). */
 void oracle_exact_sum(int64_t n, const double *x, double *out_hi, double *out_lo) {

@@ -468,6 +468,77 @@ def test_potrf_matches_numpy_on_well_conditioned_spd():
 
 
 # ---------------------------------------------------------------------------
+# quad-double exact tier
+# ---------------------------------------------------------------------------
+
+def round_qd_fraction(v):
+    """Four components by repeated correct rounding of the rational v (Python's
+    float(Fraction) rounds to nearest, ties to even)."""
+    out = []
+    for _ in range(4):
+        x = float(v)
+        out.append(x)
+        v -= Fraction(x)
+    return out
+
+
+def qd_frac(c, idx):
+    return sum((Fraction(float(P[idx])) for P in c), Fraction(0))
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_exact_qd_tier_equals_fraction_rounding(ta, tb):
+    g = datagen.rng(140)
+    m, n, k = 3, 4, 5
+    A = datagen.qd_matrix(g, k if ta == "T" else m, m if ta == "T" else k)
+    B = datagen.qd_matrix(g, n if tb == "T" else k, k if tb == "T" else n)
+    C = datagen.qd_matrix(g, m, n)
+    al, be = datagen.qd_scalar(g), datagen.qd_scalar(g)
+    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    got = oracle.exact_qd_gemm_entries(ta, tb, k, al, A, B, be, C, rr.ravel(), cc.ravel())
+    fa, fb = sum(map(Fraction, al)), sum(map(Fraction, be))
+    for q, (i, j) in enumerate(zip(rr.ravel(), cc.ravel())):
+        v = fb * qd_frac(C, (i, j))
+        for l in range(k):
+            a = qd_frac(A, (l, i) if ta == "T" else (i, l))
+            b = qd_frac(B, (j, l) if tb == "T" else (l, j))
+            v += fa * a * b
+        assert [got[t][q] for t in range(4)] == round_qd_fraction(v)
+
+
+def test_exact_qd_tier_matches_dd_tier_on_dd_inputs():
+    """With zero third and fourth components, the first two components of
+    the qd rounding are the dd rounding of the same exact value."""
+    g = datagen.rng(141)
+    m, n, k = 6, 5, 33
+    A = datagen.dd_matrix(g, m, k)
+    B = datagen.dd_matrix(g, k, n)
+    C = datagen.dd_matrix(g, m, n)
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    z = lambda P: np.zeros_like(P)
+    A4, B4, C4 = ((P[0], P[1], z(P[0]), z(P[0])) for P in (A, B, C))
+    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    q = oracle.exact_qd_gemm_entries("N", "N", k, (*al, 0.0, 0.0), A4, B4, (*be, 0.0, 0.0),
+                                     C4, rr.ravel(), cc.ravel())
+    d = oracle.exact_gemm_entries("N", "N", k, al, A, B, be, C, rr.ravel(), cc.ravel())
+    assert np.array_equal(q[0], d[0]) and np.array_equal(q[1], d[1])
+
+
+def test_exact_qd_tier_integer_inputs():
+    g = datagen.rng(142)
+    A = g.integers(-50, 51, (7, 9)).astype(np.float64)
+    B = g.integers(-50, 51, (9, 6)).astype(np.float64)
+    z = lambda P: np.zeros_like(P)
+    rr, cc = np.meshgrid(np.arange(7), np.arange(6), indexing="ij")
+    q = oracle.exact_qd_gemm_entries("N", "N", 9, (2.0, 0, 0, 0),
+                                     (np.asfortranarray(A), z(A), z(A), z(A)),
+                                     (np.asfortranarray(B), z(B), z(B), z(B)), (0, 0, 0, 0),
+                                     None, rr.ravel(), cc.ravel())
+    assert np.array_equal(q[0].reshape(7, 6), 2 * A @ B)
+    assert not q[1].any() and not q[2].any() and not q[3].any()
+
+
+# ---------------------------------------------------------------------------
 # Rsyr2k / Rsymm
 # ---------------------------------------------------------------------------
 
@@ -758,6 +829,9 @@ MUTANTS = {
                                        "        if (p != j)\n            for (int64_t c = j; c < n; ++c) {"),
     "getrs_no_unpivot": ("            for (int64_t j = n - 1; j >= 0; --j)\n                if (ipiv[j] - 1 != j) SWAPROW(j, ipiv[j] - 1);",
                          ""),
+    "qd_tier_drops_fourth_component": (
+        "                    for (int z = 0; z < 4; ++z)\n                        if (alpha[x] != 0.0 && A[y][ia] != 0.0 && B[z][ib] != 0.0)",
+        "                    for (int z = 0; z < 3; ++z)\n                        if (alpha[x] != 0.0 && A[y][ia] != 0.0 && B[z][ib] != 0.0)"),
     "symm_wrong_triangle": (
         "#define SYM(r, c) ((upper ? (r) <= (c) : (r) >= (c))",
         "#define SYM(r, c) ((upper ? (r) >= (c) : (r) <= (c))"),
