@@ -43,6 +43,7 @@ UNIT = "dd-GFlop/s"
 # costs 12.75 of them (1 DMUL + 3 DFMA + 8 DADD, FastTwoSum every 4 steps)
 NOMINAL_FP64_INSTR = 1.25e12 / 2
 FP64_OPS_PER_MAC = 12.75
+QD_OPS_PER_MAC = 117.5   # qd multiply-add: 113 FP64 operations + 4.5 for the level pass
 
 
 def parse():
@@ -246,10 +247,9 @@ def run_ours(args):
                   "crt_well_scaled": sliced_section(mp, torch, args.sliced_size, form="crt"),
                   "crt_ill_scaled_outer": sliced_section(mp, torch, args.sliced_size,
                                                          ill="outer", form="crt")}
-    trsm = None
+    routines = None
     if not args.no_sliced:
-        trsm = {f"{s}{u}{t}N_{size}": trsm_section(mp, torch, size, s, u, t)
-                for (s, u, t) in (("L", "U", "N"), ("R", "L", "T"))}
+        routines = routines_section(mp, torch, size)
     if rank == 0:
         cpu = None if args.no_cpu or world > 1 else cpu_baseline(size, budget_s=15.0)
         line = {
@@ -267,7 +267,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "sliced": sliced,
-            "rtrsm": trsm,
+            "routines": routines,
             "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
@@ -276,42 +276,98 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def trsm_section(mp, torch, size, side, uplo, transa, reps=2):
-    """Time mp_dd_Rtrsm (m = n = size, diag 'N') with CUDA events on the
-    launching stream.  dd-flops: m^2 n (side L) or m n^2 (side R), the LAPACK
-    count; FP64 work: the m^2 n / 2 multiply-adds of the off-diagonal blocks
-    at the plain kernel's instructions per multiply-add."""
-    c = datagen.trsm_case(3, side, uplo, transa, "N", size, size)
-    A = tuple(mp.to_device(x) for x in c.A)
-    B0 = tuple(mp.to_device(x) for x in c.B)
-    B = tuple(x.clone() for x in B0)
-    st = torch.cuda.current_stream()
-
-    def call():
-        mp.mp_dd_Rtrsm(side, uplo, transa, "N", size, size, c.alpha, A, size, B, size)
-
-    call()
+def _event_ms(torch, st, fn, reset=None, reps=2):
+    """Mean CUDA-event time of fn() on stream st after one untimed call;
+    reset() (untimed) restores the inputs before every call."""
+    if reset:
+        reset()
+    fn()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
-        for x, y in zip(B, B0):
-            x.copy_(y)
+        if reset:
+            reset()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        call()
+        fn()
         e1.record(st)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
-    ms = sum(ts) / len(ts)
-    flops = float(size) ** 3
-    instr = FP64_OPS_PER_MAC * flops / 2 / (ms * 1e-3) / 1e9
-    return {"workload": f"dd Rtrsm side={side} uplo={uplo} transa={transa} diag=N, "
-                        f"m=n={size}, diagonally dominant A", "ms": ms,
-            "dd_GFlops": flops / (ms * 1e-3) / 1e9,
+    return sum(ts) / len(ts)
+
+
+def _fp64_line(workload, ms, flops, macs):
+    """dd-GFlop/s and the FP64-pipe roofline of one routine call: the FP64
+    work is its multiply-adds at the plain kernel's instructions per
+    multiply-add."""
+    instr = FP64_OPS_PER_MAC * macs / (ms * 1e-3) / 1e9
+    return {"workload": workload, "ms": ms, "dd_GFlops": flops / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "alu", "achieved": instr, "peak": NOMINAL_FP64_INSTR / 1e9,
                          "unit": "GFP64instr/s", "frac": instr / (NOMINAL_FP64_INSTR / 1e9),
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FP64 "
                                         "instr/s (derived)"}}
+
+
+def routines_section(mp, torch, size):
+    """The other routines at m = n = k = size, each timed with CUDA events on
+    the launching stream: dd Rtrsm (two variants), Rsyr2k, Rsymm, Rgetrf, and
+    the quad-double Rgemm at min(size, 1024).  Flops are the LAPACK counts
+    (Rtrsm n^3, Rsyr2k 2 k n (n+1), Rsymm 2 n^3, Rgetrf 2 n^3 / 3, Rgemm
+    2 n^3)."""
+    st = torch.cuda.current_stream()
+    n = size
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    out = {}
+    for side, uplo, transa in (("L", "U", "N"), ("R", "L", "T")):
+        c = datagen.trsm_case(3, side, uplo, transa, "N", n, n)
+        A, B0 = dev(c.A), dev(c.B)
+        B = tuple(x.clone() for x in B0)
+
+        def reset():
+            for x, y in zip(B, B0):
+                x.copy_(y)
+        ms = _event_ms(torch, st, lambda: mp.mp_dd_Rtrsm(side, uplo, transa, "N", n, n, c.alpha,
+                                                         A, n, B, n), reset)
+        out[f"Rtrsm_{side}{uplo}{transa}N_{n}"] = _fp64_line(
+            f"dd Rtrsm side={side} uplo={uplo} transa={transa} diag=N, m=n={n}, diagonally "
+            "dominant A", ms, float(n) ** 3, float(n) ** 3 / 2)
+        del A, B0, B
+    g = datagen.rng(4)
+    A, B, C = (dev(datagen.dd_matrix(g, n, n)) for _ in range(3))
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rsyr2k("U", "N", n, n, al, A, n, B, n, be, C, n))
+    out[f"Rsyr2k_UN_{n}"] = _fp64_line(f"dd Rsyr2k uplo=U trans=N, n=k={n}", ms,
+                                       2.0 * n * n * (n + 1), float(n) * n * (n + 1))
+    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rsymm("L", "U", n, n, al, A, n, B, n, be, C, n))
+    out[f"Rsymm_LU_{n}"] = _fp64_line(f"dd Rsymm side=L uplo=U, m=n={n}", ms, 2.0 * n ** 3,
+                                      float(n) ** 3)
+    A0 = tuple(x.clone() for x in A)
+    ipiv = torch.zeros(n, dtype=torch.int64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def reset_lu():
+        for x, y in zip(A, A0):
+            x.copy_(y)
+    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rgetrf(n, n, A, n, ipiv, info), reset_lu)
+    out[f"Rgetrf_{n}"] = _fp64_line(f"dd Rgetrf (partial pivoting), m=n={n}, U(-1,1) entries",
+                                    ms, 2.0 * n ** 3 / 3, float(n) ** 3 / 3)
+    out[f"Rgetrf_{n}"]["info"] = int(info.item())
+    del A, B, C, A0
+    # quad-double Rgemm (117.5 FP64 instructions per qd multiply-add)
+    nq = min(n, 1024)
+    gq = datagen.rng(5)
+    Aq, Bq, Cq = (dev(datagen.qd_matrix(gq, nq, nq)) for _ in range(3))
+    aq, bq = datagen.qd_scalar(gq), datagen.qd_scalar(gq)
+    ms = _event_ms(torch, st, lambda: mp.mp_qd_Rgemm("N", "N", nq, nq, nq, aq, Aq, nq, Bq, nq,
+                                                     bq, Cq, nq))
+    line = _fp64_line(f"qd Rgemm NN m=n=k={nq}, qd entries x0~U(-1,1)", ms, 2.0 * nq ** 3,
+                      float(nq) ** 3)
+    instr = QD_OPS_PER_MAC * float(nq) ** 3 / (ms * 1e-3) / 1e9
+    line["qd_GFlops"] = line.pop("dd_GFlops")
+    line["roofline"].update(achieved=instr, frac=instr / (NOMINAL_FP64_INSTR / 1e9))
+    line["fp64_instr_per_qd_mac"] = QD_OPS_PER_MAC
+    out[f"qd_Rgemm_NN_{nq}"] = line
+    return out
 
 
 # ----------------------------------------------------------------------------

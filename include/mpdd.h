@@ -61,6 +61,23 @@ typedef struct {
     double *hi, *lo;
 } mp_dd_mat;
 
+/* Quad-double (qd) scalar: value = x[0] + x[1] + x[2] + x[3], components
+ * non-overlapping, largest first (the manual's quad-double format, Sec. 5). */
+typedef struct {
+    double x[4];
+} mp_qd;
+
+/* Read-only qd matrix: four device planes (component t of every entry in
+ * plane t) sharing one column-major leading dimension. */
+typedef struct {
+    const double *x[4];
+} mp_qd_cmat;
+
+/* Writable qd matrix planes. */
+typedef struct {
+    double *x[4];
+} mp_qd_mat;
+
 #define MP_DD_OK 0
 #define MP_DD_ERR_CUDA_BASE 1000
 #define MP_DD_ERR_TIMEOUT 2001
@@ -336,6 +353,25 @@ int mp_dd_Rgemm_grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, voi
  * between runs, its descriptors may not.  Runs that share a workspace must
  * not overlap on the device. */
 int mp_dd_Rgemm_grouped_run(void *workspace);
+
+/* ------------------------------------------------------------------------ */
+/* MPBLAS: quad-double Rgemm                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Rgemm in quad-double (the manual's qd_real MPBLAS, Sec. 5 and 7.3; DGEMM
+ * semantics): C := alpha op(A) op(B) + beta C on four-plane qd matrices.
+ * Each multiply-add forms the products of order 1, 2^-53 and 2^-106 of the
+ * components exactly and adds them error-free into a four-level
+ * accumulator; only the lowest level rounds.  Accuracy:
+ * |C - C_exact| <= 4 k 2^-209 (|alpha||A||B| + |beta||C|) componentwise
+ * (2^-209 is MPLAPACK's Rlamch epsilon for qd_real, Sec. 7.6).  beta = 0:
+ * C is write-only; alpha = 0 or k = 0: A and B are not read; the BLAS
+ * quick return applies.  Output entries are non-overlapping qd values.
+ * Errors and their numbering as mp_dd_Rgemm (-7 / -9 / -12 when any plane
+ * of A / B / C is NULL). */
+int mp_qd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                mp_qd alpha, mp_qd_cmat A, int64_t lda, mp_qd_cmat B, int64_t ldb, mp_qd beta,
+                mp_qd_mat C, int64_t ldc);
 
 /* ------------------------------------------------------------------------ */
 /* Split-precision Rgemm on the tensor cores (no counterpart in the manual)  */

@@ -27,7 +27,7 @@ __all__ = [
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
-    "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf",
+    "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_qd_Rgemm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf",
     "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
     "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
@@ -238,6 +238,31 @@ def mp_dd_Rpotrf(uplo, n, A, lda, info, check=True):
     _sync_stream()
     rc = _LIB.mp_dd_Rpotrf(_flag(uplo), n, _m(A), lda, _ptr(info))
     return _check(rc, "mp_dd_Rpotrf") if check else rc
+
+
+def _qd(x) -> _abi.MpQD:
+    v = _abi.MpQD()
+    comps = list(x) + [0.0] * (4 - len(x))
+    for t in range(4):
+        v.x[t] = float(comps[t])
+    return v
+
+
+def _qm(planes) -> _abi.MpQDCMat:
+    if len(planes) != 4:
+        raise ValueError("a qd matrix is four planes")
+    m = _abi.MpQDCMat()
+    for t in range(4):
+        m.x[t] = _ptr(planes[t])
+    return m
+
+
+def mp_qd_Rgemm(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, check=True):
+    """Quad-double Rgemm; alpha/beta 4-tuples, A/B/C four device planes each."""
+    _sync_stream()
+    rc = _LIB.mp_qd_Rgemm(_flag(transa), _flag(transb), m, n, k, _qd(alpha), _qm(A), lda,
+                          _qm(B), ldb, _qd(beta), _qm(C), ldc)
+    return _check(rc, "mp_qd_Rgemm") if check else rc
 
 
 def mp_dd_Rgetrf(m, n, A, lda, ipiv, info, check=True):

@@ -50,6 +50,19 @@ class MpDDPotrfDiagDesc(ctypes.Structure):
                 ("lower", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class MpQD(ctypes.Structure):
+    """``mp_qd``: four components."""
+    _fields_ = [("x", ctypes.c_double * 4)]
+
+
+class MpQDCMat(ctypes.Structure):
+    """``mp_qd_cmat``: four device plane pointers."""
+    _fields_ = [("x", ctypes.c_void_p * 4)]
+
+
+MpQDMat = MpQDCMat  # same layout (``mp_qd_mat``)
+
+
 class MpDDTrsmDesc(ctypes.Structure):
     """``mp_dd_trsm_desc``."""
     _fields_ = [("u_hi", ctypes.c_void_p), ("u_lo", ctypes.c_void_p), ("ldu", ctypes.c_int64),
@@ -96,6 +109,8 @@ SIGNATURES = {
     "mp_dd_potrf_diag_batch": (_int, [_i64, _vp]),
     "mp_dd_trsm_batch": (_int, [_i64, _vp, _i64]),
     "mp_dd_Rtrsm": (_int, [_c, _c, _c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDMat, _i64]),
+    "mp_qd_Rgemm": (_int, [_c, _c, _i64, _i64, _i64, MpQD, MpQDCMat, _i64, MpQDCMat, _i64, MpQD,
+                           MpQDMat, _i64]),
     "mp_dd_Rgetrf": (_int, [_i64, _i64, MpDDMat, _i64, _vp, _vp]),
     "mp_dd_Rgetrs": (_int, [_c, _i64, _i64, MpDDCMat, _i64, _vp, MpDDMat, _i64]),
     "mp_dd_Rsyr2k": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDCMat, _i64, MpDD,

@@ -252,6 +252,38 @@ int mp_dd_Rsyrk(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd
     return launch_gemm_plain(p, tls().stream);
 }
 
+int mp_qd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
+                mp_qd alpha, mp_qd_cmat A, int64_t lda, mp_qd_cmat B, int64_t ldb, mp_qd beta,
+                mp_qd_mat C, int64_t ldc) {
+    clear_error();
+    const int ta = trans_flag(transa), tb = trans_flag(transb);
+    if (ta < 0) return fail(-1, "qd Rgemm: illegal transa");
+    if (tb < 0) return fail(-2, "qd Rgemm: illegal transb");
+    if (m < 0) return fail(-3, "qd Rgemm: m < 0");
+    if (n < 0) return fail(-4, "qd Rgemm: n < 0");
+    if (k < 0) return fail(-5, "qd Rgemm: k < 0");
+    const int64_t nrowa = ta ? k : m, nrowb = tb ? n : k;
+    if (lda < imax(1, nrowa)) return fail(-8, "qd Rgemm: lda < max(1, %lld)", (long long)nrowa);
+    if (ldb < imax(1, nrowb)) return fail(-10, "qd Rgemm: ldb < max(1, %lld)", (long long)nrowb);
+    if (ldc < imax(1, m)) return fail(-13, "qd Rgemm: ldc < max(1, m)");
+    const bool alpha_zero = alpha.x[0] == 0.0 && alpha.x[1] == 0.0 && alpha.x[2] == 0.0 &&
+                            alpha.x[3] == 0.0;
+    const bool need_ab = m > 0 && n > 0 && k > 0 && !alpha_zero;
+    for (int v = 0; v < 4; ++v) {
+        if (need_ab && A.x[v] == nullptr) return fail(-7, "qd Rgemm: a plane of A is NULL");
+        if (need_ab && B.x[v] == nullptr) return fail(-9, "qd Rgemm: a plane of B is NULL");
+        if (m > 0 && n > 0 && C.x[v] == nullptr)
+            return fail(-12, "qd Rgemm: a plane of C is NULL");
+    }
+    const bool beta_one = beta.x[0] == 1.0 && beta.x[1] == 0.0 && beta.x[2] == 0.0 &&
+                          beta.x[3] == 0.0;
+    if (m == 0 || n == 0 || ((alpha_zero || k == 0) && beta_one)) return 0;
+    int rc = require_device();
+    if (rc) return rc;
+    return run_qd_gemm(ta, tb, m, n, k, alpha.x, A.x, lda, B.x, ldb, beta.x, C.x, ldc,
+                       tls().stream);
+}
+
 int mp_dd_Rsyr2k(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
                  mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
                  mp_dd_mat C, int64_t ldc) {

@@ -469,9 +469,9 @@ int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp
 // lower), update A22 -= L21 U12 (the plain dd Rgemm kernel, or a
 // one-thread-per-entry kernel when k or n is small), factor A22
 // (recursively).  A single column is a leaf: one CTA finds the pivot (the
-// first row of largest |A(i, j)|, compared as dd values), records it,
-// interchanges the two rows across the whole matrix and forms the
-// multipliers.  dgetrf2 applies each half's interchanges to the other half
+// first row of largest |A(i, j)|, compared as dd values) and records it,
+// then a second launch interchanges the two rows across the whole matrix
+// and forms the multipliers, spread over CTAs.  dgetrf2 applies each half's interchanges to the other half
 // as a block afterwards; swapping whole rows at the leaf gives the same
 // matrix, because nothing reads or writes the other half in between, and
 // needs no sequential interchange passes.  The top-level updates are large
@@ -504,18 +504,16 @@ __device__ __forceinline__ bool better(const PivotKey &b, const PivotKey &a) {
     return b.row < a.row;
 }
 
-// Column j (global) of A, rows [j, m): pivot search, interchange of rows j
-// and p across all n columns of A, and the multipliers below the diagonal
-// (as LAPACK's dgetf2: one dd reciprocal of the pivot, then a product per
-// entry; a division per entry when the pivot is below 2^-1021, where the
-// reciprocal could overflow).
-__global__ void __launch_bounds__(LT) getrf_column_kernel(double *ah, double *al, int64_t lda,
-                                                          int64_t m, int64_t n, int64_t j,
-                                                          int64_t *ipiv, int64_t *info) {
+// Column j (global) of A, rows [j, m), in two launches.
+//
+// getrf_pivot_kernel (one CTA): the pivot row p, ipiv[j] = p + 1, and the
+// interchange of the two entries of column j; a zero pivot records info and
+// changes nothing (LAPACK: no interchange, no scaling).
+__global__ void __launch_bounds__(LT) getrf_pivot_kernel(double *ah, double *al, int64_t lda,
+                                                         int64_t m, int64_t j, int64_t *ipiv,
+                                                         int64_t *info) {
     __shared__ PivotKey wk[LT / 32];
-    __shared__ int64_t piv_row;
-    __shared__ double ph, pl, rh, rl;
-    const double *ch = ah + j * lda, *cl = al + j * lda;
+    double *ch = ah + j * lda, *cl = al + j * lda;
     PivotKey best{0, 0.0, -1};
     for (int64_t i = j + threadIdx.x; i < m; i += LT) {
         const PivotKey c = pivot_key(ch[i], cl[i], i);
@@ -530,49 +528,58 @@ __global__ void __launch_bounds__(LT) getrf_column_kernel(double *ah, double *al
     }
     if (lane == 0) wk[warp] = best;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < LT / 32; ++w)
-            if (better(wk[w], best)) best = wk[w];
-        const int64_t p = best.row;
-        ipiv[j] = p + 1;
-        piv_row = p;
-        ph = ch[p];
-        pl = cl[p];
-        if (ph == 0.0 && pl == 0.0) {
-            atomicCAS(reinterpret_cast<unsigned long long *>(info), 0ull,
-                      (unsigned long long)(j + 1));
-        } else if (fabs(ph) >= 0x1p-1021) {
-            const dd r = div(dd{1.0, 0.0}, dd{ph, pl});
-            rh = r.hi;
-            rl = r.lo;
-        }
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < LT / 32; ++w)
+        if (better(wk[w], best)) best = wk[w];
+    const int64_t p = best.row;
+    ipiv[j] = p + 1;
+    const double ph = ch[p], pl = cl[p];
+    if (ph == 0.0 && pl == 0.0) {
+        atomicCAS(reinterpret_cast<unsigned long long *>(info), 0ull, (unsigned long long)(j + 1));
+        return;
     }
-    __syncthreads();
-    if (ph == 0.0 && pl == 0.0) return;   // LAPACK: no interchange, no scaling
-    const int64_t p = piv_row;
     if (p != j) {
-        for (int64_t c = threadIdx.x; c < n; c += LT) {
-            const int64_t oj = j + c * lda, op = p + c * lda;
-            const double th = ah[oj], tl = al[oj];
-            ah[oj] = ah[op]; al[oj] = al[op];
-            ah[op] = th; al[op] = tl;
-        }
+        ch[p] = ch[j]; cl[p] = cl[j];
+        ch[j] = ph; cl[j] = pl;
+    }
+}
+
+// getrf_apply_kernel: with the pivot in place at A(j, j), CTAs [0, col_ctas)
+// interchange rows j and p in every other column of A (one column per
+// thread), the rest form the multipliers of column j below the diagonal, as
+// LAPACK's dgetf2 does: one dd reciprocal of the pivot per CTA, then a product
+// per entry (a division per entry when the pivot is below 2^-1021, where the
+// reciprocal could overflow).  Column j's entries are read and written by
+// one thread each, so the two roles never touch the same entry.
+__global__ void __launch_bounds__(LT) getrf_apply_kernel(double *ah, double *al, int64_t lda,
+                                                         int64_t m, int64_t n, int64_t j,
+                                                         const int64_t *ipiv, int col_ctas) {
+    __shared__ double rh, rl;
+    const double ph = ah[j + j * lda], pl = al[j + j * lda];
+    if (ph == 0.0 && pl == 0.0) return;   // zero pivot: nothing to apply
+    const int64_t p = ipiv[j] - 1;
+    if ((int)blockIdx.x < col_ctas) {
+        const int64_t c = (int64_t)blockIdx.x * LT + threadIdx.x;
+        if (p == j || c >= n || c == j) return;
+        const int64_t oj = j + c * lda, op = p + c * lda;
+        const double th = ah[oj], tl = al[oj];
+        ah[oj] = ah[op]; al[oj] = al[op];
+        ah[op] = th; al[op] = tl;
+        return;
+    }
+    const bool recip = fabs(ph) >= 0x1p-1021;
+    if (threadIdx.x == 0 && recip) {
+        const dd r = div(dd{1.0, 0.0}, dd{ph, pl});
+        rh = r.hi;
+        rl = r.lo;
     }
     __syncthreads();
+    const int64_t i = j + 1 + (int64_t)(blockIdx.x - col_ctas) * LT + threadIdx.x;
+    if (i >= m) return;
     double *wh = ah + j * lda, *wl = al + j * lda;
-    if (fabs(ph) >= 0x1p-1021) {
-        const dd r{rh, rl};
-        for (int64_t i = j + 1 + threadIdx.x; i < m; i += LT) {
-            dd v = mul(dd{wh[i], wl[i]}, r);
-            wh[i] = v.hi; wl[i] = v.lo;
-        }
-    } else {
-        const dd pv{ph, pl};
-        for (int64_t i = j + 1 + threadIdx.x; i < m; i += LT) {
-            dd v = div(dd{wh[i], wl[i]}, pv);
-            wh[i] = v.hi; wl[i] = v.lo;
-        }
-    }
+    const dd v = recip ? mul(dd{wh[i], wl[i]}, dd{rh, rl}) : div(dd{wh[i], wl[i]}, dd{ph, pl});
+    wh[i] = v.hi;
+    wl[i] = v.lo;
 }
 
 // Row interchanges ipiv[k0 .. k1) (one-based global rows, applied in order)
@@ -636,9 +643,14 @@ int getrf_rec(const LuPlan &P, int64_t j0, int64_t n) {
     if (n <= 0 || rows <= 0) return 0;
     int rc;
     if (n == 1) {
-        getrf_column_kernel<<<1, LT, 0, P.st>>>(P.ah, P.al, P.lda, P.m, P.n, j0, P.ipiv,
-                                                P.info);
-        return check_launch("getrf_column_kernel");
+        getrf_pivot_kernel<<<1, LT, 0, P.st>>>(P.ah, P.al, P.lda, P.m, j0, P.ipiv, P.info);
+        if ((rc = check_launch("getrf_pivot_kernel"))) return rc;
+        const int col_ctas = (int)ceil_div(P.n, LT);
+        const int row_ctas = (int)ceil_div(P.m - j0 - 1, LT);
+        if (col_ctas + row_ctas == 0) return 0;
+        getrf_apply_kernel<<<col_ctas + row_ctas, LT, 0, P.st>>>(P.ah, P.al, P.lda, P.m, P.n, j0,
+                                                                 P.ipiv, col_ctas);
+        return check_launch("getrf_apply_kernel");
     }
     const int64_t mn = rows < n ? rows : n;
     const int64_t n1 = mn / 2 > 0 ? mn / 2 : 1, n2 = n - n1;

@@ -83,6 +83,11 @@ size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k);
 int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *offsets, int *count);
 int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+// Quad-double Rgemm (four planes per matrix, four components per scalar).
+int run_qd_gemm(int ta, int tb, int64_t m, int64_t n, int64_t k, const double *alpha,
+                const double *const *a, int64_t lda, const double *const *b, int64_t ldb,
+                const double *beta, double *const *c, int64_t ldc, cudaStream_t stream);
+
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();
 int run_sliced_noalloc(const GemmArgs &p, int slices, cudaStream_t stream);

@@ -70,3 +70,24 @@ def is_normalised(hi, lo) -> bool:
 
 def frac_diff(a, b):
     return abs(Fraction(a[0]) + Fraction(a[1]) - Fraction(b[0]) - Fraction(b[1]))
+
+
+EPS_QD = 2.0 ** -209   # Rlamch epsilon of qd_real
+
+
+def qd_bound_entries(transa, transb, m, n, k, alpha, A, B, beta, C, rows, cols):
+    """4 k 2^-209 (|alpha||A||B| + |beta||C|) at the given entries, from the
+    leading components (the dd bound helper scaled to the qd epsilon)."""
+    return gemm_bound_entries(transa, transb, m, n, k, alpha[:2], (A[0], A[1]), (B[0], B[1]),
+                              beta[:2], None if C is None else (C[0], C[1]), rows,
+                              cols) * (EPS_QD / EPS_DD)
+
+
+def qd_is_normalised(comps) -> bool:
+    """|x_{t+1}| <= ulp(x_t) / 2 for every entry (zero tails after a zero)."""
+    x = [np.asarray(c, dtype=np.float64) for c in comps]
+    for t in range(3):
+        half_ulp = np.where(x[t] == 0, 0.0, np.spacing(np.abs(x[t])) / 2)
+        if (np.abs(x[t + 1]) > half_ulp).any():
+            return False
+    return True
