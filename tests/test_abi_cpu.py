@@ -27,7 +27,7 @@ def mp():
 def header_functions():
     txt = open(os.path.join(ROOT, "include", "mpdd.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(mp_dd_\w+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(mp_(?:dd|qd)_\w+)\s*\(", txt)))
 
 
 def test_library_exports_every_declared_symbol(mp):
