@@ -44,6 +44,12 @@ UNIT = "dd-GFlop/s"
 NOMINAL_FP64_INSTR = 1.25e12 / 2
 FP64_OPS_PER_MAC = 12.75
 QD_OPS_PER_MAC = 117.5   # qd multiply-add: 113 FP64 operations + 4.5 for the level pass
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, from single ncu
+# captures of the current kernels (the summaries under profiles/ give the
+# commands): the plain Rgemm NN launch at 4096 and the band kernel of the
+# CRT form at 8192
+PLAIN_NN_4096_DRAM_BYTES = 3626772736 + 278080000
+BAND_CRT_8192_DRAM_BYTES = 44417327360 + 2282471424
 
 
 def parse():
@@ -229,7 +235,9 @@ def run_ours(args):
         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 625 G FP64 instr/s (derived)",
         "peak_measured_fp64_microbench": (peak_fp64 / 1e9) if peak_fp64 else None,
         "frac_of_measured": (achieved / (peak_fp64 / 1e9)) if peak_fp64 else None,
-        "traffic": None,
+        # DRAM bytes of one Rgemm NN launch at 4096 from one ncu capture of
+        # this kernel (profiles/dd_gemm_plain_4096.md); None at other sizes
+        "traffic": PLAIN_NN_4096_DRAM_BYTES if size == 4096 else None,
         "fp64_instr_per_dd_mac": FP64_OPS_PER_MAC,
     }
     e2e = None
@@ -448,7 +456,8 @@ def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=F
                                  "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                  "frac": achieved / peak, "peak_source": src,
                                  "algorithmic_flops": band_flops,
-                                 "traffic": None},
+                                 "traffic": (BAND_CRT_8192_DRAM_BYTES
+                                             if form == "crt" and size == 8192 else None)},
     }
     if compare_plain:
         # the plain FP64 path on the same inputs, and their agreement measured
@@ -680,14 +689,14 @@ def run_sliced_workload(args):
                    "l2": f"inputs {3 * mat / 1e6:.0f} MB > 129 MB L2, no flush"},
         "roofline": {"bound": "tensor", "kernel": "band_gemm_kernel", "achieved": ach,
                      "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "peak_source": src,
-                     "traffic": None},
+                     "traffic": BAND_CRT_8192_DRAM_BYTES if crt and size == 8192 else None},
         "phase_ms": {"scale_and_split": band[-1][0], "tensor_products": band[-1][1],
                      "recombine_epilogue": band[-1][2]},
         "e2e": {"value": 2.0 * size ** 3 * n_e2e / dt / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 3 * mat, "d2h_bytes_per_step": mat,
                 "api": "Python binding mp_dd_Rgemm_" + ("crt" if crt else "sliced") +
                        ", pinned host buffers"},
-        "gpu_launches": 7 * args.steps, "clocks": clocks,
+        "gpu_launches": 6 * args.steps, "clocks": clocks,  # maxima x2, split x2, products, recombination
     }
     print(json.dumps(line), flush=True)
 
