@@ -47,9 +47,9 @@ QD_OPS_PER_MAC = 117.5   # qd multiply-add: 113 FP64 operations + 4.5 for the le
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, from single ncu
 # captures of the current kernels (the summaries under profiles/ give the
 # commands): the plain Rgemm NN launch at 4096 and the band kernel of the
-# CRT form at 8192
+# CRT form at 8192 (None: not captured since the kernel last changed)
 PLAIN_NN_4096_DRAM_BYTES = 3626772736 + 278080000
-BAND_CRT_8192_DRAM_BYTES = 44417327360 + 2282471424
+BAND_CRT_8192_DRAM_BYTES = None
 
 
 def parse():
@@ -74,6 +74,54 @@ def parse():
 # ----------------------------------------------------------------------------
 # workload: plain dd Rgemm NN + Rgemm TN + Rsyrk UN
 # ----------------------------------------------------------------------------
+
+class Ranks:
+    """One replica per rank under torchrun (RANK / WORLD_SIZE / LOCAL_RANK
+    from the environment): the process group, a barrier, the maximum of a
+    timing over ranks and the whole-job value.  Every workload here is a set
+    of independent problems, so ranks exchange only these scalars."""
+
+    def __init__(self, backend: str | None = None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.device = "cpu"
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if not dist.is_initialized():
+                dist.init_process_group(backend)
+            self.dist = dist
+            self.device = f"cuda:{self.local}" if backend == "nccl" else "cpu"
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        """The largest x over all ranks (every rank gets it)."""
+        if self.dist is None:
+            return float(x)
+        import torch
+
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def whole_job(self, units_per_rank: float, seconds_max: float) -> float:
+        """Units processed by all ranks per second of the slowest rank."""
+        return self.world * units_per_rank / seconds_max
+
+    def close(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
 
 def plain_problems(size: int):
     """The step's three problems as host (numpy) data."""
@@ -153,14 +201,11 @@ class ClockSampler:
 
 def run_ours(args):
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    ranks = Ranks()
+    world, rank = ranks.world, ranks.rank
     import paper_2109_13406_gb300 as mp
 
     size = args.size
@@ -197,8 +242,7 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     peak_fp64 = mp.mp_dd_peak_fp64() if rank == 0 else None
-    if world > 1:
-        dist.barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
@@ -209,17 +253,10 @@ def run_ours(args):
     t1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        ms = float(tt.item())
-        if world > 1 and rank == 0:
-            pass
+    ms = ranks.max(t0.elapsed_time(t1))
     flops = plain_flops(size)
     step_flops = sum(flops.values())
-    value = world * step_flops * args.steps / (ms * 1e-3) / 1e9
+    value = ranks.whole_job(step_flops * args.steps, ms * 1e-3) / 1e9
     per = {}
     for nm in names:
         t = [a.elapsed_time(b) for a, b in ev[nm]]
@@ -242,7 +279,7 @@ def run_ours(args):
     }
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, mp, torch, nn, tn, syrk, world)
+        e2e = run_e2e(args, mp, torch, nn, tn, syrk, ranks)
     sliced = None
     if not args.no_sliced:
         del dnn, dtn, dsy
@@ -280,8 +317,7 @@ def run_ours(args):
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def _event_ms(torch, st, fn, reset=None, reps=2):
@@ -486,7 +522,7 @@ def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=F
     return out
 
 
-def run_e2e(args, mp, torch, nn, tn, syrk, world):
+def run_e2e(args, mp, torch, nn, tn, syrk, ranks):
     """The same step through the host-buffer entry points (pinned host
     memory), host<->device copies inside the timed region."""
     size = args.size
@@ -512,16 +548,17 @@ def run_e2e(args, mp, torch, nn, tn, syrk, world):
 
     step()
     torch.cuda.synchronize()
+    ranks.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    dt = ranks.max(time.perf_counter() - t0)
     per_mat = 16 * size * size
     h2d = 2 * 3 * per_mat + 2 * per_mat      # two GEMMs (A, B, C) + Rsyrk (A, C)
     d2h = 3 * per_mat
     flops = sum(plain_flops(size).values())
-    return {"value": world * flops * steps / dt / 1e9, "unit": UNIT,
+    return {"value": ranks.whole_job(flops * steps, dt) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
             "api": "mp_dd_Rgemm_host / mp_dd_Rsyrk_host (pinned host buffers)"}
 
@@ -601,6 +638,7 @@ def run_sliced_workload(args):
     import torch
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
     import paper_2109_13406_gb300 as mp
 
     size, S = args.sliced_size, 14
@@ -626,21 +664,26 @@ def run_sliced_workload(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    ranks.barrier()
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    band = []
     t0.record(st)
     for _ in range(args.steps):
+        step()
+    t1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ranks.max(t0.elapsed_time(t1))
+    value = ranks.whole_job(2.0 * size ** 3 * args.steps, ms * 1e-3) / 1e9
+    # per-phase times (the library's own events) from two more calls after
+    # the timed region
+    band = []
+    for _ in range(2):
         mp.mp_dd_sliced_timing(True)
         step()
         band.append(mp.mp_dd_sliced_phase_ms())
-    t1.record(st)
-    torch.cuda.synchronize()
     mp.mp_dd_sliced_timing(False)
-    clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
-    value = 2.0 * size ** 3 * args.steps / (ms * 1e-3) / 1e9
     if crt:
         L = mp.mp_dd_crt_layout(size, size, size)
         products = len(L["moduli"])
@@ -669,17 +712,19 @@ def run_sliced_workload(args):
 
     e2e_step()
     torch.cuda.synchronize()
+    ranks.barrier()
     tt = time.perf_counter()
     n_e2e = max(1, min(args.steps, 3))
     for _ in range(n_e2e):
         e2e_step()
     torch.cuda.synchronize()
-    dt = time.perf_counter() - tt
+    dt = ranks.max(time.perf_counter() - tt)
     mat = 16 * size * size
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16 tensor (exact integer slices) + i64",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ranks.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 tensor (exact integer slices) + i64",
         "data": "synthetic (seeded PCG64; dd entries hi~U(-1,1), lo=hi*2^-53*U(-1,1) "
                 "renormalised; alpha,beta random dd in [0.5,2])",
         "config": {"workload": (f"split-precision dd Rgemm NN m=n=k={size}, " +
@@ -692,13 +737,15 @@ def run_sliced_workload(args):
                      "traffic": BAND_CRT_8192_DRAM_BYTES if crt and size == 8192 else None},
         "phase_ms": {"scale_and_split": band[-1][0], "tensor_products": band[-1][1],
                      "recombine_epilogue": band[-1][2]},
-        "e2e": {"value": 2.0 * size ** 3 * n_e2e / dt / 1e9, "unit": UNIT,
+        "e2e": {"value": ranks.whole_job(2.0 * size ** 3 * n_e2e, dt) / 1e9, "unit": UNIT,
                 "h2d_bytes_per_step": 3 * mat, "d2h_bytes_per_step": mat,
                 "api": "Python binding mp_dd_Rgemm_" + ("crt" if crt else "sliced") +
                        ", pinned host buffers"},
         "gpu_launches": 6 * args.steps, "clocks": clocks,  # maxima x2, split x2, products, recombination
     }
-    print(json.dumps(line), flush=True)
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def grouped_problems_host(count: int, seed: int = 0):
@@ -716,6 +763,7 @@ def run_grouped_workload(args):
     import torch
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
     import paper_2109_13406_gb300 as mp
     from paper_2109_13406_gb300 import grouped as gr
 
@@ -732,6 +780,7 @@ def run_grouped_workload(args):
     for _ in range(args.warmup):
         G.replay()
     torch.cuda.synchronize()
+    ranks.barrier()
     st = torch.cuda.current_stream()
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
@@ -742,7 +791,7 @@ def run_grouped_workload(args):
     e1.record(st)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = ranks.max(e0.elapsed_time(e1)) / args.steps
     # per-problem launch loop on the same problems
     l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0.record(st)
@@ -766,7 +815,8 @@ def run_grouped_workload(args):
     nbytes = sum(16.0 * (c.m * c.k + c.k * c.n + 2 * c.m * c.n) for c in cases)
     achieved = FP64_OPS_PER_MAC * macs / (ms * 1e-3) / 1e9
     line = {
-        "metric": METRIC, "value": flops / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+        "metric": METRIC, "value": ranks.whole_job(flops, ms * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": ranks.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; m,n,k log-uniform integers in [16,512], NN, random dd "
@@ -788,7 +838,9 @@ def run_grouped_workload(args):
         "autotune_seconds": t_tune,
         "gpu_launches": 2 * args.steps, "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def spd_request_device(seed: int, n: int, nrhs: int = 4, smin: float = 1e-10):
@@ -836,6 +888,7 @@ def run_served_workload(args):
     import torch
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
     import paper_2109_13406_gb300 as mp
     from paper_2109_13406_gb300 import grouped as gr
     from paper_2109_13406_gb300.server import Request, SpdServer
@@ -862,14 +915,18 @@ def run_served_workload(args):
     arrivals = datagen.poisson_arrivals(0, args.requests, rate)
     reqs = [req(i, n, a) for i, (n, a) in enumerate(zip(sizes, arrivals))]
     srv = SpdServer(budget_bytes=120e9, slots=256, table=table)
+    ranks.barrier()
     clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clk.start()
     t0 = time.perf_counter()
     done = srv.serve(reqs)
-    wall = time.perf_counter() - t0
+    wall = ranks.max(time.perf_counter() - t0)
     clocks = clk.stop()
     lat = np.array([(r.done_t - r.arrival) * 1e3 for r in done])
-    makespan = max(r.done_t for r in done)
+    makespan = ranks.max(max(r.done_t for r in done))
+    # each replica serves its own copy of the stream: latencies are those of
+    # the slowest replica, throughput adds up
+    p50, p99 = (ranks.max(float(np.percentile(lat, q))) for q in (50, 99))
     flops = sum(r.flops() for r in done)
     # residual ratios on a size-stratified sample
     order = sorted(done, key=lambda r: r.n)
@@ -888,8 +945,8 @@ def run_served_workload(args):
         ratios.append({"n": n, "ratio": residual_ratio(Fs, r.X, (mp.to_numpy(bh),
                                                                  mp.to_numpy(bl)), mp)})
     line = {
-        "metric": METRIC, "value": float(np.percentile(lat, 99)), "unit": "ms (p99 latency)",
-        "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
+        "metric": METRIC, "value": p99, "unit": "ms (p99 latency)",
+        "n_gpus": ranks.world, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; G = U[diag(s) 0]V^T, s geometric 1..1e-10, Householder "
                 "orthogonal factors, generated on the device)",
@@ -898,15 +955,17 @@ def run_served_workload(args):
                                "120 GB budget, 256 slots",
                    "arrival_rate_per_s": rate, "offered_load": args.load,
                    "solo_rate_solves_per_s": solo_rate},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "mean_ms": float(lat.mean()), "solves_per_s": len(done) / makespan,
-        "dd_GFlops": flops / makespan / 1e9, "scheduler_steps": srv.steps,
+        "p50_ms": p50, "p99_ms": p99,
+        "mean_ms": float(lat.mean()), "solves_per_s": ranks.whole_job(len(done), makespan),
+        "dd_GFlops": ranks.whole_job(flops, makespan) / 1e9, "scheduler_steps": srv.steps,
         "launches": srv.launches, "max_concurrent": srv.max_active,
         "all_info_zero": all(r.info == 0 for r in done),
         "residual_ratio_sample": ratios, "clocks": clocks,
         "gpu_launches": srv.launches,
     }
-    print(json.dumps(line), flush=True)
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def main():

@@ -48,40 +48,37 @@ __host__ __device__ constexpr int modulus(int i) {
     return m[i];
 }
 
-// 256^(kDigits-1-t) mod (p_{2j} p_{2j+1}) for the moduli pairs (products < 2^16).
-struct PairWeights {
-    int w[kMaxMod / 2][kDigits];
+// 256^(kDigits-1-t) mod p_i as exact floats (< 256), and 1/p_i.
+struct ModWeights {
+    float w[kMaxMod][kDigits];
+    float inv[kMaxMod];
 };
 
-constexpr PairWeights make_pair_weights() {
-    PairWeights pw{};
-    for (int j = 0; j < kMaxMod / 2; ++j) {
-        const long long m = (long long)modulus(2 * j) * modulus(2 * j + 1);
-        long long v = 1;
+constexpr ModWeights make_mod_weights() {
+    ModWeights mw{};
+    for (int i = 0; i < kMaxMod; ++i) {
+        const int p = modulus(i);
+        int v = 1;
         for (int t = kDigits - 1; t >= 0; --t) {
-            pw.w[j][t] = (int)v;
-            v = (v * 256) % m;
+            mw.w[i][t] = (float)v;
+            v = (v * 256) % p;
         }
+        mw.inv[i] = 1.0f / (float)p;
     }
-    return pw;
+    return mw;
 }
 
-__constant__ PairWeights c_pair_weights = make_pair_weights();
+__constant__ ModWeights c_mod_weights = make_mod_weights();
 
-__device__ __forceinline__ int sym_mod(int v, int p) {
-    int r = v % p;
-    if (r < 0) r += p;
-    return r > (p - 1) / 2 ? r - p : r;   // [-floor(p/2), ceil(p/2) - 1]
-}
-
-__device__ __forceinline__ uint16_t half_bits(int r) {   // fp16 of r in [-512, 511]
-    __half x = __hsub(__ushort_as_half((unsigned short)(0x6600 + r)), __float2half(1536.0f));
-    return __half_as_ushort(x);
-}
-
-// 4 threads per (row, 16 consecutive k), 4 entries each; residues of the
-// NP moduli pairs, one 8-byte store per plane and thread (a quad of lanes
-// writes one 32-byte sector).
+// 4 threads per (row, 16 consecutive k), 4 entries each, one 8-byte store
+// per residue plane and thread (a quad of lanes writes one 32-byte sector).
+// Residues from the balanced digits d_t of X on the FP32 pipe:
+// s = sum_t d_t (256^(13-t) mod p) is an integer below 14 * 128 * 255 < 2^24,
+// so every partial sum is exact in fp32, and r = s - p rint(s / p) is the
+// residue in [-(p-1)/2, (p-1)/2] for odd p: the fp32 quotient is within
+// |s / p| 2^-23 < 1e-3 of s / p, while s / p, an integer over an odd p, is
+// never within 1 / (2 p) > 0.0019 of a half-integer.  For p = 256 the
+// lowest digit, in [-128, 127], is the residue.
 template <int NP>
 __global__ void __launch_bounds__(128) residue_kernel(
     const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
@@ -92,7 +89,8 @@ __global__ void __launch_bounds__(128) residue_kernel(
     const int64_t l0 = (int64_t)blockIdx.y * 16 + 4 * (threadIdx.x & 3);
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
     const int shift = 8 * kDigits - e;
-    int dg[4][kDigits];
+    float df[4][kDigits];
+    uint32_t low[2] = {0u, 0u};   // plane 0: the lowest digits as fp16
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t l = l0 + q;
@@ -102,30 +100,29 @@ __global__ void __launch_bounds__(128) residue_kernel(
             hi = Xh[off];
             lo = Xl[off];
         }
-        dd_digits<kDigits>(hi, lo, shift, dg[q]);
-    }
+        int dg[kDigits];
+        dd_digits<kDigits>(hi, lo, shift, dg);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        const int p0 = modulus(2 * j), p1 = modulus(2 * j + 1);
-        uint32_t w0[2], w1[2];
+        for (int t = 0; t < kDigits; ++t) df[q][t] = (float)dg[t];
+        const uint32_t h = __half_as_ushort(__float2half_rn((float)dg[kDigits - 1]));
+        low[q / 2] |= (q & 1) ? h << 16 : h;
+    }
+    *reinterpret_cast<uint2 *>(R + r * k_pad + l0) = make_uint2(low[0], low[1]);
+#pragma unroll
+    for (int i = 1; i < 2 * NP; ++i) {
+        const float p = (float)modulus(i), inv = c_mod_weights.inv[i];
+        uint32_t w[2] = {0u, 0u};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int s = 0;
+            float s = 0.0f;
 #pragma unroll
-            for (int t = 0; t < kDigits; ++t) s += dg[q][t] * c_pair_weights.w[j][t];
-            const int rr = s % (p0 * p1);   // keeps the residues of both moduli
-            const uint32_t h0 = half_bits(sym_mod(rr, p0)), h1 = half_bits(sym_mod(rr, p1));
-            if (q & 1) {
-                w0[q / 2] |= h0 << 16;
-                w1[q / 2] |= h1 << 16;
-            } else {
-                w0[q / 2] = h0;
-                w1[q / 2] = h1;
-            }
+            for (int t = 0; t < kDigits; ++t) s = __fmaf_rn(df[q][t], c_mod_weights.w[i][t], s);
+            const float res = __fmaf_rn(-p, rintf(__fmul_rn(s, inv)), s);
+            const uint32_t h = __half_as_ushort(__float2half_rn(res));
+            w[q / 2] |= (q & 1) ? h << 16 : h;
         }
-        uint2 v0 = make_uint2(w0[0], w0[1]), v1 = make_uint2(w1[0], w1[1]);
-        *reinterpret_cast<uint2 *>(R + ((int64_t)(2 * j) * rows_pad + r) * k_pad + l0) = v0;
-        *reinterpret_cast<uint2 *>(R + ((int64_t)(2 * j + 1) * rows_pad + r) * k_pad + l0) = v1;
+        *reinterpret_cast<uint2 *>(R + ((int64_t)i * rows_pad + r) * k_pad + l0) =
+            make_uint2(w[0], w[1]);
     }
 }
 
@@ -150,10 +147,11 @@ struct CrtArgs {
 
 // Word idx of a little-endian multiword value, without dynamic indexing
 // (which would move the array to local memory).
-__device__ __forceinline__ uint32_t word_at(const uint32_t (&v)[kWords], int idx) {
+template <int NW>
+__device__ __forceinline__ uint32_t word_at(const uint32_t (&v)[NW], int idx) {
     uint32_t r = 0;
 #pragma unroll
-    for (int t = 0; t < kWords; ++t) r = (t == idx) ? v[t] : r;
+    for (int t = 0; t < NW; ++t) r = (t == idx) ? v[t] : r;
     return r;
 }
 
@@ -173,15 +171,16 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
 // Round the magnitude v (little-endian 32-bit words) to the nearest binary64
 // (ties to even) times 2^scale.  rem receives the exact remainder v - RN(v)
 // as a magnitude, rem_neg its sign.
-__device__ __forceinline__ double round_words(const uint32_t (&v)[kWords], int scale,
-                                              uint32_t (&rem)[kWords], bool &rem_neg) {
+template <int NW>
+__device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale,
+                                              uint32_t (&rem)[NW], bool &rem_neg) {
     int top = -1;
 #pragma unroll
-    for (int t = kWords - 1; t >= 0; --t)
+    for (int t = NW - 1; t >= 0; --t)
         if (top < 0 && v[t] != 0) top = t;
     rem_neg = false;
 #pragma unroll
-    for (int t = 0; t < kWords; ++t) rem[t] = 0;
+    for (int t = 0; t < NW; ++t) rem[t] = 0;
     if (top < 0) return 0.0;
     const int msb = 32 * top + (31 - __clz(word_at(v, top)));
     if (msb <= 52) {
@@ -196,7 +195,7 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[kWords], int s
     const int hw = (q - 1) / 32, hb = (q - 1) % 32;
     bool gt = false, eq = true;
 #pragma unroll
-    for (int t = kWords - 1; t >= 0; --t) {
+    for (int t = NW - 1; t >= 0; --t) {
         uint32_t word = v[t];
         word = (t > w) ? 0u : (t == w ? (b ? (word & ((1u << b) - 1)) : 0u) : word);
         rem[t] = word;
@@ -211,7 +210,7 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[kWords], int s
         rem_neg = true;
         uint64_t borrow = 0;
 #pragma unroll
-        for (int t = 0; t < kWords; ++t) {
+        for (int t = 0; t < NW; ++t) {
             const uint64_t bit = (t == w) ? (1ull << b) : 0ull;
             const uint64_t d = bit - (uint64_t)rem[t] - borrow;
             rem[t] = (uint32_t)d;
@@ -221,24 +220,36 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[kWords], int s
     return scale_pow2(__ull2double_rn(mant), q + scale);   // mant <= 2^53: exact
 }
 
+// NW: 32-bit words of the sums (P < 2^(32 (NW - 1)), and the sum of N
+// residues < 256 times the weights < P stays below 2^(32 NW)).
+template <int NW>
 __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
     const int64_t total = p.m * p.n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx % p.m, j = idx / p.m;
-        // S = sum_b c_b w_b with 64-bit column sums, then carries
-        uint64_t acc[kWords];
+        // S = sum_b c_b w_b with 64-bit column sums, then carries; the
+        // products are read 8 moduli at a time, the 8 loads in flight together
+        const uint8_t *res = p.res + j * p.m_pad + i;
+        const int64_t plane = p.n_pad * p.m_pad;
+        uint64_t acc[NW];
 #pragma unroll
-        for (int t = 0; t < kWords; ++t) acc[t] = 0;
-        for (int b = 0; b < p.N; ++b) {
-            const uint32_t c = p.res[((int64_t)b * p.n_pad + j) * p.m_pad + i];
+        for (int t = 0; t < NW; ++t) acc[t] = 0;
+        for (int b0 = 0; b0 < p.N; b0 += 8) {
+            uint32_t cv[8];
 #pragma unroll
-            for (int t = 0; t < kWords; ++t) acc[t] += (uint64_t)c * p.w[b][t];
+            for (int u = 0; u < 8; ++u) cv[u] = b0 + u < p.N ? res[(b0 + u) * plane] : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + u < p.N ? b0 + u : 0;   // cv[u] = 0 past N
+#pragma unroll
+                for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * p.w[b][t];
+            }
         }
-        uint32_t S[kWords];
+        uint32_t S[NW];
         uint64_t carry = 0;
 #pragma unroll
-        for (int t = 0; t < kWords; ++t) {
+        for (int t = 0; t < NW; ++t) {
             const uint64_t v = acc[t] + carry;
             S[t] = (uint32_t)v;
             carry = v >> 32;
@@ -249,11 +260,11 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
                           (float)word_at(S, p.ptop) + (float)word_at(S, p.ptop - 1) * 2.3283064e-10f;
         int64_t qest = (int64_t)floorf(s_f / p.p_f);
         if (qest < 0) qest = 0;
-        // S -= qest * P (two's complement over kWords words)
+        // S -= qest * P (two's complement over NW words)
         {
             uint64_t borrow = 0, mc = 0;
 #pragma unroll
-            for (int t = 0; t < kWords; ++t) {
+            for (int t = 0; t < NW; ++t) {
                 const uint64_t prod = (uint64_t)qest * p.P[t] + mc;
                 mc = prod >> 32;
                 const uint64_t d = (uint64_t)S[t] - (uint32_t)prod - borrow;
@@ -263,12 +274,12 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
         }
         // correct into [0, P): at most a couple of steps either way
         for (int it = 0; it < 4; ++it) {
-            const bool neg = (S[kWords - 1] & 0x80000000u) != 0;
+            const bool neg = (S[NW - 1] & 0x80000000u) != 0;
             bool ge = false;
             if (!neg) {
                 bool eq = true;
 #pragma unroll
-                for (int t = kWords - 1; t >= 0; --t)
+                for (int t = NW - 1; t >= 0; --t)
                     if (eq && S[t] != p.P[t]) {
                         ge = S[t] > p.P[t];
                         eq = false;
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
             if (!neg && !ge) break;
             uint64_t c2 = 0;
 #pragma unroll
-            for (int t = 0; t < kWords; ++t) {
+            for (int t = 0; t < NW; ++t) {
                 uint64_t d = neg ? (uint64_t)S[t] + p.P[t] + c2
                                  : (uint64_t)S[t] - p.P[t] - c2;
                 S[t] = (uint32_t)d;
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
         {
             bool eq = true;
 #pragma unroll
-            for (int t = kWords - 1; t >= 0; --t)
+            for (int t = NW - 1; t >= 0; --t)
                 if (eq && S[t] != p.Phalf[t]) {
                     gt_half = S[t] > p.Phalf[t];
                     eq = false;
@@ -300,7 +311,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
         if (gt_half) {            // magnitude P - S
             uint64_t b2 = 0;
 #pragma unroll
-            for (int t = 0; t < kWords; ++t) {
+            for (int t = 0; t < NW; ++t) {
                 const uint64_t d = (uint64_t)p.P[t] - S[t] - b2;
                 S[t] = (uint32_t)d;
                 b2 = (d >> 63) & 1;
@@ -308,7 +319,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
             negative = true;
         }
         const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * 8 * kDigits;
-        uint32_t rem[kWords], rem2[kWords];
+        uint32_t rem[NW], rem2[NW];
         bool rem_neg, unused;
         double vh = round_words(S, sc, rem, rem_neg);
         double vl = round_words(rem, sc, rem2, unused);
@@ -397,10 +408,20 @@ struct CrtLayout {
 
 size_t align1k(size_t x) { return (x + 1023) / 1024 * 1024; }
 
+// Tile width of the residue products: 256 (a quarter fewer operand bytes per
+// flop than 128) once the (modulus, tile) work items fill the SMs twice over
+// and the wider padding of n adds at most n / 8.
+int crt_band_tn(int64_t m, int64_t n, int N) {
+    const int64_t items = ceil_div(imax(m, 1), kBandTM) * ceil_div(imax(n, 1), 256) * N;
+    const int64_t pad256 = ceil_div(imax(n, 1), 256) * 256;
+    const int64_t pad128 = ceil_div(imax(n, 1), 128) * 128;
+    return (items >= 2 * 152 && (pad256 - pad128) * 8 <= imax(n, 1)) ? 256 : 128;
+}
+
 CrtLayout crt_layout(int64_t m, int64_t n, int64_t k) {
     CrtLayout L{};
     L.N = moduli_count(k);
-    const int TN = band_tn(m, n);
+    const int TN = crt_band_tn(m, n, L.N);
     L.m_pad = ceil_div(imax(m, 1), kBandTM) * kBandTM;
     L.n_pad = ceil_div(imax(n, 1), TN) * TN;
     L.k_pad = ceil_div(imax(k, 1), kBandTK) * kBandTK;
@@ -472,7 +493,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     if ((int64_t)L.N * L.m_pad > 0x7fffffffLL || (int64_t)L.N * L.n_pad > 0x7fffffffLL)
         return fail(MP_DD_ERR_TOO_LARGE, "matrix too large for the CRT path");
     if (p.alpha_zero) return launch_gemm_plain(p, st);
-    const int TN = band_tn(p.m, p.n);
+    const int TN = crt_band_tn(p.m, p.n, L.N);
 
     uint8_t *w = static_cast<uint8_t *>(ws);
     cudaError_t e = cudaMemsetAsync(w, 0, L.off_ra, st);
@@ -542,7 +563,11 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int64_t total = p.m * p.n;
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
-    crt_kernel<<<(unsigned)blocks, 256, 0, st>>>(ca);
+    const int nw = (int)P.size() + 1;
+    if (nw <= 8) crt_kernel<8><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    else if (nw == 9) crt_kernel<9><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    else if (nw == 10) crt_kernel<10><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    else crt_kernel<11><<<(unsigned)blocks, 256, 0, st>>>(ca);
     rc = check_launch("crt_kernel");
     sliced_timing_mark(3, st);
     return rc;

@@ -195,6 +195,24 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
     tm = local / gn;
 }
 
+// Work item -> output tile and the bands [b0, b1) it accumulates.  Digit
+// pairs (sliced form): one item per tile, all S bands, so each tile's int32
+// sums are finished in one visit.  Residues (diagonal mode): one item per
+// (modulus, tile) with the modulus slowest, so the CTAs resident at one time
+// share one modulus's operand panels in L2.
+__device__ __forceinline__ void item_coords(const BandArgs &p, int item, int num_tiles, int &tm,
+                                            int &tn, int &b0, int &b1) {
+    int tile = item;
+    b0 = 0;
+    b1 = p.S;
+    if (p.diag) {
+        b0 = item / num_tiles;
+        b1 = b0 + 1;
+        tile = item % num_tiles;
+    }
+    tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+}
+
 template <int TN>
 __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -240,7 +258,8 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     const uint32_t tmem = *tmem_holder;
 
     const int num_tiles = p.tiles_m * p.tiles_n;
-    const int KB = p.kb_count, S = p.S;
+    const int KB = p.kb_count;
+    const int num_items = p.diag ? num_tiles * p.S : num_tiles;
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -249,10 +268,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             prefetch_tmap(&tmB);
             uint32_t it = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-                int tm, tn;
-                tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
-                for (int b = 0; b < S && ok; ++b)
+            for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+                int tm, tn, b0, b1;
+                item_coords(p, item, num_tiles, tm, tn, b0, b1);
+                for (int b = b0; b < b1 && ok; ++b)
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
                         const int yb = (int)((p.diag ? b : b - t) * p.n_pad) + tn * TN;
@@ -287,8 +306,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             const uint32_t idesc = idesc_f16_f32(TM, TN);
             uint32_t it = 0, chunk = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-                for (int b = 0; b < S && ok; ++b) {
+            for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+                int tm, tn, b0, b1;
+                item_coords(p, item, num_tiles, tm, tn, b0, b1);
+                for (int b = b0; b < b1 && ok; ++b) {
                     const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t)
@@ -341,10 +362,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t chunk = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-            int tm, tn;
-            tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
-            for (int b = 0; b < S && ok; ++b) {
+        for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+            int tm, tn, b0, b1;
+            item_coords(p, item, num_tiles, tm, tn, b0, b1);
+            for (int b = b0; b < b1 && ok; ++b) {
                 int32_t acc[kEpiCols];
 #pragma unroll
                 for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
@@ -727,7 +748,8 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
                              (int)BandCfg<256>::SMEM);
     });
     const int tiles = ba.tiles_m * ba.tiles_n;
-    const int grid = tiles < sm_count() ? tiles : sm_count();
+    const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords
+    const int grid = items < sm_count() ? items : sm_count();
     if (TN == 256)
         band_gemm_kernel<256><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(tmA, tmB,
                                                                                       ba);

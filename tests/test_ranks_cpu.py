@@ -1,0 +1,76 @@
+"""The N > 1 host logic of bench.py on CPU: two ranks over the gloo backend.
+
+Every workload runs one replica per rank with no collective on the data
+path; the ranks exchange only the barrier before the timed region and the
+maximum of the timings after it.  These tests run that exchange with two
+real processes, and the reference arm's rank gating (only rank 0 works)."""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+import socket
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank: int, world: int, port: int, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+
+    ranks = bench.Ranks("gloo")
+    ranks.barrier()
+    slowest = ranks.max(10.0 + 3.0 * rank)        # per-rank timing, seconds
+    value = ranks.whole_job(100.0, slowest)        # 100 units per rank
+    ranks.close()
+    out.put((rank, ranks.world, slowest, value))
+
+
+def test_two_ranks_max_timing_and_whole_job_value():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, world, slowest, value in results:
+        assert world == 2
+        assert slowest == 13.0                     # the max over both ranks, on every rank
+        assert abs(value - 2 * 100.0 / 13.0) < 1e-12
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    env = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK") if k in os.environ}
+    try:
+        ranks = bench.Ranks()
+        assert ranks.world == 1 and ranks.dist is None
+        assert ranks.max(4.5) == 4.5
+        assert ranks.whole_job(10.0, 2.0) == 5.0
+        ranks.close()
+    finally:
+        os.environ.update(env)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
