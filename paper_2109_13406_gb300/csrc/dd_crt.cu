@@ -139,10 +139,8 @@ struct CrtArgs {
     int64_t ldc;
     int moduli[kMaxMod];
     uint32_t P[kWords];                   // product of the moduli
-    uint32_t Phalf[kWords];               // floor(P / 2)
-    uint32_t w[kMaxMod][kWords];          // CRT weights
-    int ptop;                             // index of P's most significant word
-    float p_f;                            // P / 2^(32 ptop) (for quotient estimates)
+    uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
+    float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
 };
 
 // Word idx of a little-endian multiword value, without dynamic indexing
@@ -232,9 +230,11 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
         // products are read 8 moduli at a time, the 8 loads in flight together
         const uint8_t *res = p.res + j * p.m_pad + i;
         const int64_t plane = p.n_pad * p.m_pad;
+        // (and, for the quotient below, qf = sum_b c_b (inv_b / p_b) in fp32)
         uint64_t acc[NW];
 #pragma unroll
         for (int t = 0; t < NW; ++t) acc[t] = 0;
+        float qf = 0.0f;
         for (int b0 = 0; b0 < p.N; b0 += 8) {
             uint32_t cv[8];
 #pragma unroll
@@ -244,79 +244,39 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
                 const int b = b0 + u < p.N ? b0 + u : 0;   // cv[u] = 0 past N
 #pragma unroll
                 for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * p.w[b][t];
+                qf = __fmaf_rn((float)cv[u], p.frac[b], qf);
             }
         }
+        // The symmetric representative is Z = S - q P with q the integer
+        // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| <= k 2^222 < P / 4,
+        // and the fp32 sum of the 32 fractions (each term below 256, the sum
+        // below 8192) is off by less than 0.02, so rounding it gives q.
+        const uint64_t q = (uint64_t)(int64_t)rintf(qf);
+        // Z = S - q P in two's complement over NW words (exact: |Z| < 2^(32 NW - 1))
         uint32_t S[NW];
-        uint64_t carry = 0;
-#pragma unroll
-        for (int t = 0; t < NW; ++t) {
-            const uint64_t v = acc[t] + carry;
-            S[t] = (uint32_t)v;
-            carry = v >> 32;
-        }
-        // S mod P: quotient estimate (S < N 256 P < 2^14 P, so an fp32 ratio of
-        // the leading words is within one of the quotient; corrected below)
-        const float s_f = (float)word_at(S, p.ptop + 1) * 4294967296.0f +
-                          (float)word_at(S, p.ptop) + (float)word_at(S, p.ptop - 1) * 2.3283064e-10f;
-        int64_t qest = (int64_t)floorf(s_f / p.p_f);
-        if (qest < 0) qest = 0;
-        // S -= qest * P (two's complement over NW words)
         {
-            uint64_t borrow = 0, mc = 0;
+            uint64_t carry = 0, mc = 0, borrow = 0;
 #pragma unroll
             for (int t = 0; t < NW; ++t) {
-                const uint64_t prod = (uint64_t)qest * p.P[t] + mc;
+                const uint64_t v = acc[t] + carry;
+                carry = v >> 32;
+                const uint64_t prod = q * p.P[t] + mc;
                 mc = prod >> 32;
-                const uint64_t d = (uint64_t)S[t] - (uint32_t)prod - borrow;
+                const uint64_t d = (uint64_t)(uint32_t)v - (uint32_t)prod - borrow;
                 S[t] = (uint32_t)d;
                 borrow = (d >> 63) & 1;
             }
         }
-        // correct into [0, P): at most a couple of steps either way
-        for (int it = 0; it < 4; ++it) {
-            const bool neg = (S[NW - 1] & 0x80000000u) != 0;
-            bool ge = false;
-            if (!neg) {
-                bool eq = true;
-#pragma unroll
-                for (int t = NW - 1; t >= 0; --t)
-                    if (eq && S[t] != p.P[t]) {
-                        ge = S[t] > p.P[t];
-                        eq = false;
-                    }
-                if (eq) ge = true;
-            }
-            if (!neg && !ge) break;
-            uint64_t c2 = 0;
+        // magnitude and sign
+        const bool negative = (S[NW - 1] & 0x80000000u) != 0;
+        if (negative) {
+            uint64_t c2 = 1;
 #pragma unroll
             for (int t = 0; t < NW; ++t) {
-                uint64_t d = neg ? (uint64_t)S[t] + p.P[t] + c2
-                                 : (uint64_t)S[t] - p.P[t] - c2;
-                S[t] = (uint32_t)d;
-                c2 = neg ? (d >> 32) : ((d >> 63) & 1);
+                const uint64_t v = (uint64_t)(uint32_t)~S[t] + c2;
+                S[t] = (uint32_t)v;
+                c2 = v >> 32;
             }
-        }
-        // symmetric range: S > P/2 -> S - P (store the magnitude, remember the sign)
-        bool gt_half = false;
-        {
-            bool eq = true;
-#pragma unroll
-            for (int t = NW - 1; t >= 0; --t)
-                if (eq && S[t] != p.Phalf[t]) {
-                    gt_half = S[t] > p.Phalf[t];
-                    eq = false;
-                }
-        }
-        bool negative = false;
-        if (gt_half) {            // magnitude P - S
-            uint64_t b2 = 0;
-#pragma unroll
-            for (int t = 0; t < NW; ++t) {
-                const uint64_t d = (uint64_t)p.P[t] - S[t] - b2;
-                S[t] = (uint32_t)d;
-                b2 = (d >> 63) & 1;
-            }
-            negative = true;
         }
         const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * 8 * kDigits;
         uint32_t rem[NW], rem2[NW];
@@ -549,17 +509,15 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     }
     if ((int)P.size() > kWords - 1) return fail(MP_DD_ERR_TOO_LARGE, "moduli product too wide");
     for (int t = 0; t < kWords; ++t) ca.P[t] = t < (int)P.size() ? P[t] : 0;
-    Big half = big_div_small(P, 2, nullptr);
-    for (int t = 0; t < kWords; ++t) ca.Phalf[t] = t < (int)half.size() ? half[t] : 0;
     for (int i = 0; i < L.N; ++i) {
         uint32_t mi_mod = 0;
         Big Mi = big_div_small(P, modulus(i), nullptr);
         big_div_small(Mi, modulus(i), &mi_mod);
-        Big wi = big_mul_small(Mi, inv_mod(mi_mod, modulus(i)));
+        const uint32_t inv = inv_mod(mi_mod, modulus(i));
+        Big wi = big_mul_small(Mi, inv);
         for (int t = 0; t < kWords; ++t) ca.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
+        ca.frac[i] = (float)((double)inv / (double)modulus(i));
     }
-    ca.ptop = (int)P.size() - 1;
-    ca.p_f = (float)P.back() + (float)P[P.size() - 2] * 2.3283064e-10f;
     const int64_t total = p.m * p.n;
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
