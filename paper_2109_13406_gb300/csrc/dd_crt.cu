@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(128) residue_kernel(
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
     const int shift = 8 * kDigits - e;
     float df[4][kDigits];
-    uint32_t low[2] = {0u, 0u};   // plane 0: the lowest digits as fp16
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t l = l0 + q;
@@ -102,27 +101,38 @@ __global__ void __launch_bounds__(128) residue_kernel(
         }
         int dg[kDigits];
         dd_digits<kDigits>(hi, lo, shift, dg);
+        // d as a float without a conversion instruction: the bits of 2^23 + 128 + d
+        // (exact, d in [-128, 128]) minus 2^23 + 128
 #pragma unroll
-        for (int t = 0; t < kDigits; ++t) df[q][t] = (float)dg[t];
-        const uint32_t h = __half_as_ushort(__float2half_rn((float)dg[kDigits - 1]));
-        low[q / 2] |= (q & 1) ? h << 16 : h;
+        for (int t = 0; t < kDigits; ++t)
+            df[q][t] = __fsub_rn(__int_as_float(0x4B000000 + 128 + dg[t]), 8388736.0f);
     }
-    *reinterpret_cast<uint2 *>(R + r * k_pad + l0) = make_uint2(low[0], low[1]);
+    // plane 0 (p = 256): the lowest digits; two fp16 per conversion
+    {
+        const __half2 h01 = __floats2half2_rn(df[0][kDigits - 1], df[1][kDigits - 1]);
+        const __half2 h23 = __floats2half2_rn(df[2][kDigits - 1], df[3][kDigits - 1]);
+        *reinterpret_cast<uint2 *>(R + r * k_pad + l0) =
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
+                       *reinterpret_cast<const uint32_t *>(&h23));
+    }
 #pragma unroll
     for (int i = 1; i < 2 * NP; ++i) {
         const float p = (float)modulus(i), inv = c_mod_weights.inv[i];
-        uint32_t w[2] = {0u, 0u};
+        float res[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float s = 0.0f;
 #pragma unroll
             for (int t = 0; t < kDigits; ++t) s = __fmaf_rn(df[q][t], c_mod_weights.w[i][t], s);
-            const float res = __fmaf_rn(-p, rintf(__fmul_rn(s, inv)), s);
-            const uint32_t h = __half_as_ushort(__float2half_rn(res));
-            w[q / 2] |= (q & 1) ? h << 16 : h;
+            // rint(s / p) by the 1.5 2^23 shift (|s / p| < 2^22), then the residue
+            const float qn = __fsub_rn(__fmaf_rn(s, inv, 12582912.0f), 12582912.0f);
+            res[q] = __fmaf_rn(-p, qn, s);
         }
+        const __half2 h01 = __floats2half2_rn(res[0], res[1]);
+        const __half2 h23 = __floats2half2_rn(res[2], res[3]);
         *reinterpret_cast<uint2 *>(R + ((int64_t)i * rows_pad + r) * k_pad + l0) =
-            make_uint2(w[0], w[1]);
+            make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
+                       *reinterpret_cast<const uint32_t *>(&h23));
     }
 }
 
@@ -166,6 +176,37 @@ __device__ __forceinline__ double scale_pow2(double x, int e) {
     return __dmul_rn(r, __longlong_as_double((long long)(e + 1023) << 52));
 }
 
+// m 2^e for an integer 0 <= m <= 2^53, assembled from the binary64 fields
+// when the result is normal (integer instructions only), else by scale_pow2.
+__device__ __forceinline__ double mant_pow2(uint64_t m, int e) {
+    if (m == 0) return 0.0;
+    const int top = 63 - __clzll((long long)m);          // m in [2^top, 2^(top+1))
+    const uint64_t norm = top > 52 ? m >> (top - 52) : m << (52 - top);   // exact
+    const int E = top + e + 1023;
+    if (E >= 1 && E <= 2046)
+        return __longlong_as_double((long long)(((uint64_t)E << 52) | (norm & ((1ull << 52) - 1))));
+    return scale_pow2(__ull2double_rn(m), e);
+}
+
+// alpha v + beta c in dd with one rounding chain: the two leading products
+// split exactly (product and FMA error), their sum by TwoSum, every
+// lower-order term added into the error word, one FastTwoSum.  Absolute error
+// within about 3u^2 (|alpha v| + |beta c|), u = 2^-53; 20 FP64 operations
+// against 25 for two dd products and a dd sum.
+__device__ __forceinline__ dd axpby_dd(dd alpha, dd v, dd beta, dd c) {
+    const double p1 = __dmul_rn(alpha.hi, v.hi), e1 = __fma_rn(alpha.hi, v.hi, -p1);
+    const double p2 = __dmul_rn(beta.hi, c.hi), e2 = __fma_rn(beta.hi, c.hi, -p2);
+    double s, t;
+    two_sum(p1, p2, s, t);
+    const double low = __fma_rn(alpha.hi, v.lo,
+                                __fma_rn(alpha.lo, v.hi, __fma_rn(beta.hi, c.lo,
+                                                                  __dmul_rn(beta.lo, c.hi))));
+    t = __dadd_rn(t, __dadd_rn(__dadd_rn(e1, e2), low));
+    dd r;
+    fast_two_sum(s, t, r.hi, r.lo);
+    return r;
+}
+
 // Round the magnitude v (little-endian 32-bit words) to the nearest binary64
 // (ties to even) times 2^scale.  rem receives the exact remainder v - RN(v)
 // as a magnitude, rem_neg its sign.
@@ -183,7 +224,7 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale
     const int msb = 32 * top + (31 - __clz(word_at(v, top)));
     if (msb <= 52) {
         const uint64_t x = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
-        return scale_pow2(__ull2double_rn(x), scale);   // exact
+        return mant_pow2(x, scale);   // exact
     }
     const int q = msb - 52, w = q / 32, b = q % 32;
     const uint64_t v0 = word_at(v, w), v1 = word_at(v, w + 1), v2 = word_at(v, w + 2);
@@ -215,7 +256,7 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale
             borrow = (d >> 63) & 1;
         }
     }
-    return scale_pow2(__ull2double_rn(mant), q + scale);   // mant <= 2^53: exact
+    return mant_pow2(mant, q + scale);   // mant <= 2^53: exact
 }
 
 // NW: 32-bit words of the sums (P < 2^(32 (NW - 1)), and the sum of N
@@ -289,10 +330,12 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
             vl = -vl;
         }
         dd v{vh, vl};
-        if (!p.alpha_one) v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
         const int64_t off = i + j * p.ldc;
         if (!p.beta_zero)
-            v = add_sloppy(v, mul(dd{p.beta.hi, p.beta.lo}, dd{p.ch[off], p.cl[off]}));
+            v = axpby_dd(dd{p.alpha.hi, p.alpha.lo}, v, dd{p.beta.hi, p.beta.lo},
+                         dd{p.ch[off], p.cl[off]});
+        else if (!p.alpha_one)
+            v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
         p.ch[off] = v.hi;
         p.cl[off] = v.lo;
     }
