@@ -123,6 +123,33 @@ def test_server_alone_equals_mix_bitwise(cuda_lib):
         assert np.array_equal(alone.X[1], by_id[i].X[1])
 
 
+def test_server_tensor_core_trailing_updates(cuda_lib):
+    """Trailing updates through the residue-form Rgemm (forced on for every
+    trailing block of 64 rows or more): bitwise the same alone and in a mix,
+    the LAPACK ratio < 30, and the same solution as the FP64 updates within
+    what the condition of F (~1e20) allows."""
+    from paper_2109_13406_gb300.server import SpdServer, residual_ratio
+
+    sizes = [300, 64, 260, 200]
+    mix = SpdServer(slots=3, crt_min_rest=64).serve(make_requests(650, sizes))
+    by_id = {r.rid: r for r in mix}
+    assert all(r.info == 0 for r in mix)
+    for i in (0, 2):
+        alone = SpdServer(crt_min_rest=64).serve([make_requests(650, sizes)[i]])[0]
+        assert np.array_equal(alone.X[0], by_id[i].X[0])
+        assert np.array_equal(alone.X[1], by_id[i].X[1])
+        fp64 = SpdServer(crt_min_rest=10 ** 9).serve([make_requests(650, sizes)[i]])[0]
+        rel = np.abs((fp64.X[0] - alone.X[0]) + (fp64.X[1] - alone.X[1])).max()
+        assert rel <= 1e20 * EPS_DD * 100 * np.abs(fp64.X[0]).max()
+    n = sizes[0]
+    G, B = datagen.spd_request(650, n)
+    F = cuda_lib.dd_empty(n, n, fill=0.0)
+    cuda_lib.mp_dd_Rsyrk("U", "N", n, 2 * n, (1.0, 0.0), dev(G), n, (0.0, 0.0), F, n)
+    fh, fl = host(F)
+    Fs = (np.triu(fh) + np.triu(fh, 1).T, np.triu(fl) + np.triu(fl, 1).T)
+    assert residual_ratio(Fs, by_id[0].X, B, cuda_lib) < 30
+
+
 @pytest.mark.parametrize("n", [130, 300])
 def test_server_matches_single_matrix_routines(cuda_lib, n):
     from paper_2109_13406_gb300.server import SpdServer
