@@ -5,10 +5,8 @@ a fixed list of operations on its own device buffers:
 
   * F := G G^T: for n >= ``sliced_min_n`` one split-precision Rgemm on the
     tensor cores (``mp_dd_Rgemm_crt``, the residue form; both triangles
-    written, within the same accuracy bound); for smaller n as 2n/nb chunked
-    Rsyrk updates
-    F += G_c G_c^T over column chunks G_c of G (so no single FP64 operation
-    is large enough to hold a scheduler step hostage);
+    written, within the same accuracy bound); for smaller n one FP64
+    Rsyrk-type update of the upper triangle;
   * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
     factorisation, the panel solve U_JJ^T X = F(J, J+1:), and the trailing
     update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:): on the upper triangle in
@@ -101,6 +99,7 @@ class SpdServer:
         self.nb = int(nb)
         self.table = table
         self.active: list[Request] = []
+        self.draining: list = []    # finished on the device, result copy in flight
         self.used = 0
         self.steps = 0
         self.max_active = 0
@@ -131,7 +130,7 @@ class SpdServer:
         r.dev = {"G": G, "F": F, "X": X, "info": info}
         if r.sliced_ws:
             r.dev["ws"] = workspace(r.sliced_ws)
-        r.ops = self._plan(r)
+        r.ops = self._compile(r, self._plan(r))
         r.pos = 0
         r.admit_t = now
         self.active.append(r)
@@ -150,15 +149,13 @@ class SpdServer:
         G, F, X = r.dev["G"], r.dev["F"], r.dev["X"]
         one, mone, zero = (1.0, 0.0), (-1.0, 0.0), (0.0, 0.0)
         steps = []
-        # F := G G^T (chunked FP64 updates of one output are separate steps)
+        # F := G G^T: the tensor-core product, or below sliced_min_n one FP64
+        # Rsyrk-type update of the upper triangle (k = 2n < 512, a small
+        # share of a step)
         if r.sliced_ws:
             steps.append([("sliced", (G, F))])
-        else:   # upper triangle, in column chunks of G
-            for c0 in range(0, 2 * n, nb):
-                w = min(nb, 2 * n - c0)
-                Gc = _pair(G, 0, c0, n, w)
-                steps.append([("gemm", ("N", "T", n, n, w, one, Gc, Gc,
-                                        zero if c0 == 0 else one, F, 1))])
+        else:
+            steps.append([("gemm", ("N", "T", n, n, 2 * n, one, G, G, zero, F, 1))])
         # blocked Cholesky, upper: block J's step = [update left by J-1,
         # diagonal factor J, panel solve J]; the first joins the last F step
         pending = None
@@ -212,77 +209,122 @@ class SpdServer:
             steps.append(ops)
         return steps
 
+    def _compile(self, r: Request, steps: list) -> list:
+        """Turn every batched operation into its descriptor bytes once, at
+        admission (the pointers and sizes never change), so that a scheduler
+        step only concatenates bytes."""
+        info = r.dev["info"]
+        out = []
+        for ops in steps:
+            cops = []
+            for kind, args in ops:
+                if kind == "gemm":
+                    ta, tb, m, n, k, al, A, B, be, C, uplo = args
+                    d = gr.desc(ta, tb, m, n, k, al, A, B, be, C, gr.shape_for(self.table, m, n),
+                                uplo, info)
+                    cops.append(("gemm", bytes(d)))
+                elif kind == "diag":
+                    P, b, off = args
+                    d = _abi.MpDDPotrfDiagDesc()
+                    d.a_hi, d.a_lo = P[0].data_ptr(), P[1].data_ptr()
+                    d.lda, d.n, d.offset = P[0].stride(1), b, off
+                    d.info, d.lower = info.data_ptr(), 0
+                    cops.append(("diag", bytes(d)))
+                elif kind == "trsm":
+                    U, Bm, b, cols, trans = args
+                    d = _abi.MpDDTrsmDesc()
+                    d.u_hi, d.u_lo, d.ldu = U[0].data_ptr(), U[1].data_ptr(), U[0].stride(1)
+                    d.b_hi, d.b_lo = Bm[0].data_ptr(), Bm[1].data_ptr()
+                    d.ldb = max(Bm[0].stride(1), Bm[0].shape[0])
+                    d.n, d.nrhs, d.info = b, cols, info.data_ptr()
+                    d.trans, d.lower_u, d.lower_b = trans, 0, 0
+                    cops.append(("trsm", (bytes(d), cols)))
+                else:
+                    cops.append((kind, args))
+            out.append(cops)
+        return out
+
     # ---------------------------------------------------------------- one step
 
     def step(self) -> list[Request]:
-        """Run the next operation of every active request; return the requests
-        that finished (their results copied to the host)."""
+        """Run the next step of every active request.  Requests whose last
+        step this was start an asynchronous copy of X to the host; returns the
+        requests whose copies have landed (finished, results on the host)."""
         gemm, diag, trsm = [], [], []
-        for r, (kind, args) in ((r, op) for r in self.active for op in r.ops[r.pos]):
-            info = r.dev["info"]
-            if kind == "sliced":
-                G, F = args
-                n = r.n
-                ws = r.dev["ws"]
-                mp_dd_Rgemm_crt("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F, n,
-                                ws, ws.numel())
-                self.launches += 1
-            elif kind == "crt":
-                P, Ct, rest, b = args
-                ws = r.dev["ws"]
-                ld = P[0].stride(1)
-                mp_dd_Rgemm_crt("T", "N", rest, rest, b, (-1.0, 0.0), P, ld, P, ld, (1.0, 0.0), Ct,
-                                Ct[0].stride(1), ws, ws.numel())
-                self.launches += 1
-            elif kind == "gemm":
-                ta, tb, m, n, k, al, A, B, be, C, uplo = args
-                gemm.append(gr.desc(ta, tb, m, n, k, al, A, B, be, C,
-                                    gr.shape_for(self.table, m, n), uplo, info))
-            elif kind == "diag":
-                P, b, off = args
-                d = _abi.MpDDPotrfDiagDesc()
-                d.a_hi, d.a_lo = P[0].data_ptr(), P[1].data_ptr()
-                d.lda, d.n, d.offset = P[0].stride(1), b, off
-                d.info, d.lower = info.data_ptr(), 0
-                diag.append(d)
-            else:
-                U, Bm, b, cols, trans = args
-                d = _abi.MpDDTrsmDesc()
-                d.u_hi, d.u_lo, d.ldu = U[0].data_ptr(), U[1].data_ptr(), U[0].stride(1)
-                d.b_hi, d.b_lo = Bm[0].data_ptr(), Bm[1].data_ptr()
-                d.ldb = max(Bm[0].stride(1), Bm[0].shape[0])
-                d.n, d.nrhs, d.info = b, cols, info.data_ptr()
-                d.trans, d.lower_u, d.lower_b = trans, 0, 0
-                trsm.append(d)
+        max_rhs = 0
+        for r in self.active:
+            for kind, args in r.ops[r.pos]:
+                if kind == "gemm":
+                    gemm.append(args)
+                elif kind == "diag":
+                    diag.append(args)
+                elif kind == "trsm":
+                    trsm.append(args[0])
+                    max_rhs = max(max_rhs, args[1])
+                elif kind == "sliced":
+                    G, F = args
+                    n = r.n
+                    ws = r.dev["ws"]
+                    mp_dd_Rgemm_crt("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F,
+                                    n, ws, ws.numel())
+                    self.launches += 1
+                else:   # "crt"
+                    P, Ct, rest, b = args
+                    ws = r.dev["ws"]
+                    ld = P[0].stride(1)
+                    mp_dd_Rgemm_crt("T", "N", rest, rest, b, (-1.0, 0.0), P, ld, P, ld,
+                                    (1.0, 0.0), Ct, Ct[0].stride(1), ws, ws.numel())
+                    self.launches += 1
         if gemm:
-            arr = gr.descs_array(gemm)
+            arr = (_abi.MpDDGemmDesc * len(gemm)).from_buffer_copy(b"".join(gemm))
             ws = workspace(gr.mp_dd_Rgemm_grouped_workspace(len(arr), arr))
             gr.mp_dd_Rgemm_grouped_prepare(len(arr), arr, ws, ws.numel())
             gr.mp_dd_Rgemm_grouped_run(ws)
             self.launches += 1
         if diag:
-            buf = _to_device_bytes((_abi.MpDDPotrfDiagDesc * len(diag))(*diag))
-            mp_dd_potrf_diag_batch(len(diag), buf)
+            mp_dd_potrf_diag_batch(len(diag), _to_device_bytes(b"".join(diag)))
             self.launches += 1
         if trsm:
-            buf = _to_device_bytes((_abi.MpDDTrsmDesc * len(trsm))(*trsm))
-            mp_dd_trsm_batch(len(trsm), buf, max(d.nrhs for d in trsm))
+            mp_dd_trsm_batch(len(trsm), _to_device_bytes(b"".join(trsm)), max_rhs)
             self.launches += 1
+        still = []
         for r in self.active:
             r.pos += 1
-        finished = [r for r in self.active if r.pos == len(r.ops)]
-        if finished:
-            torch.cuda.synchronize()
-            now = time.perf_counter()
-            for r in finished:
-                r.X = (to_numpy(r.dev["X"][0]), to_numpy(r.dev["X"][1]))
-                r.info = int(r.dev["info"].item())
-                r.done_t = now
-                self.used -= r.footprint()
-                r.dev = {}
-            self.active = [r for r in self.active if r.pos < len(r.ops)]
+            if r.pos < len(r.ops):
+                still.append(r)
+                continue
+            # done on the device: copy X and info out without stopping the GPU
+            Xh = tuple(torch.empty(x.shape[::-1], dtype=x.dtype, pin_memory=True)
+                       for x in r.dev["X"])
+            for h, x in zip(Xh, r.dev["X"]):
+                h.copy_(x.t(), non_blocking=True)
+            ih = torch.empty(1, dtype=torch.int64, pin_memory=True)
+            ih.copy_(r.dev["info"], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record()
+            self.draining.append((r, Xh, ih, ev))
+        self.active = still
         self.steps += 1
-        return finished
+        return self._harvest()
+
+    def _harvest(self, wait: bool = False) -> list[Request]:
+        """Requests whose result copies have completed (all of them with wait)."""
+        done, keep = [], []
+        for item in self.draining:
+            r, Xh, ih, ev = item
+            if wait:
+                ev.synchronize()
+            elif not ev.query():
+                keep.append(item)
+                continue
+            r.done_t = time.perf_counter()
+            r.X = (Xh[0].numpy().T, Xh[1].numpy().T)
+            r.info = int(ih.item())
+            self.used -= r.footprint()
+            r.dev = {}
+            done.append(r)
+        self.draining = keep
+        return done
 
     # ---------------------------------------------------------------- driver
 
@@ -294,7 +336,7 @@ class SpdServer:
         done: list[Request] = []
         t0 = time.perf_counter()
         i = 0
-        while i < len(pending) or self.active:
+        while i < len(pending) or self.active or self.draining:
             now = time.perf_counter() - t0
             if i < len(pending) and pending[i].footprint() > self.budget:
                 raise ValueError(f"request {pending[i].rid} needs more than the memory budget")
@@ -302,11 +344,14 @@ class SpdServer:
                     self.can_admit(pending[i]):
                 self.admit(pending[i], now)
                 i += 1
-            if not self.active:
-                if i < len(pending):
-                    time.sleep(max(0.0, min(0.002, pending[i].arrival * time_scale - now)))
-                continue
-            for r in self.step():
+            if self.active:
+                finished = self.step()
+            else:
+                # nothing to launch: collect results, wait for arrivals or copies
+                finished = self._harvest(wait=i >= len(pending))
+                if not finished and i < len(pending):
+                    time.sleep(max(0.0, min(0.0005, pending[i].arrival * time_scale - now)))
+            for r in finished:
                 r.done_t -= t0
                 done.append(r)
         return done
