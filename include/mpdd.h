@@ -340,9 +340,12 @@ size_t mp_dd_Rgemm_grouped_workspace(int64_t count, const mp_dd_gemm_desc *descs
 /* Check the host descriptors (DGEMM rules per problem; a bad one returns -2
  * and mp_dd_last_error names it), cut every problem into tiles of its shape,
  * order all tiles longest first (k x tile area), and copy descriptors and
- * tile list into `workspace` (device memory owned by the caller).
- * Synchronous.  The problems' matrices are not touched.  Errors: -1 count,
- * -2 descriptor, -3 workspace NULL, 2003 workspace too small. */
+ * tile list into `workspace` (device memory owned by the caller).  The
+ * upload is asynchronous on the current stream (staged through pinned memory
+ * the library owns), so the host descriptors may be reused at once and the
+ * call does not wait for earlier work; a run must follow on the same stream.
+ * The problems' matrices are not touched.  Errors: -1 count, -2 descriptor,
+ * -3 workspace NULL, 2003 workspace too small. */
 int mp_dd_Rgemm_grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *workspace,
                                 size_t workspace_bytes);
 

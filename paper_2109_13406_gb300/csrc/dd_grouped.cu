@@ -22,6 +22,8 @@
 // give each thread more independent chains.  All shapes fit 128 registers,
 // so two CTAs share an SM.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -288,6 +290,50 @@ size_t grouped_workspace_bytes(int64_t count, const mp_dd_gemm_desc *descs) {
     return tiles_offset(count) + sizeof(TileRef) * (size_t)(tiles > 0 ? tiles : 1);
 }
 
+namespace {
+
+// Pinned staging blocks for the uploads of grouped_prepare: the image of the
+// workspace head (header, descriptors, tile list) is written into a block
+// and copied with one asynchronous cudaMemcpyAsync; an event recorded after
+// the copy marks when the block may be written again.  Blocks are kept for
+// reuse, so steady-state calls neither allocate nor wait for the GPU.
+struct StageBlock {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+};
+
+std::mutex g_stage_mu;
+std::vector<StageBlock> g_stage;
+
+int stage_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    std::lock_guard<std::mutex> lock(g_stage_mu);
+    StageBlock *blk = nullptr;
+    for (auto &b : g_stage)
+        if (b.cap >= bytes && cudaEventQuery(b.done) == cudaSuccess) {
+            blk = &b;
+            break;
+        }
+    cudaGetLastError();   // a not-ready query leaves an error state to clear
+    if (blk == nullptr) {
+        StageBlock nb;
+        nb.cap = 64 * 1024;
+        while (nb.cap < bytes) nb.cap *= 2;
+        cudaError_t e = cudaHostAlloc(&nb.ptr, nb.cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped: pinned staging");
+        e = cudaEventCreateWithFlags(&nb.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped: staging event");
+        g_stage.push_back(nb);
+        blk = &g_stage.back();
+    }
+    std::memcpy(blk->ptr, src, bytes);
+    cudaError_t e = cudaMemcpyAsync(dst, blk->ptr, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(blk->done, st);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "grouped: upload");
+}
+
+}  // namespace
+
 int grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *ws, size_t bytes,
                     cudaStream_t st) {
     std::vector<mp_dd_gemm_desc> dv(descs, descs + count);
@@ -329,17 +375,16 @@ int grouped_prepare(int64_t count, const mp_dd_gemm_desc *descs, void *ws, size_
     for (size_t q = 0; q < order.size(); ++q) sorted[q] = tiles[order[q]];
     GroupedHeader h{0ull, (long long)sorted.size(), (long long)count,
                     (long long)tiles_offset(count)};
-    uint8_t *w = static_cast<uint8_t *>(ws);
-    cudaError_t e = cudaMemcpyAsync(w, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && count > 0)
-        e = cudaMemcpyAsync(w + desc_offset(), dv.data(), sizeof(mp_dd_gemm_desc) * count,
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !sorted.empty())
-        e = cudaMemcpyAsync(w + tiles_offset(count), sorted.data(),
-                            sizeof(TileRef) * sorted.size(), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
-    if (e != cudaSuccess) return cuda_fail(e, "grouped: upload");
-    return 0;
+    // one image of header, descriptors and tile list, uploaded asynchronously
+    const size_t img = tiles_offset(count) + sizeof(TileRef) * sorted.size();
+    std::vector<uint8_t> image(img, 0);
+    std::memcpy(image.data(), &h, sizeof(h));
+    if (count > 0)
+        std::memcpy(image.data() + desc_offset(), dv.data(), sizeof(mp_dd_gemm_desc) * count);
+    if (!sorted.empty())
+        std::memcpy(image.data() + tiles_offset(count), sorted.data(),
+                    sizeof(TileRef) * sorted.size());
+    return stage_upload(ws, image.data(), img, st);
 }
 
 int grouped_run(void *ws, cudaStream_t st) {

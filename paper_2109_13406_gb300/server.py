@@ -91,7 +91,8 @@ class SpdServer:
     """Admission, per-request operation lists and the batched scheduler step."""
 
     def __init__(self, budget_bytes: float = 120e9, slots: int = 256, nb: int = 64,
-                 table: dict | None = None, sliced_min_n: int = 256, crt_min_rest: int = 512):
+                 table: dict | None = None, sliced_min_n: int = 256, crt_min_rest: int = 512,
+                 depth: int = 2):
         self.sliced_min_n = int(sliced_min_n)
         self.crt_min_rest = int(crt_min_rest)
         self.budget = float(budget_bytes)
@@ -100,6 +101,8 @@ class SpdServer:
         self.table = table
         self.active: list[Request] = []
         self.draining: list = []    # finished on the device, result copy in flight
+        self.inflight: list = []    # events of the steps queued on the GPU
+        self.depth = int(depth)
         self.used = 0
         self.steps = 0
         self.max_active = 0
@@ -305,6 +308,14 @@ class SpdServer:
             self.draining.append((r, Xh, ih, ev))
         self.active = still
         self.steps += 1
+        # keep at most `depth` steps queued on the GPU: the host prepares the
+        # next step while the GPU runs the previous one, but a new arrival
+        # never queues behind a long backlog of launched steps
+        ev = torch.cuda.Event()
+        ev.record()
+        self.inflight.append(ev)
+        while len(self.inflight) > self.depth:
+            self.inflight.pop(0).synchronize()
         return self._harvest()
 
     def _harvest(self, wait: bool = False) -> list[Request]:
@@ -357,9 +368,12 @@ class SpdServer:
         return done
 
 
-def _to_device_bytes(carr) -> torch.Tensor:
-    raw = np.frombuffer(bytes(carr), dtype=np.uint8)
-    return torch.from_numpy(raw.copy()).to("cuda", non_blocking=False)
+def _to_device_bytes(data: bytes) -> torch.Tensor:
+    """Descriptor bytes on the device without waiting for the GPU: staged in
+    pinned memory (PyTorch's host allocator keeps the block until the copy is
+    done) and copied asynchronously on the current stream."""
+    host = torch.frombuffer(bytearray(data), dtype=torch.uint8).pin_memory()
+    return host.to("cuda", non_blocking=True)
 
 
 def residual_ratio(F_host, X_host, B_host, mp) -> float:
