@@ -462,6 +462,24 @@ int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n
                     mp_dd beta, mp_dd_mat C, int64_t ldc, void *workspace,
                     size_t workspace_bytes);
 
+/* Rsyrk in the residue (CRT) form (the manual's Rsyrk, Sec. 7.3, on the
+ * tensor cores; DSYRK argument list and error numbering, -12 workspace NULL):
+ *
+ *     C := alpha A A^T + beta C   (trans N, A n x k), or
+ *     C := alpha A^T A + beta C   (trans T, A k x n),
+ *
+ * on the uplo triangle of C only (the other is neither read nor written).
+ * op(A) is rounded and reduced once and serves as both operands, and only
+ * the tiles and entries of the triangle are formed: about half the work of
+ * mp_dd_Rgemm_crt on (A, A^T).  Every entry of the triangle is bitwise equal
+ * to mp_dd_Rgemm_crt(N, T) (trans N) or (T, N) (trans T) on A, A.  Accuracy
+ * and limits as mp_dd_Rgemm_crt.  workspace: at least
+ * mp_dd_Rsyrk_crt_workspace(n, k) bytes.  Asynchronous. */
+size_t mp_dd_Rsyrk_crt_workspace(int64_t n, int64_t k);
+int mp_dd_Rsyrk_crt(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                    mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc,
+                    void *workspace, size_t workspace_bytes);
+
 /* Workspace layout of mp_dd_Rgemm_crt (for inspection and testing):
  * offsets[0..4] byte offsets of the row maxima (uint64), column maxima,
  * residue planes of op(A) (fp16 [N][m_pad][k_pad]), of op(B)^T (fp16

@@ -26,7 +26,8 @@ __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
     "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
-    "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
+    "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_Rsyrk_crt",
+    "mp_dd_Rsyrk_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
     "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_qd_Rgemm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf",
     "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
     "workspace", "dd_empty", "to_device", "to_numpy", "lib",
@@ -171,6 +172,18 @@ def mp_dd_Rgemm_crt(transa, transb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc
                               _cm(B), ldb, _dd(beta), _m(C), ldc, _ptr(workspace),
                               workspace_bytes)
     return _check(rc, "mp_dd_Rgemm_crt") if check else rc
+
+
+def mp_dd_Rsyrk_crt_workspace(n, k) -> int:
+    return int(_LIB.mp_dd_Rsyrk_crt_workspace(n, k))
+
+
+def mp_dd_Rsyrk_crt(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, workspace, workspace_bytes,
+                    check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rsyrk_crt(_flag(uplo), _flag(trans), n, k, _dd(alpha), _cm(A), lda,
+                              _dd(beta), _m(C), ldc, _ptr(workspace), workspace_bytes)
+    return _check(rc, "mp_dd_Rsyrk_crt") if check else rc
 
 
 def mp_dd_crt_layout(m, n, k) -> dict:

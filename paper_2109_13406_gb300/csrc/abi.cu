@@ -441,6 +441,24 @@ int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n
     return run_crt(p, workspace, workspace_bytes, tls().stream);
 }
 
+size_t mp_dd_Rsyrk_crt_workspace(int64_t n, int64_t k) {
+    if (n < 0 || k < 0) return 0;
+    return crt_workspace_bytes(n, n, k, true);
+}
+
+int mp_dd_Rsyrk_crt(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
+                    mp_dd_cmat A, int64_t lda, mp_dd beta, mp_dd_mat C, int64_t ldc,
+                    void *workspace, size_t workspace_bytes) {
+    clear_error();
+    GemmArgs p;
+    int rc = check_syrk(uplo, trans, n, k, alpha, A, lda, beta, C, ldc, p);
+    if (rc) return rc;
+    if (quick_return(p)) return 0;
+    if (workspace == nullptr) return fail(-12, "Rsyrk_crt: workspace is NULL");
+    if ((rc = require_device())) return rc;
+    return run_crt(p, workspace, workspace_bytes, tls().stream);
+}
+
 int mp_dd_crt_layout(int64_t m, int64_t n, int64_t k, size_t offsets[48], int *moduli) {
     clear_error();
     if (offsets == nullptr || moduli == nullptr) return fail(-4, "crt_layout: NULL output");

@@ -151,6 +151,7 @@ struct CrtArgs {
     uint32_t P[kWords];                   // product of the moduli
     uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
     float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
+    int tri;                              // 0: all of C; 1 / 2: upper / lower triangle
 };
 
 // Word idx of a little-endian multiword value, without dynamic indexing
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx % p.m, j = idx / p.m;
+        if ((p.tri == 1 && i > j) || (p.tri == 2 && i < j)) continue;
         // S = sum_b c_b w_b with 64-bit column sums, then carries; the
         // products are read 8 moduli at a time, the 8 loads in flight together
         const uint8_t *res = p.res + j * p.m_pad + i;
@@ -421,19 +423,23 @@ int crt_band_tn(int64_t m, int64_t n, int N) {
     return (items >= 2 * 152 && (pad256 - pad128) * 8 <= imax(n, 1)) ? 256 : 128;
 }
 
-CrtLayout crt_layout(int64_t m, int64_t n, int64_t k) {
+// sym: the Rsyrk form, op(B) = op(A)^T (m = n): one set of maxima and
+// residue planes serves both operands, padded alike (m_pad = n_pad).
+CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
     CrtLayout L{};
     L.N = moduli_count(k);
     const int TN = crt_band_tn(m, n, L.N);
-    L.m_pad = ceil_div(imax(m, 1), kBandTM) * kBandTM;
     L.n_pad = ceil_div(imax(n, 1), TN) * TN;
+    L.m_pad = sym ? L.n_pad : ceil_div(imax(m, 1), kBandTM) * kBandTM;
     L.k_pad = ceil_div(imax(k, 1), kBandTK) * kBandTK;
     const size_t N = L.N > 0 ? (size_t)L.N : 0;
     size_t o = 1024;
     L.off_rowmax = o; o = align1k(o + 8 * (size_t)L.m_pad);
-    L.off_colmax = o; o = align1k(o + 8 * (size_t)L.n_pad);
+    L.off_colmax = sym ? L.off_rowmax : o;
+    if (!sym) o = align1k(o + 8 * (size_t)L.n_pad);
     L.off_ra = o; o = align1k(o + 2 * N * L.m_pad * L.k_pad);
-    L.off_rb = o; o = align1k(o + 2 * N * L.n_pad * L.k_pad);
+    L.off_rb = sym ? L.off_ra : o;
+    if (!sym) o = align1k(o + 2 * N * L.n_pad * L.k_pad);
     L.off_res = o; o = align1k(o + N * L.n_pad * L.m_pad);
     L.total = o;
     return L;
@@ -465,8 +471,8 @@ int launch_residues(int N, const double *Xh, const double *Xl, int64_t ld, int r
 
 }  // namespace
 
-size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k) {
-    return crt_layout(m, n, k).total;
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k, bool sym) {
+    return crt_layout(m, n, k, sym).total;
 }
 
 int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *off, int *count) {
@@ -488,7 +494,11 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (p.k > ((int64_t)1 << 17) - 1)
         return fail(MP_DD_ERR_TOO_LARGE, "k = %lld exceeds 131071 (int32 products)",
                     (long long)p.k);
-    CrtLayout L = crt_layout(p.m, p.n, p.k);
+    // the Rsyrk form: one triangle of op(A) op(A)^T
+    const bool sym = p.tri != 0;
+    if (sym && (p.m != p.n || p.ah != p.bh || p.al != p.bl || p.lda != p.ldb || p.ta == p.tb))
+        return fail(MP_DD_ERR_TOO_LARGE, "CRT Rsyrk: operands are not A and A^T");
+    CrtLayout L = crt_layout(p.m, p.n, p.k, sym);
     if (L.N < 0 || L.N > kMaxMod) return fail(MP_DD_ERR_TOO_LARGE, "k too large for the moduli");
     if (ws == nullptr || ws_bytes < L.total)
         return fail(MP_DD_ERR_WORKSPACE, "CRT Rgemm needs %zu workspace bytes, got %zu",
@@ -510,13 +520,15 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     int rc;
     sliced_timing_mark(0, st);
     if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
-    if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
     if ((rc = launch_residues(L.N, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
                               RA, st)))
         return rc;
-    if ((rc = launch_residues(L.N, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax,
-                              RB, st)))
-        return rc;
+    if (!sym) {   // (the Rsyrk form reuses the maxima and planes of op(A))
+        if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
+        if ((rc = launch_residues(L.N, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad,
+                                  cmax, RB, st)))
+            return rc;
+    }
 
     sliced_timing_mark(1, st);
     CUtensorMap tmA, tmB;
@@ -533,6 +545,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ba.R = RES;
     ba.status = reinterpret_cast<int *>(w);
     ba.diag = 1;
+    ba.tri = p.tri;
     for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
     if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
     sliced_timing_mark(2, st);
@@ -545,6 +558,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ca.alpha = p.alpha; ca.beta = p.beta;
     ca.alpha_one = p.alpha_one; ca.beta_zero = p.beta_zero;
     ca.ch = p.ch; ca.cl = p.cl; ca.ldc = p.ldc;
+    ca.tri = p.tri;
     Big P{1};
     for (int i = 0; i < L.N; ++i) {
         ca.moduli[i] = modulus(i);

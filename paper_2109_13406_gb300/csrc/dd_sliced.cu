@@ -200,6 +200,9 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
 // sums are finished in one visit.  Residues (diagonal mode): one item per
 // (modulus, tile) with the modulus slowest, so the CTAs resident at one time
 // share one modulus's operand panels in L2.
+// Tiles entirely outside the requested triangle (Rsyrk form) get an empty
+// band range, so every role skips them alike.
+template <int TN>
 __device__ __forceinline__ void item_coords(const BandArgs &p, int item, int num_tiles, int &tm,
                                             int &tn, int &b0, int &b1) {
     int tile = item;
@@ -211,6 +214,8 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int item, int num
         tile = item % num_tiles;
     }
     tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+    const int64_t r0 = (int64_t)tm * TM, c0 = (int64_t)tn * TN;
+    if ((p.tri == 1 && r0 > c0 + TN - 1) || (p.tri == 2 && r0 + TM - 1 < c0)) b1 = b0;
 }
 
 template <int TN>
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             bool ok = true;
             for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
                 int tm, tn, b0, b1;
-                item_coords(p, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b)
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             bool ok = true;
             for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
                 int tm, tn, b0, b1;
-                item_coords(p, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b) {
                     const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
@@ -364,7 +369,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         bool ok = true;
         for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
             int tm, tn, b0, b1;
-            item_coords(p, item, num_tiles, tm, tn, b0, b1);
+            item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
             for (int b = b0; b < b1 && ok; ++b) {
                 int32_t acc[kEpiCols];
 #pragma unroll

@@ -79,8 +79,9 @@ int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
                       cudaStream_t st);
 
 // Residue (CRT) form of the split-precision Rgemm.
-size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k);
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t k, bool sym = false);
 int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *offsets, int *count);
+// p.tri != 0: the Rsyrk form (op(B) = op(A)^T, one triangle of C).
 int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t stream);
 
 // Quad-double Rgemm (four planes per matrix, four components per scalar).

@@ -22,6 +22,7 @@ struct BandArgs {
     uint8_t *R;   // [S][n_pad][m_pad] (diagonal mode)
     int *status;
     int diag;
+    int tri;      // diagonal mode: 1 / 2 = only tiles meeting the upper / lower triangle
     int moduli[kMaxBands];
 };
 

@@ -3,17 +3,17 @@
 Each request brings G (n x 2n) and B (n x nrhs) as dd matrices.  Its work is
 a fixed list of operations on its own device buffers:
 
-  * F := G G^T: for n >= ``sliced_min_n`` one split-precision Rgemm on the
-    tensor cores (``mp_dd_Rgemm_crt``, the residue form; both triangles
-    written, within the same accuracy bound); for smaller n one FP64
-    Rsyrk-type update of the upper triangle;
+  * F := G G^T: for n >= ``sliced_min_n`` one split-precision Rsyrk on the
+    tensor cores (``mp_dd_Rsyrk_crt``, the residue form, upper triangle,
+    within the same accuracy bound); for smaller n one FP64 Rsyrk-type
+    update of the upper triangle;
   * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
     factorisation, the panel solve U_JJ^T X = F(J, J+1:), and the trailing
-    update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:): on the upper triangle in
+    update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) on the upper triangle: in
     FP64, or, once the trailing block has ``crt_min_rest`` rows or more, as
-    one residue-form Rgemm on the tensor cores (both triangles; the lower one
-    is never read), within the same accuracy bound and far faster (a 2048 x
-    2048 x 64 update: ~0.5 ms against ~8 ms);
+    one residue-form Rsyrk on the tensor cores, within the same accuracy
+    bound and far faster (a 2048 x 2048 x 64 update: well under 1 ms against
+    ~8 ms);
   * the solve F X = B: blocked forward (U^T) and backward (U) substitution.
 
 A scheduler step takes the next step of every admitted request -- a short
@@ -37,7 +37,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rgemm_crt, mp_dd_Rgemm_crt_workspace,
+from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rsyrk_crt, mp_dd_Rsyrk_crt_workspace,
                mp_dd_trsm_batch, to_device, to_numpy, workspace)
 from . import grouped as gr
 
@@ -118,8 +118,8 @@ class SpdServer:
     def _size(self, r: Request) -> None:
         if r.n >= self.sliced_min_n and r.sliced_ws == 0:
             # one workspace for F = G G^T (k = 2n) and the trailing updates (k = nb)
-            r.sliced_ws = max(mp_dd_Rgemm_crt_workspace(r.n, r.n, 2 * r.n),
-                              mp_dd_Rgemm_crt_workspace(r.n, r.n, self.nb))
+            r.sliced_ws = max(mp_dd_Rsyrk_crt_workspace(r.n, 2 * r.n),
+                              mp_dd_Rsyrk_crt_workspace(r.n, self.nb))
 
     def admit(self, r: Request, now: float) -> None:
         self._size(r)
@@ -268,14 +268,13 @@ class SpdServer:
                     G, F = args
                     n = r.n
                     ws = r.dev["ws"]
-                    mp_dd_Rgemm_crt("N", "T", n, n, 2 * n, (1.0, 0.0), G, n, G, n, (0.0, 0.0), F,
-                                    n, ws, ws.numel())
+                    mp_dd_Rsyrk_crt("U", "N", n, 2 * n, (1.0, 0.0), G, n, (0.0, 0.0), F, n, ws,
+                                    ws.numel())
                     self.launches += 1
                 else:   # "crt"
                     P, Ct, rest, b = args
                     ws = r.dev["ws"]
-                    ld = P[0].stride(1)
-                    mp_dd_Rgemm_crt("T", "N", rest, rest, b, (-1.0, 0.0), P, ld, P, ld,
+                    mp_dd_Rsyrk_crt("U", "T", rest, b, (-1.0, 0.0), P, P[0].stride(1),
                                     (1.0, 0.0), Ct, Ct[0].stride(1), ws, ws.numel())
                     self.launches += 1
         if gemm:

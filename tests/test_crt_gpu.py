@@ -111,3 +111,61 @@ def test_crt_config2_2048(cuda_lib, ill):
     got, _ = run_crt(cuda_lib, c)
     rr, cc = sample_blocks(n, n, bs=16, count=8)
     assert check_against_exact(c, got, rr, cc) <= 1.0
+
+
+@pytest.mark.parametrize("uplo", ["U", "L"])
+@pytest.mark.parametrize("trans", ["N", "T"])
+def test_rsyrk_crt_triangle_equals_rgemm_crt(cuda_lib, uplo, trans):
+    """The Rsyrk form: only the uplo triangle is read and written (NaN in the
+    other one stays NaN), and it equals mp_dd_Rgemm_crt on (A, A^T) bit for
+    bit; the triangle meets the bound against the exact tier."""
+    mp = cuda_lib
+    n, k = 300, 200
+    g = datagen.rng(760 + "UL".index(uplo) * 2 + "NT".index(trans))
+    ar, ac = (n, k) if trans == "N" else (k, n)
+    A = datagen.dd_matrix(g, ar, ac, ar + 2)
+    C = datagen.dd_matrix(g, n, n, n + 1)
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    r, cc = np.meshgrid(np.arange(n + 1), np.arange(n), indexing="ij")
+    other = (r > cc) if uplo == "U" else (r < cc)
+    other |= r >= n
+    Cn = tuple(np.where(other, np.nan, P) for P in C)
+    dA, dC = dev(A), dev(tuple(np.asfortranarray(P) for P in Cn))
+    ws = mp.workspace(mp.mp_dd_Rsyrk_crt_workspace(n, k))
+    mp.mp_dd_Rsyrk_crt(uplo, trans, n, k, al, dA, ar + 2, be, dC, n + 1, ws, ws.numel())
+    got = host(dC)
+    assert mp.mp_dd_workspace_status(ws) == 0
+    assert np.isnan(got[0][other]).all() and np.isnan(got[1][other]).all()
+    # the same triangle through the Rgemm form
+    ta, tb = ("N", "T") if trans == "N" else ("T", "N")
+    dC2 = dev(C)
+    ws2 = mp.workspace(mp.mp_dd_Rgemm_crt_workspace(n, n, k))
+    mp.mp_dd_Rgemm_crt(ta, tb, n, n, k, al, dA, ar + 2, dA, ar + 2, be, dC2, n + 1, ws2,
+                       ws2.numel())
+    ref = host(dC2)
+    keep = ~other
+    assert np.array_equal(got[0][keep], ref[0][keep])
+    assert np.array_equal(got[1][keep], ref[1][keep])
+    c = datagen.GemmCase(ta, tb, n, n, k, al, A, A, be, C)
+    rows, cols = np.nonzero(keep[:n])
+    pick = np.linspace(0, rows.size - 1, 4000).astype(int)
+    assert check_against_exact(c, (got[0][:n], got[1][:n]), rows[pick], cols[pick]) <= 1.0
+
+
+def test_rsyrk_crt_errors(cuda_lib):
+    mp = cuda_lib
+    A = dev(datagen.dd_matrix(datagen.rng(770), 8, 4))
+    C = dev(datagen.dd_matrix(datagen.rng(771), 8, 8))
+    ws = mp.workspace(mp.mp_dd_Rsyrk_crt_workspace(8, 4))
+    assert mp.mp_dd_Rsyrk_crt("X", "N", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 8, ws, ws.numel(),
+                              check=False) == -1
+    assert mp.mp_dd_Rsyrk_crt("U", "X", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 8, ws, ws.numel(),
+                              check=False) == -2
+    assert mp.mp_dd_Rsyrk_crt("U", "N", 8, 4, (1.0, 0.0), A, 7, (0.0, 0.0), C, 8, ws, ws.numel(),
+                              check=False) == -7
+    assert mp.mp_dd_Rsyrk_crt("U", "N", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 7, ws, ws.numel(),
+                              check=False) == -10
+    assert mp.mp_dd_Rsyrk_crt("U", "N", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 8, None, 0,
+                              check=False) == -12
+    assert mp.mp_dd_Rsyrk_crt("U", "N", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 8, ws, 16,
+                              check=False) == 2003
