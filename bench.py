@@ -291,7 +291,8 @@ def run_ours(args):
                                                       form="crt"),
                   "crt_well_scaled": sliced_section(mp, torch, args.sliced_size, form="crt"),
                   "crt_ill_scaled_outer": sliced_section(mp, torch, args.sliced_size,
-                                                         ill="outer", form="crt")}
+                                                         ill="outer", form="crt"),
+                  "crt_rsyrk": syrk_crt_section(mp, torch, args.sliced_size)}
     routines = None
     if not args.no_sliced:
         routines = routines_section(mp, torch, size)
@@ -428,6 +429,32 @@ def tensor_peak_tflops():
         return float(json.load(open(MEASURED))["bf16_tflops"]), "measured (bf16 burst, = fp16 rate)"
     except (OSError, KeyError, ValueError):
         return 1900.0, "fallback (1.9 PFLOP/s bf16 burst)"
+
+
+def syrk_crt_section(mp, torch, size, reps=3):
+    """mp_dd_Rsyrk_crt U/N at n = k = size (dd-flops k n (n+1)) with CUDA
+    events on the launching stream, and its per-phase times."""
+    g = datagen.rng(6)
+    A = tuple(mp.to_device(x) for x in datagen.dd_matrix(g, size, size))
+    C = tuple(mp.to_device(x) for x in datagen.dd_matrix(g, size, size))
+    al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+    ws = mp.workspace(mp.mp_dd_Rsyrk_crt_workspace(size, size))
+    st = torch.cuda.current_stream()
+
+    def call():
+        mp.mp_dd_Rsyrk_crt("U", "N", size, size, al, A, size, be, C, size, ws, ws.numel())
+
+    ms = _event_ms(torch, st, call, reps=reps)
+    mp.mp_dd_sliced_timing(True)
+    call()
+    phases = mp.mp_dd_sliced_phase_ms()
+    mp.mp_dd_sliced_timing(False)
+    flops = float(size) * size * (size + 1)
+    return {"workload": f"split-precision dd Rsyrk U/N n=k={size}, CRT form, upper triangle",
+            "ms": ms, "dd_GFlops": flops / (ms * 1e-3) / 1e9,
+            "phase_ms": {"scale_and_split": phases[0], "band_products": phases[1],
+                         "recombine_epilogue": phases[2]},
+            "status": mp.mp_dd_workspace_status(ws)}
 
 
 def sliced_section(mp, torch, size, reps=3, slices=14, ill=None, compare_plain=False,

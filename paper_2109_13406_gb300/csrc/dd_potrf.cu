@@ -115,7 +115,7 @@ constexpr int TC = 32;   // right-hand-side columns per CTA
 
 struct TrsmSmem {
     double uh[NB][NB + 1], ul[NB][NB + 1];
-    double bh[NB][TC + 1], bl[NB][TC + 1];
+    double xh[NB][TC], xl[NB][TC];   // the solved rows (each written once)
 };
 
 // B := alpha B before the solve when scale != 0.
@@ -127,6 +127,14 @@ struct TrsmScale {
 // Solve U^T X = B (trans = 1) or U X = B (trans = 0) for the columns
 // [c0, c0 + TC) of B, in place.  U is the n x n upper factor block; with
 // d.unit_diag its diagonal is taken as one and never read.
+//
+// Thread t owns column t % 32 and the rows t / 32 + 8 q (q = 0..7) as dd
+// accumulators in registers.  Step i: the owner of row i finishes x_i (its
+// accumulator, divided by U(i, i)) and publishes it in shared memory; after
+// one barrier every thread subtracts U-entry x_i from its rows still to be
+// solved, with the deferred renormalisation of the GEMM kernels (TwoSum on
+// the leading parts, a FastTwoSum every 4 steps).
+template <int TRANS>
 __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, TrsmScale sc) {
     const int n = (int)d.n;
     const int tid = threadIdx.x;
@@ -134,6 +142,8 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, Trsm
     const int64_t ncol = d.nrhs - c0 < TC ? d.nrhs - c0 : TC;
     if (ncol <= 0) return;
     const int unit = d.unit_diag != 0;
+    const int col = tid % TC, rg = tid / TC;   // NT / TC = 8 row groups
+    const bool col_ok = col < ncol;
     for (int e = tid; e < n * n; e += NT) {
         int r = e % n, c = e / n;
         if (r < c || (r == c && !unit)) {
@@ -142,59 +152,85 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, Trsm
             s.ul[r][c] = d.u_lo[o];
         }
     }
-    for (int e = tid; e < n * TC; e += NT) {
-        int r = e % n, c = e / n;
-        if (c < ncol) {
-            int64_t o = uidx(d.lower_b, r, c0 + c, d.ldb);
-            dd b{d.b_hi[o], d.b_lo[o]};
-            if (sc.scale) b = mul(sc.alpha, b);
-            s.bh[r][c] = b.hi;
-            s.bl[r][c] = b.lo;
+    dd acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int r = rg + 8 * q;
+        acc[q] = dd{0.0, 0.0};
+        if (r < n && col_ok) {
+            const int64_t o = uidx(d.lower_b, r, c0 + col, d.ldb);
+            acc[q] = dd{d.b_hi[o], d.b_lo[o]};
+            if (sc.scale) acc[q] = mul(sc.alpha, acc[q]);
         }
     }
     __syncthreads();
-    for (int step = 0; step < n; ++step) {
-        const int i = d.trans ? step : n - 1 - step;
-        if (tid < ncol && !unit) {
-            dd x = div(dd{s.bh[i][tid], s.bl[i][tid]}, dd{s.uh[i][i], s.ul[i][i]});
-            s.bh[i][tid] = x.hi;
-            s.bl[i][tid] = x.lo;
+    // rows in solve order: i = 8 qq + ri, qq unrolled so that the owner's
+    // accumulator acc[qq] has a compile-time index
+    int step = 0;
+#pragma unroll
+    for (int qs = 0; qs < 8; ++qs) {
+        const int qq = TRANS ? qs : 7 - qs;
+#pragma unroll 1
+        for (int k8 = 0; k8 < 8; ++k8) {
+            const int i = 8 * qq + (TRANS ? k8 : 7 - k8);
+            if (i >= n) continue;
+            if (rg == (i & 7) && col_ok) {
+                renorm(acc[qq]);
+                if (!unit) acc[qq] = div(acc[qq], dd{s.uh[i][i], s.ul[i][i]});
+                s.xh[i][col] = acc[qq].hi;
+                s.xl[i][col] = acc[qq].lo;
+            }
+            __syncthreads();
+            if (col_ok) {
+                // eliminate x_i: U^T: rows r > i use U(i, r); U: rows r < i use U(r, i)
+                const dd x{s.xh[i][col], s.xl[i][col]};
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int r = rg + 8 * q;
+                    if (r < n && (TRANS ? r > i : r < i)) {
+                        const dd u = TRANS ? dd{s.uh[i][r], s.ul[i][r]}
+                                           : dd{s.uh[r][i], s.ul[r][i]};
+                        mac_deferred(acc[q], dd{-u.hi, -u.lo}, x);
+                    }
+                }
+                if ((step & (kRenormEvery - 1)) == kRenormEvery - 1) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) renorm(acc[q]);
+                }
+            }
+            ++step;
         }
-        __syncthreads();
-        // eliminate x_i from the remaining rows: U^T: rows r > i use U(i, r);
-        // U: rows r < i use U(r, i)
-        const int lo_r = d.trans ? i + 1 : 0, hi_r = d.trans ? n : i;
-        const int rows = hi_r - lo_r;
-        for (int e = tid; e < rows * (int)ncol; e += NT) {
-            int r = lo_r + e % rows, c = e / rows;
-            dd u = d.trans ? dd{s.uh[i][r], s.ul[i][r]} : dd{s.uh[r][i], s.ul[r][i]};
-            dd b{s.bh[r][c], s.bl[r][c]};
-            mac(b, dd{-u.hi, -u.lo}, dd{s.bh[i][c], s.bl[i][c]});
-            s.bh[r][c] = b.hi;
-            s.bl[r][c] = b.lo;
-        }
-        __syncthreads();
     }
-    for (int e = tid; e < n * TC; e += NT) {
-        int r = e % n, c = e / n;
-        if (c < ncol) {
-            int64_t o = uidx(d.lower_b, r, c0 + c, d.ldb);
-            d.b_hi[o] = s.bh[r][c];
-            d.b_lo[o] = s.bl[r][c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int r = rg + 8 * q;
+        if (r < n && col_ok) {
+            renorm(acc[q]);
+            const int64_t o = uidx(d.lower_b, r, c0 + col, d.ldb);
+            d.b_hi[o] = acc[q].hi;
+            d.b_lo[o] = acc[q].lo;
         }
     }
 }
 
-__global__ void __launch_bounds__(NT) trsm_batch_kernel(const mp_dd_trsm_desc *ds) {
+__device__ __forceinline__ void trsm_any(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s,
+                                         TrsmScale sc) {
+    if (d.trans)
+        trsm_one<1>(d, c0, s, sc);
+    else
+        trsm_one<0>(d, c0, s, sc);
+}
+
+__global__ void __launch_bounds__(NT, 2) trsm_batch_kernel(const mp_dd_trsm_desc *ds) {
     extern __shared__ double smem_t[];
-    trsm_one(ds[blockIdx.x], (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t),
+    trsm_any(ds[blockIdx.x], (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t),
              TrsmScale{dd{1.0, 0.0}, 0});
 }
 
-__global__ void __launch_bounds__(NT) trsm_single_kernel(const mp_dd_trsm_desc d,
+__global__ void __launch_bounds__(NT, 2) trsm_single_kernel(const mp_dd_trsm_desc d,
                                                          TrsmScale sc) {
     extern __shared__ double smem_t[];
-    trsm_one(d, (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t), sc);
+    trsm_any(d, (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t), sc);
 }
 
 constexpr TrsmScale kNoScale{dd{1.0, 0.0}, 0};
