@@ -49,7 +49,7 @@ QD_OPS_PER_MAC = 117.5   # qd multiply-add: 113 FP64 operations + 4.5 for the le
 # commands): the plain Rgemm NN launch at 4096 and the band kernel of the
 # CRT form at 8192 (None: not captured since the kernel last changed)
 PLAIN_NN_4096_DRAM_BYTES = 3626772736 + 278080000
-BAND_CRT_8192_DRAM_BYTES = 30803877888 + 2938833664
+BAND_CRT_8192_DRAM_BYTES = 30944334848 + 2938408704
 
 
 def parse():
