@@ -22,7 +22,9 @@ solve -- and runs all of them in a fixed launch order: tensor-core products,
 one grouped dd Rgemm launch for every Rsyrk/Rgemm-type operation
 (``mp_dd_Rgemm_grouped``), one batched diagonal factorisation
 (``mp_dd_potrf_diag_batch``) and one batched triangular solve
-(``mp_dd_trsm_batch``).  A request of order n takes about 3 n / 64 steps.  Requests arriving while others run are admitted as
+(``mp_dd_trsm_batch``).  A request of order n takes about 2 n / 64 steps:
+the Cholesky blocks with the forward substitution one block behind, then
+the backward substitution.  Requests arriving while others run are admitted as
 soon as a slot and device memory (the budget) are free, and join the next
 step.  A request's operation sequence and every operation's arithmetic are
 independent of which other requests share the step, so each result is
@@ -160,9 +162,24 @@ class SpdServer:
         else:
             steps.append([("gemm", ("N", "T", n, n, 2 * n, one, G, G, zero, F, 1))])
         # blocked Cholesky, upper: block J's step = [update left by J-1,
-        # diagonal factor J, panel solve J]; the first joins the last F step
+        # diagonal factor J, panel solve J]; the first joins the F step.
+        # The forward substitution U^T Y = B runs one block behind in the same
+        # steps: block J's solve needs only U_JJ and the updates from blocks
+        # before it, and its update of the later rows only the finished row
+        # block U(J, J+1:), so step J also holds [forward update left by
+        # J-2, forward solve J-1] (the grouped launch runs before the
+        # triangular solves).  The last forward pair follows the loop.
+        blocks = list(range(0, n, nb))
+        fwd_trsm, fwd_upd = [], []
+        for j in blocks:
+            b = min(nb, n - j)
+            fwd_trsm.append(("trsm", (_pair(F, j, j, b, b), _pair(X, j, 0, b, nrhs), b, nrhs, 1)))
+            rest = n - j - b
+            fwd_upd.append(("gemm", ("T", "N", rest, nrhs, b, mone, _pair(F, j, j + b, b, rest),
+                                     _pair(X, j, 0, b, nrhs), one,
+                                     _pair(X, j + b, 0, rest, nrhs), 0)) if rest > 0 else None)
         pending = None
-        for j in range(0, n, nb):
+        for t, j in enumerate(blocks):
             b = min(nb, n - j)
             ops = [pending] if pending else []
             ops.append(("diag", (_pair(F, j, j, b, b), b, j)))
@@ -176,28 +193,19 @@ class SpdServer:
                     pending = ("crt", (P, Ct, rest, b))
                 else:
                     pending = ("gemm", ("T", "N", rest, rest, b, mone, P, P, one, Ct, 1))
-            if j == 0:
+            if t >= 2 and fwd_upd[t - 2]:
+                ops.append(fwd_upd[t - 2])
+            if t >= 1:
+                ops.append(fwd_trsm[t - 1])
+            if t == 0:
                 steps[-1].extend(ops)
             else:
                 steps.append(ops)
-        # forward substitution U^T Y = B: [update left by J-1, block solve J];
-        # the first block solve joins the last Cholesky step (after its
-        # diagonal factor in launch order, and U_00 is long final)
-        pending = None
-        for j in range(0, n, nb):
-            b = min(nb, n - j)
-            ops = [pending] if pending else []
-            ops.append(("trsm", (_pair(F, j, j, b, b), _pair(X, j, 0, b, nrhs), b, nrhs, 1)))
-            rest = n - j - b
-            pending = None
-            if rest > 0:
-                pending = ("gemm", ("T", "N", rest, nrhs, b, mone, _pair(F, j, j + b, b, rest),
-                                    _pair(X, j, 0, b, nrhs), one, _pair(X, j + b, 0, rest, nrhs),
-                                    0))
-            if j == 0:
-                steps[-1].extend(ops)
-            else:
-                steps.append(ops)
+        last = len(blocks) - 1
+        if last == 0:
+            steps[-1].append(fwd_trsm[0])      # after its diagonal factor in launch order
+        else:
+            steps.append(([fwd_upd[last - 1]] if fwd_upd[last - 1] else []) + [fwd_trsm[last]])
         # backward substitution U X = Y, last block first (its own step: the
         # forward solve of the same block is in the previous one)
         pending = None
