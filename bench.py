@@ -355,9 +355,10 @@ def _fp64_line(workload, ms, flops, macs):
 
 def routines_section(mp, torch, size):
     """The other routines at m = n = k = size, each timed with CUDA events on
-    the launching stream: dd Rtrsm (two variants), Rsyr2k, Rsymm, Rgetrf, and
-    the quad-double Rgemm at min(size, 1024).  Flops are the LAPACK counts
-    (Rtrsm n^3, Rsyr2k 2 k n (n+1), Rsymm 2 n^3, Rgetrf 2 n^3 / 3, Rgemm
+    the launching stream: dd Rtrsm (two variants), Rsyr2k, Rsymm, Rgetrf,
+    Rpotrf (FP64 pipe and tensor-core updates), and the quad-double Rgemm at
+    min(size, 1024).  Flops are the LAPACK counts (Rtrsm n^3, Rsyr2k
+    2 k n (n+1), Rsymm 2 n^3, Rgetrf 2 n^3 / 3, Rpotrf n^3 / 3, Rgemm
     2 n^3)."""
     st = torch.cuda.current_stream()
     n = size
@@ -398,6 +399,30 @@ def routines_section(mp, torch, size):
                                     ms, 2.0 * n ** 3 / 3, float(n) ** 3 / 3)
     out[f"Rgetrf_{n}"]["info"] = int(info.item())
     del A, B, C, A0
+    # Rpotrf on the FP64 pipe and with the trailing updates on the tensor
+    # cores, on a diagonally dominant SPD matrix (symmetric U(-1,1) + 2n I)
+    Sh, Sl = datagen.dd_matrix(datagen.rng(6), n, n)
+    Sh = np.asfortranarray(np.triu(Sh) + np.triu(Sh, 1).T + 2.0 * n * np.eye(n))
+    Sl = np.asfortranarray(np.triu(Sl) + np.triu(Sl, 1).T)
+    S0 = dev((Sh, Sl))
+    S = tuple(x.clone() for x in S0)
+
+    def reset_s():
+        for x, y in zip(S, S0):
+            x.copy_(y)
+    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf("U", n, S, n, info), reset_s)
+    out[f"Rpotrf_U_{n}"] = _fp64_line(f"dd Rpotrf uplo=U, n={n}, diagonally dominant SPD", ms,
+                                      float(n) ** 3 / 3, float(n) ** 3 / 6)
+    out[f"Rpotrf_U_{n}"]["info"] = int(info.item())
+    ws = mp.workspace(mp.mp_dd_Rpotrf_crt_workspace(n))
+    ms_c = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf_crt("U", n, S, n, info, ws, ws.numel()),
+                     reset_s)
+    out[f"Rpotrf_crt_U_{n}"] = {
+        "workload": f"dd Rpotrf uplo=U, n={n}, trailing updates of >= 512 rows as residue-form "
+                    "Rsyrk on the fp16 tensor cores", "ms": ms_c,
+        "dd_GFlops": float(n) ** 3 / 3 / (ms_c * 1e-3) / 1e9, "speedup_vs_fp64_pipe": ms / ms_c,
+        "info": int(info.item())}
+    del S0, S, ws
     # quad-double Rgemm (117.5 FP64 instructions per qd multiply-add)
     nq = min(n, 1024)
     gq = datagen.rng(5)

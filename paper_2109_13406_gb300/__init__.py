@@ -28,7 +28,7 @@ __all__ = [
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_Rsyrk_crt",
     "mp_dd_Rsyrk_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
-    "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_qd_Rgemm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf",
+    "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_qd_Rgemm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf", "mp_dd_Rpotrf_crt",
     "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
     "workspace", "dd_empty", "to_device", "to_numpy", "lib",
 ]
@@ -309,6 +309,17 @@ def mp_dd_Rtrsm(side, uplo, transa, diag, m, n, alpha, A, lda, B, ldb, check=Tru
     rc = _LIB.mp_dd_Rtrsm(_flag(side), _flag(uplo), _flag(transa), _flag(diag), m, n,
                           _dd(alpha), _cm(A), lda, _m(B), ldb)
     return _check(rc, "mp_dd_Rtrsm") if check else rc
+
+
+def mp_dd_Rpotrf_crt_workspace(n) -> int:
+    return int(_LIB.mp_dd_Rpotrf_crt_workspace(n))
+
+
+def mp_dd_Rpotrf_crt(uplo, n, A, lda, info, workspace, workspace_bytes, check=True):
+    _sync_stream()
+    rc = _LIB.mp_dd_Rpotrf_crt(_flag(uplo), n, _m(A), lda, _ptr(info), _ptr(workspace),
+                               workspace_bytes)
+    return _check(rc, "mp_dd_Rpotrf_crt") if check else rc
 
 
 def mp_dd_Rpotrs(uplo, n, nrhs, A, lda, B, ldb, factor_info=None, check=True):

@@ -110,6 +110,8 @@ SIGNATURES = {
     "mp_dd_trsm_batch": (_int, [_i64, _vp, _i64]),
     "mp_dd_Rtrsm": (_int, [_c, _c, _c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDDMat, _i64]),
     "mp_dd_Rsyrk_crt_workspace": (_sz, [_i64, _i64]),
+    "mp_dd_Rpotrf_crt_workspace": (_sz, [_i64]),
+    "mp_dd_Rpotrf_crt": (_int, [_c, _i64, MpDDMat, _i64, _vp, _vp, _sz]),
     "mp_dd_Rsyrk_crt": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDD, MpDDMat, _i64, _vp,
                                _sz]),
     "mp_qd_Rgemm": (_int, [_c, _c, _i64, _i64, _i64, MpQD, MpQDCMat, _i64, MpQDCMat, _i64, MpQD,

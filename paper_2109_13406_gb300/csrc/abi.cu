@@ -497,6 +497,34 @@ int mp_dd_Rpotrf(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t 
     return run_potrf(ul == 2, n, A.hi, A.lo, lda, info, tls().stream);
 }
 
+size_t mp_dd_Rpotrf_crt_workspace(int64_t n) {
+    if (n < 0) return 0;
+    return potrf_crt_workspace_bytes(n);
+}
+
+int mp_dd_Rpotrf_crt(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info,
+                     void *workspace, size_t workspace_bytes) {
+    clear_error();
+    int ul = uplo_flag(uplo);
+    if (ul < 0) return fail(-1, "Rpotrf_crt: illegal uplo");
+    if (n < 0) return fail(-2, "Rpotrf_crt: n < 0");
+    if (n > 0 && (A.hi == nullptr || A.lo == nullptr)) return fail(-3, "Rpotrf_crt: A is NULL");
+    if (lda < imax(1, n)) return fail(-4, "Rpotrf_crt: lda < max(1, n)");
+    if (info == nullptr) return fail(-5, "Rpotrf_crt: info is NULL");
+    const size_t need = potrf_crt_workspace_bytes(n);
+    if (need > 0 && (workspace == nullptr || workspace_bytes < need))
+        return fail(MP_DD_ERR_WORKSPACE, "Rpotrf_crt needs %zu workspace bytes, got %zu", need,
+                    workspace_bytes);
+    int rc = require_device();
+    if (rc) return rc;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), tls().stream);
+        return e == cudaSuccess ? 0 : cuda_fail(e, "info reset");
+    }
+    return run_potrf(ul == 2, n, A.hi, A.lo, lda, info, tls().stream,
+                     need > 0 ? workspace : nullptr, workspace_bytes);
+}
+
 int mp_dd_Rpotrs(const char *uplo, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_t lda,
                  mp_dd_mat B, int64_t ldb, const int64_t *factor_info) {
     clear_error();

@@ -152,6 +152,7 @@ struct CrtArgs {
     uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
     float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
     int tri;                              // 0: all of C; 1 / 2: upper / lower triangle
+    const int64_t *info;                  // optional: non-zero -> leave C as is
 };
 
 // Word idx of a little-endian multiword value, without dynamic indexing
@@ -264,6 +265,7 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale
 // residues < 256 times the weights < P stays below 2^(32 NW)).
 template <int NW>
 __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
+    if (p.info != nullptr && *p.info != 0) return;   // an earlier step failed
     const int64_t total = p.m * p.n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -559,6 +561,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ca.alpha_one = p.alpha_one; ca.beta_zero = p.beta_zero;
     ca.ch = p.ch; ca.cl = p.cl; ca.ldc = p.ldc;
     ca.tri = p.tri;
+    ca.info = p.info;
     Big P{1};
     for (int i = 0; i < L.N; ++i) {
         ca.moduli[i] = modulus(i);

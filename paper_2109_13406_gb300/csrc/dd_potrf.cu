@@ -280,9 +280,19 @@ int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
     return check_launch("trsm_batch_kernel");
 }
 
-// Blocked right-looking Cholesky of one matrix (LAPACK dpotrf order).
+// Trailing updates of at least this many rows go through the residue-form
+// Rsyrk when a workspace is given.
+constexpr int64_t kCrtMinRest = 512;
+
+size_t potrf_crt_workspace_bytes(int64_t n) {
+    return n > kCrtMinRest ? crt_workspace_bytes(n - 1, n - 1, NB, true) : 0;
+}
+
+// Blocked right-looking Cholesky of one matrix (LAPACK dpotrf order); with a
+// workspace (ws != nullptr) the trailing updates of kCrtMinRest rows or more
+// run on the tensor cores.
 int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
-              cudaStream_t st) {
+              cudaStream_t st, void *ws, size_t ws_bytes) {
     int rc = set_attrs();
     if (rc) return rc;
     if (info != nullptr) {
@@ -322,7 +332,11 @@ int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t
         p.ta = lower ? 0 : 1; p.tb = lower ? 1 : 0; p.tri = lower ? 2 : 1;
         p.alpha_zero = 0; p.alpha_one = 0; p.beta_zero = 0;
         p.info = info;
-        if ((rc = launch_gemm_plain(p, st))) return rc;
+        if (ws != nullptr && rest >= kCrtMinRest)
+            rc = run_crt(p, ws, ws_bytes, st);
+        else
+            rc = launch_gemm_plain(p, st);
+        if (rc) return rc;
     }
     return 0;
 }

@@ -59,7 +59,8 @@ int grouped_run(void *ws, cudaStream_t stream);
 
 // dd Cholesky (blocked, LAPACK order) and its building blocks.
 int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
-              cudaStream_t stream);
+              cudaStream_t stream, void *ws = nullptr, size_t ws_bytes = 0);
+size_t potrf_crt_workspace_bytes(int64_t n);
 int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double *al,
               int64_t lda, double *bh, double *bl, int64_t ldb, const int64_t *info,
               cudaStream_t stream);
