@@ -119,28 +119,38 @@ __device__ __forceinline__ dd add_sloppy(dd a, dd b) {
 __device__ __forceinline__ dd neg(dd a) { return dd{-a.hi, -a.lo}; }
 __device__ __forceinline__ dd sub(dd a, dd b) { return add(a, neg(b)); }
 
-// dd division: three binary64 quotient digits by long division.
+// dd division by two steps of long division.  q1 = RN(a.hi / b.hi); the
+// remainder of a correctly rounded quotient, a.hi - q1 b.hi, is a binary64
+// number, so one FMA gives it exactly; the rest of a - q1 b (a.lo - q1 b.lo)
+// is added with two roundings, and q2 = RN(remainder / b.hi).  Relative
+// error at most ~11 u^2 (u = 2^-53).  When a and b are binary64 numbers
+// (a.lo = b.lo = 0) whose quotient is one too, q1 is that quotient, the
+// remainder is 0 and the result exact.  The dependent chain is two
+// divisions and five FP64 operations: this is what the row-serial
+// triangular solves and the Cholesky pivots wait on.
 __device__ __forceinline__ dd div(dd a, dd b) {
-    double q1 = __ddiv_rn(a.hi, b.hi);
-    dd r = sub(a, mul(dd{q1, 0.0}, b));
-    double q2 = __ddiv_rn(r.hi, b.hi);
-    r = sub(r, mul(dd{q2, 0.0}, b));
-    double q3 = __ddiv_rn(r.hi, b.hi);
+    const double q1 = __ddiv_rn(a.hi, b.hi);
+    double r = __fma_rn(-q1, b.hi, a.hi);
+    r = __dadd_rn(r, __fma_rn(-q1, b.lo, a.lo));
+    const double q2 = __ddiv_rn(r, b.hi);
     dd q;
     fast_two_sum(q1, q2, q.hi, q.lo);
-    return add(q, dd{q3, 0.0});
+    return q;
 }
 
-// dd square root: binary64 root plus one Newton correction (a - x^2)/(2x)
-// with the residual in dd.  Returns 0 for a <= 0.
+// dd square root: x = RN(sqrt(a.hi)), whose remainder a.hi - x^2 is a
+// binary64 number (one FMA gives it exactly), plus one Newton correction
+// (a - x^2) / (2x) with a.lo added; the neglected second-order term is
+// below u^2 / 8 relative.  Exact when a.hi is the square of a binary64
+// number and a.lo = 0.  Returns 0 for a <= 0.
 __device__ __forceinline__ dd sqrt_dd(dd a) {
     if (!(a.hi > 0.0)) return dd{0.0, 0.0};
-    double x = __dsqrt_rn(a.hi);
-    dd res = sub(a, mul(dd{x, 0.0}, dd{x, 0.0}));
-    double corr = __ddiv_rn(res.hi, __dmul_rn(2.0, x));
-    dd r;
-    fast_two_sum(x, corr, r.hi, r.lo);
-    return r;
+    const double x = __dsqrt_rn(a.hi);
+    const double r = __dadd_rn(__fma_rn(-x, x, a.hi), a.lo);
+    const double corr = __ddiv_rn(r, __dadd_rn(x, x));
+    dd s;
+    fast_two_sum(x, corr, s.hi, s.lo);
+    return s;
 }
 
 }  // namespace mpdd

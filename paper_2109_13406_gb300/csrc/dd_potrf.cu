@@ -34,67 +34,132 @@ __host__ __device__ __forceinline__ int64_t uidx(int lower, int64_t i, int64_t j
     return lower ? (j + i * ld) : (i + j * ld);
 }
 
+// Unblocked Cholesky of one nb x nb block (nb <= 64), right-looking, with
+// the block's upper triangle in registers.  The triangle's 2080 entries are
+// numbered row by row (row r holds columns r..63) and thread t holds the
+// entries t + 256 s (s = 0..8) as dd accumulators; the rows that are done
+// form a prefix of that numbering, so a warp whose entries are all done
+// issues nothing.  Step j: the holder of (j, j) takes the square root of its
+// accumulator; after a barrier the holders of row j divide by it and publish
+// the row in shared memory (two buffers by the parity of j); after a second
+// barrier every entry (r, c) with j < r <= c subtracts U(j, r) U(j, c), with
+// the GEMM kernels' deferred renormalisation (every entry has taken
+// exactly j + 1 updates after step j, so all renormalise at the same steps).
+constexpr int kTri = NB * (NB + 1) / 2;
+constexpr int kSlots = (kTri + NT - 1) / NT;
+
 struct DiagSmem {
-    double h[NB][NB + 1], l[NB][NB + 1];   // U block, [row][col], upper part used
+    double rh[2][NB], rl[2][NB];   // the pivot row U(j, :)
+    double uh, ul;                 // U(j, j)
     int fail;
 };
+
+__device__ __forceinline__ int tri_start(int r) { return r * NB - (r * (r - 1)) / 2; }
+
+// acc[s] with a run-time s, without local memory
+__device__ __forceinline__ dd pick(const dd (&acc)[kSlots], int s) {
+    dd v = acc[0];
+#pragma unroll
+    for (int q = 1; q < kSlots; ++q)
+        if (q == s) v = acc[q];
+    return v;
+}
+
+__device__ __forceinline__ void put(dd (&acc)[kSlots], int s, dd v) {
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q)
+        if (q == s) acc[q] = v;
+}
 
 __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
     const int nbe = (int)d.n;
     const int tid = threadIdx.x;
     if (d.info != nullptr && *d.info != 0) return;   // an earlier block failed
-    for (int e = tid; e < nbe * nbe; e += NT) {
-        int r = e % nbe, c = e / nbe;
-        if (r <= c) {
-            int64_t o = uidx(d.lower, r, c, d.lda);
-            s.h[r][c] = d.a_hi[o];
-            s.l[r][c] = d.a_lo[o];
+    // the (row, column) of each entry this thread holds; c = NB marks none
+    int er[kSlots], ec[kSlots];
+    {
+        int r = 0;
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            const int e = tid + NT * q;
+            while (r < NB - 1 && tri_start(r + 1) <= e) ++r;
+            const bool ok = e < kTri && r + (e - tri_start(r)) < nbe;
+            er[q] = ok ? r : NB;
+            ec[q] = ok ? r + (e - tri_start(r)) : NB;
+        }
+    }
+    dd acc[kSlots];
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+        acc[q] = dd{0.0, 0.0};
+        if (ec[q] < NB) {
+            const int64_t o = uidx(d.lower, er[q], ec[q], d.lda);
+            acc[q] = dd{d.a_hi[o], d.a_lo[o]};
         }
     }
     if (tid == 0) s.fail = 0;
-    __syncthreads();
+    int jdone = nbe;
     for (int j = 0; j < nbe; ++j) {
-        if (tid == 0) {
-            dd p{s.h[j][j], s.l[j][j]};
+        const int e0 = tri_start(j);             // (j, j)
+        if (tid == e0 % NT) {
+            const int q = e0 / NT;
+            dd p = pick(acc, q);
+            renorm(p);
             if (!(p.hi > 0.0)) {
                 s.fail = 1;
                 if (d.info != nullptr)
                     atomicCAS(reinterpret_cast<unsigned long long *>(d.info), 0ull,
                               (unsigned long long)(d.offset + j + 1));
+                put(acc, q, p);
             } else {
-                dd u = sqrt_dd(p);
-                s.h[j][j] = u.hi;
-                s.l[j][j] = u.lo;
+                const dd u = sqrt_dd(p);
+                s.uh = u.hi;
+                s.ul = u.lo;
+                put(acc, q, u);
             }
         }
         __syncthreads();
-        if (s.fail) break;
-        const dd ujj{s.h[j][j], s.l[j][j]};
-        for (int c = j + 1 + tid; c < nbe; c += NT) {
-            dd v = div(dd{s.h[j][c], s.l[j][c]}, ujj);
-            s.h[j][c] = v.hi;
-            s.l[j][c] = v.lo;
+        if (s.fail) {
+            jdone = j;
+            break;
         }
-        __syncthreads();
-        // trailing update of the block: U(r, c) -= U(j, r) U(j, c), j < r <= c
-        const int w = nbe - j - 1;
-        for (int e = tid; e < w * w; e += NT) {
-            int r = j + 1 + e % w, c = j + 1 + e / w;
-            if (r <= c) {
-                dd a{s.h[r][c], s.l[r][c]};
-                mac(a, dd{-s.h[j][r], -s.l[j][r]}, dd{s.h[j][c], s.l[j][c]});
-                s.h[r][c] = a.hi;
-                s.l[r][c] = a.lo;
+        // row j: the entries e0 + 1 .. e0 + nbe - j - 1, at most one per thread
+        {
+            const int first = e0 + 1, count = nbe - j - 1;
+            const int e = first + (tid - first % NT + NT) % NT;
+            if (e < first + count) {
+                const int q = e / NT;
+                dd v = pick(acc, q);
+                renorm(v);
+                v = div(v, dd{s.uh, s.ul});
+                put(acc, q, v);
+                const int c = j + 1 + (e - first);
+                s.rh[j & 1][c] = v.hi;
+                s.rl[j & 1][c] = v.lo;
             }
         }
         __syncthreads();
+        const bool renorm_now = (j & (kRenormEvery - 1)) == kRenormEvery - 1;
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            if (er[q] > j && ec[q] < NB) {
+                const dd ur{-s.rh[j & 1][er[q]], -s.rl[j & 1][er[q]]};
+                const dd uc{s.rh[j & 1][ec[q]], s.rl[j & 1][ec[q]]};
+                mac_deferred(acc[q], ur, uc);
+                if (renorm_now) renorm(acc[q]);
+            }
+        }
     }
-    for (int e = tid; e < nbe * nbe; e += NT) {
-        int r = e % nbe, c = e / nbe;
-        if (r <= c) {
-            int64_t o = uidx(d.lower, r, c, d.lda);
-            d.a_hi[o] = s.h[r][c];
-            d.a_lo[o] = s.l[r][c];
+    // rows r < jdone hold their final values; a failing pivot leaves the
+    // rest partially updated (LAPACK leaves the trailing block unspecified)
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+        if (ec[q] < NB) {
+            dd v = acc[q];
+            if (er[q] >= jdone) renorm(v);
+            const int64_t o = uidx(d.lower, er[q], ec[q], d.lda);
+            d.a_hi[o] = v.hi;
+            d.a_lo[o] = v.lo;
         }
     }
 }
