@@ -314,7 +314,8 @@ typedef struct {
 /* One launch: one CTA per diagonal block.  Errors: -1 count, -2 descs. */
 int mp_dd_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *descs);
 
-/* One launch over count descriptors, 32 right-hand-side columns per CTA;
+/* One launch over count descriptors, 4 to 32 right-hand-side columns per
+ * CTA (chosen from count and max_nrhs; the result does not depend on it);
  * max_nrhs is the largest nrhs in the batch.  Errors: -1, -2, -3. */
 int mp_dd_trsm_batch(int64_t count, const mp_dd_trsm_desc *descs, int64_t max_nrhs);
 

@@ -5,7 +5,7 @@
 //
 //  * diag:  unblocked Cholesky of one nb x nb diagonal block (nb <= 64), in
 //           shared memory, one CTA per block;
-//  * trsm:  triangular solve with one nb x nb factor block for up to 32
+//  * trsm:  triangular solve with one nb x nb factor block for 4 to 32
 //           right-hand-side columns per CTA (forward with U^T, backward
 //           with U), optionally scaling the right-hand sides by alpha and
 //           taking the diagonal as unit;
@@ -176,51 +176,60 @@ __global__ void __launch_bounds__(NT) potrf_diag_single_kernel(const mp_dd_potrf
 
 // ------------------------------------------------------------------ trsm
 
-constexpr int TC = 32;   // right-hand-side columns per CTA
-
-struct TrsmSmem {
-    double uh[NB][NB + 1], ul[NB][NB + 1];
-    double xh[NB][TC], xl[NB][TC];   // the solved rows (each written once)
-};
-
 // B := alpha B before the solve when scale != 0.
 struct TrsmScale {
     dd alpha;
     int scale;
 };
 
+__device__ __forceinline__ int col_start(int c) { return (c * (c + 1)) / 2; }
+
+// Shared memory of one solve CTA with RG row groups: U's triangle packed
+// (hi, lo) and the solved rows x_i of its NT / RG columns.
+__host__ __device__ constexpr size_t trsm_smem_bytes(int rg) {
+    return sizeof(double) * (2 * (size_t)kTri + 2 * (size_t)NB * (NT / rg));
+}
+
 // Solve U^T X = B (trans = 1) or U X = B (trans = 0) for the columns
-// [c0, c0 + TC) of B, in place.  U is the n x n upper factor block; with
-// d.unit_diag its diagonal is taken as one and never read.
+// [c0, c0 + NT / RG) of B, in place.  U is the n x n upper factor block;
+// with d.unit_diag its diagonal is taken as one and never read.
 //
-// Thread t owns column t % 32 and the rows t / 32 + 8 q (q = 0..7) as dd
-// accumulators in registers.  Step i: the owner of row i finishes x_i (its
-// accumulator, divided by U(i, i)) and publishes it in shared memory; after
-// one barrier every thread subtracts U-entry x_i from its rows still to be
-// solved, with the deferred renormalisation of the GEMM kernels (TwoSum on
-// the leading parts, a FastTwoSum every 4 steps).
-template <int TRANS>
-__device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, TrsmScale sc) {
+// Thread t owns column t % (NT / RG) and the rows t / (NT / RG) + RG q (q <
+// 64 / RG) as dd accumulators in registers.  Step i: the owner of row i
+// finishes x_i (its accumulator, divided by U(i, i)) and publishes it in
+// shared memory; after one barrier every thread subtracts U-entry x_i from
+// its rows still to be solved, with the deferred renormalisation of the GEMM
+// kernels (TwoSum on the leading parts, a FastTwoSum every 4 steps).  U's
+// triangle sits in shared memory packed in the order the steps read it: by
+// rows for U^T (step i reads U(i, i+1:)), by columns for U (step i reads
+// U(:i-1, i)).  Every row takes the same operations in the same order
+// whatever RG is, so the result does not depend on it: RG only trades
+// columns per CTA (32, 16, 8, 4) against the number of CTAs.
+template <int TRANS, int RG>
+__device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmScale sc) {
+    constexpr int COLS = NT / RG, RPT = NB / RG;
+    double *uh = sm, *ul = sm + kTri, *xh = sm + 2 * kTri, *xl = xh + NB * COLS;
     const int n = (int)d.n;
     const int tid = threadIdx.x;
     if (d.info != nullptr && *d.info != 0) return;
-    const int64_t ncol = d.nrhs - c0 < TC ? d.nrhs - c0 : TC;
+    const int64_t ncol = d.nrhs - c0 < COLS ? d.nrhs - c0 : COLS;
     if (ncol <= 0) return;
     const int unit = d.unit_diag != 0;
-    const int col = tid % TC, rg = tid / TC;   // NT / TC = 8 row groups
+    const int col = tid % COLS, rg = tid / COLS;
     const bool col_ok = col < ncol;
     for (int e = tid; e < n * n; e += NT) {
-        int r = e % n, c = e / n;
+        const int r = e % n, c = e / n;
         if (r < c || (r == c && !unit)) {
-            int64_t o = uidx(d.lower_u, r, c, d.ldu);
-            s.uh[r][c] = d.u_hi[o];
-            s.ul[r][c] = d.u_lo[o];
+            const int64_t o = uidx(d.lower_u, r, c, d.ldu);
+            const int k = TRANS ? tri_start(r) + (c - r) : col_start(c) + r;
+            uh[k] = d.u_hi[o];
+            ul[k] = d.u_lo[o];
         }
     }
-    dd acc[8];
+    dd acc[RPT];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int r = rg + 8 * q;
+    for (int q = 0; q < RPT; ++q) {
+        const int r = rg + RG * q;
         acc[q] = dd{0.0, 0.0};
         if (r < n && col_ok) {
             const int64_t o = uidx(d.lower_b, r, c0 + col, d.ldb);
@@ -229,46 +238,48 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, Trsm
         }
     }
     __syncthreads();
-    // rows in solve order: i = 8 qq + ri, qq unrolled so that the owner's
+    // rows in solve order: i = RG qq + ri, qq unrolled so that the owner's
     // accumulator acc[qq] has a compile-time index
     int step = 0;
 #pragma unroll
-    for (int qs = 0; qs < 8; ++qs) {
-        const int qq = TRANS ? qs : 7 - qs;
+    for (int qs = 0; qs < RPT; ++qs) {
+        const int qq = TRANS ? qs : RPT - 1 - qs;
 #pragma unroll 1
-        for (int k8 = 0; k8 < 8; ++k8) {
-            const int i = 8 * qq + (TRANS ? k8 : 7 - k8);
+        for (int k = 0; k < RG; ++k) {
+            const int ri = TRANS ? k : RG - 1 - k;
+            const int i = RG * qq + ri;
             if (i >= n) continue;
-            if (rg == (i & 7) && col_ok) {
+            if (rg == ri && col_ok) {
                 renorm(acc[qq]);
-                if (!unit) acc[qq] = div(acc[qq], dd{s.uh[i][i], s.ul[i][i]});
-                s.xh[i][col] = acc[qq].hi;
-                s.xl[i][col] = acc[qq].lo;
+                if (!unit) {
+                    const int kd = TRANS ? tri_start(i) : col_start(i) + i;
+                    acc[qq] = div(acc[qq], dd{uh[kd], ul[kd]});
+                }
+                xh[i * COLS + col] = acc[qq].hi;
+                xl[i * COLS + col] = acc[qq].lo;
             }
             __syncthreads();
             if (col_ok) {
                 // eliminate x_i: U^T: rows r > i use U(i, r); U: rows r < i use U(r, i)
-                const dd x{s.xh[i][col], s.xl[i][col]};
+                const dd x{xh[i * COLS + col], xl[i * COLS + col]};
+                const int base = TRANS ? tri_start(i) - i : col_start(i);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int r = rg + 8 * q;
-                    if (r < n && (TRANS ? r > i : r < i)) {
-                        const dd u = TRANS ? dd{s.uh[i][r], s.ul[i][r]}
-                                           : dd{s.uh[r][i], s.ul[r][i]};
-                        mac_deferred(acc[q], dd{-u.hi, -u.lo}, x);
-                    }
+                for (int q = 0; q < RPT; ++q) {
+                    const int r = rg + RG * q;
+                    if (r < n && (TRANS ? r > i : r < i))
+                        mac_deferred(acc[q], dd{-uh[base + r], -ul[base + r]}, x);
                 }
                 if ((step & (kRenormEvery - 1)) == kRenormEvery - 1) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) renorm(acc[q]);
+                    for (int q = 0; q < RPT; ++q) renorm(acc[q]);
                 }
             }
             ++step;
         }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int r = rg + 8 * q;
+    for (int q = 0; q < RPT; ++q) {
+        const int r = rg + RG * q;
         if (r < n && col_ok) {
             renorm(acc[q]);
             const int64_t o = uidx(d.lower_b, r, c0 + col, d.ldb);
@@ -278,29 +289,79 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s, Trsm
     }
 }
 
-__device__ __forceinline__ void trsm_any(const mp_dd_trsm_desc &d, int64_t c0, TrsmSmem &s,
+template <int RG>
+__device__ __forceinline__ void trsm_any(const mp_dd_trsm_desc &d, int64_t c0, double *sm,
                                          TrsmScale sc) {
     if (d.trans)
-        trsm_one<1>(d, c0, s, sc);
+        trsm_one<1, RG>(d, c0, sm, sc);
     else
-        trsm_one<0>(d, c0, s, sc);
+        trsm_one<0, RG>(d, c0, sm, sc);
 }
 
+template <int RG>
 __global__ void __launch_bounds__(NT, 2) trsm_batch_kernel(const mp_dd_trsm_desc *ds) {
     extern __shared__ double smem_t[];
-    trsm_any(ds[blockIdx.x], (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t),
-             TrsmScale{dd{1.0, 0.0}, 0});
+    trsm_any<RG>(ds[blockIdx.x], (int64_t)blockIdx.y * (NT / RG), smem_t,
+                 TrsmScale{dd{1.0, 0.0}, 0});
 }
 
+template <int RG>
 __global__ void __launch_bounds__(NT, 2) trsm_single_kernel(const mp_dd_trsm_desc d,
                                                          TrsmScale sc) {
     extern __shared__ double smem_t[];
-    trsm_any(d, (int64_t)blockIdx.y * TC, *reinterpret_cast<TrsmSmem *>(smem_t), sc);
+    trsm_any<RG>(d, (int64_t)blockIdx.y * (NT / RG), smem_t, sc);
 }
 
 constexpr TrsmScale kNoScale{dd{1.0, 0.0}, 0};
 
+// Row groups for count solves of nrhs columns: the widest CTAs (most
+// columns each) that still give every SM two of them, else 4 columns.
+int trsm_row_groups(int64_t count, int64_t nrhs) {
+    const int64_t want = 2 * (int64_t)(sm_count() > 0 ? sm_count() : 152);
+    for (int rg = 8; rg <= 32; rg *= 2)
+        if (count * ceil_div(nrhs, NT / rg) >= want) return rg;
+    return 64;
+}
+
+// One launch of count solves (ds on the device) or of the single solve d.
+int launch_trsm(const mp_dd_trsm_desc *ds, int64_t count, const mp_dd_trsm_desc &d,
+                TrsmScale sc, int64_t nrhs, cudaStream_t st) {
+    const int rg = trsm_row_groups(ds != nullptr ? count : 1, nrhs);
+    const int64_t gy = ceil_div(nrhs, NT / rg);
+    if (gy > 65535) return fail(MP_DD_ERR_TOO_LARGE, "too many right-hand sides");
+    const dim3 grid(ds != nullptr ? (unsigned)count : 1u, (unsigned)gy);
+    const size_t sm = trsm_smem_bytes(rg);
+    switch (rg) {
+#define MPDD_TRSM_CASE(RG)                                                  \
+    case RG:                                                                \
+        if (ds != nullptr)                                                  \
+            trsm_batch_kernel<RG><<<grid, NT, sm, st>>>(ds);                \
+        else                                                                \
+            trsm_single_kernel<RG><<<grid, NT, sm, st>>>(d, sc);            \
+        break;
+        MPDD_TRSM_CASE(8) MPDD_TRSM_CASE(16) MPDD_TRSM_CASE(32) MPDD_TRSM_CASE(64)
+#undef MPDD_TRSM_CASE
+    }
+    return check_launch(ds != nullptr ? "trsm_batch_kernel" : "trsm_single_kernel");
+}
+
+int launch_trsm_single(const mp_dd_trsm_desc &d, TrsmScale sc, cudaStream_t st) {
+    return launch_trsm(nullptr, 1, d, sc, d.nrhs, st);
+}
+
 bool g_attr_done = false;
+
+template <int RG>
+cudaError_t trsm_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(trsm_batch_kernel<RG>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)trsm_smem_bytes(RG));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(trsm_single_kernel<RG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)trsm_smem_bytes(RG));
+    return e;
+}
 
 int set_attrs() {
     if (g_attr_done) return 0;
@@ -311,13 +372,10 @@ int set_attrs() {
         e = cudaFuncSetAttribute(potrf_diag_single_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(DiagSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(trsm_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(TrsmSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(trsm_single_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(TrsmSmem));
+    if (e == cudaSuccess) e = trsm_attrs<8>();
+    if (e == cudaSuccess) e = trsm_attrs<16>();
+    if (e == cudaSuccess) e = trsm_attrs<32>();
+    if (e == cudaSuccess) e = trsm_attrs<64>();
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(potrf kernels)");
     g_attr_done = true;
     return 0;
@@ -339,10 +397,8 @@ int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
     if (count == 0 || max_rhs == 0) return 0;
     int rc = set_attrs();
     if (rc) return rc;
-    dim3 grid((unsigned)count, (unsigned)ceil_div(max_rhs, TC));
-    if (grid.y > 65535) return fail(MP_DD_ERR_TOO_LARGE, "too many right-hand sides");
-    trsm_batch_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(ds);
-    return check_launch("trsm_batch_kernel");
+    if (count > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "too many solves");
+    return launch_trsm(ds, count, mp_dd_trsm_desc{}, kNoScale, max_rhs, st);
 }
 
 // Trailing updates of at least this many rows go through the residue-form
@@ -381,9 +437,7 @@ int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t
         tr.b_hi = ah + ob; tr.b_lo = al + ob; tr.ldb = lda;
         tr.n = nb; tr.nrhs = rest; tr.trans = 1; tr.lower_u = lower; tr.lower_b = lower;
         tr.info = info;
-        dim3 grid(1, (unsigned)ceil_div(rest, TC));
-        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr, kNoScale);
-        if ((rc = check_launch("trsm_single_kernel"))) return rc;
+        if ((rc = launch_trsm_single(tr, kNoScale, st))) return rc;
         // trailing: A(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) on the stored triangle
         GemmArgs p{};
         p.m = rest; p.n = rest; p.k = nb;
@@ -424,9 +478,7 @@ int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double
         // read through the factor accessor
         tr.n = nb; tr.nrhs = nrhs; tr.trans = trans; tr.lower_u = lower; tr.lower_b = 0;
         tr.info = info;
-        dim3 grid(1, (unsigned)ceil_div(nrhs, TC));
-        trsm_single_kernel<<<grid, NT, sizeof(TrsmSmem), st>>>(tr, kNoScale);
-        return check_launch("trsm_single_kernel");
+        return launch_trsm_single(tr, kNoScale, st);
     };
     auto update = [&](int64_t j, int forward) -> int {
         const int64_t nb = n - j < NB ? n - j : NB;
@@ -507,10 +559,7 @@ int trsm_leaf(const TrsmPlan &P, int64_t j0, int64_t nt, bool first) {
     tr.n = nt; tr.nrhs = P.nrhs; tr.trans = P.forward; tr.lower_u = P.lower_a;
     tr.lower_b = P.right; tr.unit_diag = P.unit; tr.info = nullptr;
     const TrsmScale sc{dd{P.alpha.hi, P.alpha.lo}, first && !P.alpha_one};
-    const int64_t gy = ceil_div(P.nrhs, TC);
-    if (gy > 65535) return fail(MP_DD_ERR_TOO_LARGE, "Rtrsm: too many right-hand sides");
-    trsm_single_kernel<<<dim3(1, (unsigned)gy), NT, sizeof(TrsmSmem), P.st>>>(tr, sc);
-    return check_launch("trsm_single_kernel");
+    return launch_trsm_single(tr, sc, P.st);
 }
 
 // B'(rows r0 .. r0+mr) -= T(rows, cols c0 .. c0+kc) B'(cols), with beta = alpha

@@ -152,3 +152,19 @@ def test_deterministic(cuda_lib):
     a = gpu_trsm(cuda_lib, c)
     b = gpu_trsm(cuda_lib, c)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("transa", ["N", "T"])
+def test_result_independent_of_columns_per_cta(cuda_lib, transa):
+    """The solve kernel runs 32, 16, 8 or 4 right-hand-side columns per CTA
+    depending on how many columns there are; each column's result is the
+    same bits in every configuration."""
+    m, wide = 150, 10000
+    c = datagen.trsm_case(851, "L", "U", transa, "N", m, wide)
+    outs = []
+    for n in (6, 2500, 5000, wide):
+        B = tuple(np.asfortranarray(P[:, :n]) for P in c.B)
+        sub = datagen.TrsmCase(c.side, c.uplo, c.transa, c.diag, m, n, c.alpha, c.A, B)
+        outs.append(gpu_trsm(cuda_lib, sub))
+    for h, l in outs[1:]:
+        assert np.array_equal(h[:, :6], outs[0][0]) and np.array_equal(l[:, :6], outs[0][1])
