@@ -418,8 +418,9 @@ def routines_section(mp, torch, size):
     ms_c = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf_crt("U", n, S, n, info, ws, ws.numel()),
                      reset_s)
     out[f"Rpotrf_crt_U_{n}"] = {
-        "workload": f"dd Rpotrf uplo=U, n={n}, trailing updates of >= 512 rows as residue-form "
-                    "Rsyrk on the fp16 tensor cores", "ms": ms_c,
+        "workload": f"dd Rpotrf uplo=U, n={n}, outer steps of 256 columns; panel and trailing "
+                    "updates of >= 512 columns as residue-form Rgemm / Rsyrk on the fp16 tensor "
+                    "cores", "ms": ms_c,
         "dd_GFlops": float(n) ** 3 / 3 / (ms_c * 1e-3) / 1e9, "speedup_vs_fp64_pipe": ms / ms_c,
         "info": int(info.item())}
     del S0, S, ws

@@ -261,14 +261,17 @@ int mp_dd_Rgetrs(const char *trans, int64_t n, int64_t nrhs, mp_dd_cmat A, int64
  * -5 info NULL. */
 int mp_dd_Rpotrf(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info);
 
-/* Rpotrf with the trailing updates of 512 rows or more on the tensor cores:
- * each update U(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) (or the L form) is
- * one residue-form Rsyrk (see mp_dd_Rsyrk_crt) on the stored triangle, the
- * diagonal factors and panel solves as mp_dd_Rpotrf.  Same arguments,
- * semantics and info; after a failing pivot the later updates leave A as
- * it is.  workspace: device memory of at least mp_dd_Rpotrf_crt_workspace(n)
- * bytes (0 for n <= 512: then this is mp_dd_Rpotrf).  Errors: as
- * mp_dd_Rpotrf, 2003 workspace NULL or too small. */
+/* Rpotrf with the updates on the tensor cores.  Outer steps of 256 columns
+ * factor the diagonal block as mp_dd_Rpotrf does, solve the panel U(J, J+1:)
+ * by 64-row blocks (each first subtracting the blocks above it, a
+ * residue-form Rgemm, see mp_dd_Rgemm_crt) and update the trailing matrix
+ * with one residue-form Rsyrk of depth 256 (see mp_dd_Rsyrk_crt); updates
+ * of fewer than 512 columns run on the FP64 pipe.  Same arguments,
+ * semantics and info as mp_dd_Rpotrf; after a failing pivot the later
+ * updates leave A as it is.  workspace: device memory of at least
+ * mp_dd_Rpotrf_crt_workspace(n) bytes (0 for n < 768: then the call
+ * factors like mp_dd_Rpotrf).  Errors: as mp_dd_Rpotrf, 2003 workspace NULL
+ * or too small. */
 size_t mp_dd_Rpotrf_crt_workspace(int64_t n);
 int mp_dd_Rpotrf_crt(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info,
                      void *workspace, size_t workspace_bytes);

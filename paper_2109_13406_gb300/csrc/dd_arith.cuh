@@ -138,16 +138,39 @@ __device__ __forceinline__ dd div(dd a, dd b) {
     return q;
 }
 
+// dd division with a given approximate reciprocal y of b.hi (within a few
+// ulps): div's long division with the second quotient digit taken as
+// remainder * y instead of a second binary64 division, so the dependent
+// chain holds one division.  The second digit's extra relative error (a few
+// u) is scaled by |q2| <= ~3u |a / b|: the result's relative error stays
+// at most ~20 u^2, and an exactly representable quotient of binary64
+// operands is still exact (its remainder is 0).  a need not be
+// renormalised: |a.lo| may be a few ulps of a.hi.
+__device__ __forceinline__ dd div_rcp(dd a, dd b, double y) {
+    const double q1 = __ddiv_rn(a.hi, b.hi);
+    double r = __fma_rn(-q1, b.hi, a.hi);
+    r = __dadd_rn(r, __fma_rn(-q1, b.lo, a.lo));
+    const double q2 = __dmul_rn(r, y);
+    dd q;
+    fast_two_sum(q1, q2, q.hi, q.lo);
+    return q;
+}
+
 // dd square root: x = RN(sqrt(a.hi)), whose remainder a.hi - x^2 is a
 // binary64 number (one FMA gives it exactly), plus one Newton correction
-// (a - x^2) / (2x) with a.lo added; the neglected second-order term is
-// below u^2 / 8 relative.  Exact when a.hi is the square of a binary64
-// number and a.lo = 0.  Returns 0 for a <= 0.
-__device__ __forceinline__ dd sqrt_dd(dd a) {
+// (a - x^2) / (2x) with a.lo added, the division taken as a product with
+// z = rsqrt(a.hi) (1 ulp); the neglected second-order term is below u^2 / 8
+// relative.  Exact when a.hi is the square of a binary64 number and a.lo =
+// 0.  z, an approximate reciprocal of the result's leading part within a
+// few ulps, is returned for div_rcp.  a need not be renormalised.  Returns
+// 0 (and z = 0) for a <= 0.
+__device__ __forceinline__ dd sqrt_dd(dd a, double &z) {
+    z = 0.0;
     if (!(a.hi > 0.0)) return dd{0.0, 0.0};
     const double x = __dsqrt_rn(a.hi);
+    z = rsqrt(a.hi);
     const double r = __dadd_rn(__fma_rn(-x, x, a.hi), a.lo);
-    const double corr = __ddiv_rn(r, __dadd_rn(x, x));
+    const double corr = __dmul_rn(__dmul_rn(r, z), 0.5);
     dd s;
     fast_two_sum(x, corr, s.hi, s.lo);
     return s;

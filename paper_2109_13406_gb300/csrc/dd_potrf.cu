@@ -40,8 +40,11 @@ __host__ __device__ __forceinline__ int64_t uidx(int lower, int64_t i, int64_t j
 // entries t + 256 s (s = 0..8) as dd accumulators; the rows that are done
 // form a prefix of that numbering, so a warp whose entries are all done
 // issues nothing.  Step j: the holder of (j, j) takes the square root of its
-// accumulator; after a barrier the holders of row j divide by it and publish
-// the row in shared memory (two buffers by the parity of j); after a second
+// accumulator, with an approximate reciprocal of it; after a barrier the
+// holders of row j divide by it (one binary64 division each, div_rcp) and
+// publish the row in shared memory (two buffers by the parity of j); every
+// FP64 instruction on this chain costs the warp ~64 cycles on GB300, so
+// the chain is kept short.  After a second
 // barrier every entry (r, c) with j < r <= c subtracts U(j, r) U(j, c), with
 // the GEMM kernels' deferred renormalisation (every entry has taken
 // exactly j + 1 updates after step j, so all renormalise at the same steps).
@@ -50,7 +53,7 @@ constexpr int kSlots = (kTri + NT - 1) / NT;
 
 struct DiagSmem {
     double rh[2][NB], rl[2][NB];   // the pivot row U(j, :)
-    double uh, ul;                 // U(j, j)
+    double uh, ul, uz;             // U(j, j) and an approximate 1 / U(j, j)
     int fail;
 };
 
@@ -104,17 +107,19 @@ __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
         if (tid == e0 % NT) {
             const int q = e0 / NT;
             dd p = pick(acc, q);
-            renorm(p);
             if (!(p.hi > 0.0)) {
+                renorm(p);
                 s.fail = 1;
                 if (d.info != nullptr)
                     atomicCAS(reinterpret_cast<unsigned long long *>(d.info), 0ull,
                               (unsigned long long)(d.offset + j + 1));
                 put(acc, q, p);
             } else {
-                const dd u = sqrt_dd(p);
+                double z;
+                const dd u = sqrt_dd(p, z);
                 s.uh = u.hi;
                 s.ul = u.lo;
+                s.uz = z;
                 put(acc, q, u);
             }
         }
@@ -129,9 +134,7 @@ __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
             const int e = first + (tid - first % NT + NT) % NT;
             if (e < first + count) {
                 const int q = e / NT;
-                dd v = pick(acc, q);
-                renorm(v);
-                v = div(v, dd{s.uh, s.ul});
+                const dd v = div_rcp(pick(acc, q), dd{s.uh, s.ul}, s.uz);
                 put(acc, q, v);
                 const int c = j + 1 + (e - first);
                 s.rh[j & 1][c] = v.hi;
@@ -187,7 +190,7 @@ __device__ __forceinline__ int col_start(int c) { return (c * (c + 1)) / 2; }
 // Shared memory of one solve CTA with RG row groups: U's triangle packed
 // (hi, lo) and the solved rows x_i of its NT / RG columns.
 __host__ __device__ constexpr size_t trsm_smem_bytes(int rg) {
-    return sizeof(double) * (2 * (size_t)kTri + 2 * (size_t)NB * (NT / rg));
+    return sizeof(double) * (2 * (size_t)kTri + 2 * (size_t)NB * (NT / rg) + NB);
 }
 
 // Solve U^T X = B (trans = 1) or U X = B (trans = 0) for the columns
@@ -209,6 +212,7 @@ template <int TRANS, int RG>
 __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmScale sc) {
     constexpr int COLS = NT / RG, RPT = NB / RG;
     double *uh = sm, *ul = sm + kTri, *xh = sm + 2 * kTri, *xl = xh + NB * COLS;
+    double *rcp = xl + NB * COLS;   // 1 / U(i, i).hi
     const int n = (int)d.n;
     const int tid = threadIdx.x;
     if (d.info != nullptr && *d.info != 0) return;
@@ -224,6 +228,7 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmS
             const int k = TRANS ? tri_start(r) + (c - r) : col_start(c) + r;
             uh[k] = d.u_hi[o];
             ul[k] = d.u_lo[o];
+            if (r == c) rcp[r] = __drcp_rn(d.u_hi[o]);
         }
     }
     dd acc[RPT];
@@ -250,10 +255,11 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmS
             const int i = RG * qq + ri;
             if (i >= n) continue;
             if (rg == ri && col_ok) {
-                renorm(acc[qq]);
                 if (!unit) {
                     const int kd = TRANS ? tri_start(i) : col_start(i) + i;
-                    acc[qq] = div(acc[qq], dd{uh[kd], ul[kd]});
+                    acc[qq] = div_rcp(acc[qq], dd{uh[kd], ul[kd]}, rcp[i]);
+                } else {
+                    renorm(acc[qq]);
                 }
                 xh[i * COLS + col] = acc[qq].hi;
                 xl[i * COLS + col] = acc[qq].lo;
@@ -401,30 +407,18 @@ int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
     return launch_trsm(ds, count, mp_dd_trsm_desc{}, kNoScale, max_rhs, st);
 }
 
-// Trailing updates of at least this many rows go through the residue-form
-// Rsyrk when a workspace is given.
-constexpr int64_t kCrtMinRest = 512;
-
-size_t potrf_crt_workspace_bytes(int64_t n) {
-    return n > kCrtMinRest ? crt_workspace_bytes(n - 1, n - 1, NB, true) : 0;
-}
-
-// Blocked right-looking Cholesky of one matrix (LAPACK dpotrf order); with a
-// workspace (ws != nullptr) the trailing updates of kCrtMinRest rows or more
-// run on the tensor cores.
-int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
-              cudaStream_t st, void *ws, size_t ws_bytes) {
-    int rc = set_attrs();
-    if (rc) return rc;
-    if (info != nullptr) {
-        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), st);
-        if (e != cudaSuccess) return cuda_fail(e, "info reset");
-    }
+// The blocked right-looking Cholesky (LAPACK dpotrf order) of the n x n
+// block at (ah, al): 64-column steps of diagonal factor, panel solve and a
+// plain dd Rsyrk trailing update.  off is the block's position in the whole
+// matrix (for info).
+int potrf_blocked(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
+                  int64_t off, cudaStream_t st) {
+    int rc = 0;
     for (int64_t j = 0; j < n; j += NB) {
         const int64_t nb = n - j < NB ? n - j : NB;
         mp_dd_potrf_diag_desc dg{};
         int64_t o = uidx(lower, j, j, lda);
-        dg.a_hi = ah + o; dg.a_lo = al + o; dg.lda = lda; dg.n = nb; dg.offset = j;
+        dg.a_hi = ah + o; dg.a_lo = al + o; dg.lda = lda; dg.n = nb; dg.offset = off + j;
         dg.info = info; dg.lower = lower;
         potrf_diag_single_kernel<<<1, NT, sizeof(DiagSmem), st>>>(dg);
         if ((rc = check_launch("potrf_diag_single_kernel"))) return rc;
@@ -451,13 +445,108 @@ int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t
         p.ta = lower ? 0 : 1; p.tb = lower ? 1 : 0; p.tri = lower ? 2 : 1;
         p.alpha_zero = 0; p.alpha_one = 0; p.beta_zero = 0;
         p.info = info;
-        if (ws != nullptr && rest >= kCrtMinRest)
-            rc = run_crt(p, ws, ws_bytes, st);
-        else
-            rc = launch_gemm_plain(p, st);
+        if ((rc = launch_gemm_plain(p, st))) return rc;
+    }
+    return 0;
+}
+
+// The tensor-core form: outer steps of kOuter columns.  Each factors its
+// diagonal block with potrf_blocked, solves its panel P = U(J, J+1:) by
+// 64-row blocks, left-looking (block i first subtracts U_JJ(:i, i)^T
+// P(:i, :), a residue-form Rgemm with k = 64 i, then takes the 64-row
+// solve), and updates the trailing matrix with one residue-form Rsyrk of
+// k = kOuter.  Against 64-column steps this reconstructs about a quarter as
+// many entries (n^3 / (6 kOuter) instead of n^3 / 384) and runs the tensor
+// products with four times the depth; updates of fewer than kCrtMinRest
+// columns stay on the FP64 pipe.
+constexpr int64_t kCrtMinRest = 512;
+constexpr int64_t kOuter = 256;
+
+size_t potrf_crt_workspace_bytes(int64_t n) {
+    const int64_t rest = n - kOuter;
+    if (rest < kCrtMinRest) return 0;
+    size_t w = crt_workspace_bytes(rest, rest, kOuter, true);
+    const size_t g1 = crt_workspace_bytes(NB, rest, kOuter - NB, false);
+    const size_t g2 = crt_workspace_bytes(rest, NB, kOuter - NB, false);
+    if (g1 > w) w = g1;
+    if (g2 > w) w = g2;
+    return w;
+}
+
+int potrf_crt(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
+              cudaStream_t st, void *ws, size_t ws_bytes) {
+    int rc = 0;
+    for (int64_t J = 0; J < n; J += kOuter) {
+        const int64_t nbo = n - J < kOuter ? n - J : kOuter;
+        const int64_t oJ = uidx(lower, J, J, lda);
+        if ((rc = potrf_blocked(lower, nbo, ah + oJ, al + oJ, lda, info, J, st))) return rc;
+        const int64_t rest = n - J - nbo;
+        if (rest <= 0) break;
+        const bool crt = rest >= kCrtMinRest;
+        const int64_t oP = uidx(lower, J, J + nbo, lda);      // the panel
+        for (int64_t i = 0; i < nbo; i += NB) {
+            const int64_t nb = nbo - i < NB ? nbo - i : NB;
+            if (i > 0) {
+                GemmArgs p{};
+                p.k = i;
+                p.alpha = mp_dd{-1.0, 0.0}; p.beta = mp_dd{1.0, 0.0};
+                p.alpha_zero = 0; p.alpha_one = 0; p.beta_zero = 0; p.tri = 0;
+                p.info = info;
+                const int64_t oC = uidx(lower, J + i, J + nbo, lda);
+                const int64_t oU = uidx(lower, J, J + i, lda);  // U_JJ(:i, i:i+nb)
+                p.ch = ah + oC; p.cl = al + oC; p.ldc = lda;
+                if (!lower) {
+                    // U(J+i, J+nbo:) (nb x rest) -= U_JJ(:i, i:)^T (nb x i) P(:i, :) (i x rest)
+                    p.m = nb; p.n = rest; p.ta = 1; p.tb = 0;
+                    p.ah = ah + oU; p.al = al + oU; p.lda = lda;
+                    p.bh = ah + oP; p.bl = al + oP; p.ldb = lda;
+                } else {
+                    // L(J+nbo:, J+i) (rest x nb) -= P(:, :i) (rest x i) L_JJ(i:, :i)^T (i x nb)
+                    p.m = rest; p.n = nb; p.ta = 0; p.tb = 1;
+                    p.ah = ah + oP; p.al = al + oP; p.lda = lda;
+                    p.bh = ah + oU; p.bl = al + oU; p.ldb = lda;
+                }
+                rc = crt ? run_crt(p, ws, ws_bytes, st) : launch_gemm_plain(p, st);
+                if (rc) return rc;
+            }
+            mp_dd_trsm_desc tr{};
+            const int64_t od = uidx(lower, J + i, J + i, lda);
+            const int64_t ob = uidx(lower, J + i, J + nbo, lda);
+            tr.u_hi = ah + od; tr.u_lo = al + od; tr.ldu = lda;
+            tr.b_hi = ah + ob; tr.b_lo = al + ob; tr.ldb = lda;
+            tr.n = nb; tr.nrhs = rest; tr.trans = 1; tr.lower_u = lower; tr.lower_b = lower;
+            tr.info = info;
+            if ((rc = launch_trsm_single(tr, kNoScale, st))) return rc;
+        }
+        // trailing: A(J+1:, J+1:) -= P^T P (upper) / P P^T (lower), k = nbo
+        GemmArgs p{};
+        p.m = rest; p.n = rest; p.k = nbo;
+        p.alpha = mp_dd{-1.0, 0.0}; p.beta = mp_dd{1.0, 0.0};
+        p.ah = ah + oP; p.al = al + oP; p.lda = lda;
+        p.bh = ah + oP; p.bl = al + oP; p.ldb = lda;
+        const int64_t oC = uidx(lower, J + nbo, J + nbo, lda);
+        p.ch = ah + oC; p.cl = al + oC; p.ldc = lda;
+        p.ta = lower ? 0 : 1; p.tb = lower ? 1 : 0; p.tri = lower ? 2 : 1;
+        p.alpha_zero = 0; p.alpha_one = 0; p.beta_zero = 0;
+        p.info = info;
+        rc = crt ? run_crt(p, ws, ws_bytes, st) : launch_gemm_plain(p, st);
         if (rc) return rc;
     }
     return 0;
+}
+
+// Cholesky of one matrix; with a workspace (ws != nullptr) the tensor-core
+// form above.
+int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
+              cudaStream_t st, void *ws, size_t ws_bytes) {
+    int rc = set_attrs();
+    if (rc) return rc;
+    if (info != nullptr) {
+        cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "info reset");
+    }
+    if (ws != nullptr) return potrf_crt(lower, n, ah, al, lda, info, st, ws, ws_bytes);
+    return potrf_blocked(lower, n, ah, al, lda, info, 0, st);
 }
 
 // Solve A X = B with the factor of run_potrf (blocked forward and backward

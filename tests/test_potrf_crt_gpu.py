@@ -1,7 +1,8 @@
 """dd Rpotrf with residue-form (tensor-core) trailing updates (GPU).
 
-The blocked Cholesky of Sec. 10.5's Rpotrf benchmark where every trailing
-update of 512 rows or more is one residue-form Rsyrk.  Pins: an integer
+The Cholesky of Sec. 10.5's Rpotrf benchmark in outer steps of 256 columns
+whose panel and trailing updates of 512 columns or more are residue-form
+Rgemm / Rsyrk calls.  Pins: an integer
 Cholesky factor is recovered bit-exactly (each update is exact and the
 Schur complements stay integers); on an SPD matrix of condition ~1e20 the
 componentwise backward error |U^T U - A| <= c n eps (|U|^T |U|) (the
@@ -44,14 +45,14 @@ def upper_factor(uplo, fh, fl):
 def test_workspace_size_and_threshold(cuda_lib):
     mp = cuda_lib
     assert mp.mp_dd_Rpotrf_crt_workspace(0) == 0
-    assert mp.mp_dd_Rpotrf_crt_workspace(512) == 0
-    assert mp.mp_dd_Rpotrf_crt_workspace(700) >= mp.mp_dd_Rsyrk_crt_workspace(636, 64)
-    assert mp.mp_dd_Rpotrf_crt_workspace(1400) >= mp.mp_dd_Rpotrf_crt_workspace(700)
+    assert mp.mp_dd_Rpotrf_crt_workspace(767) == 0
+    assert mp.mp_dd_Rpotrf_crt_workspace(768) >= mp.mp_dd_Rsyrk_crt_workspace(512, 256)
+    assert mp.mp_dd_Rpotrf_crt_workspace(1400) >= mp.mp_dd_Rsyrk_crt_workspace(1144, 256)
 
 
 @pytest.mark.parametrize("uplo", ["U", "L"])
 def test_integer_factor_recovered_exactly(cuda_lib, uplo):
-    n = 700                            # updates of 636 and 572 rows on the tensor cores
+    n = 900                            # a 644-column panel and update on the tensor cores
     g = datagen.rng(620)
     U = np.triu(g.integers(-3, 4, (n, n))).astype(np.float64)
     np.fill_diagonal(U, g.integers(1, 5, n))
@@ -88,7 +89,7 @@ def componentwise_ratio(Ut, Fs, rows, cols):
 @pytest.mark.parametrize("uplo", ["U", "L"])
 def test_ill_conditioned_backward_error_and_solve(cuda_lib, uplo):
     mp = cuda_lib
-    n = 640
+    n = 800
     G, B, Fs = spd_problem(621, n)
     F, info = potrf_crt(mp, uplo, *Fs)
     assert info == 0
@@ -135,7 +136,7 @@ def test_failing_minor_info_and_untouched_trailing_block(cuda_lib, uplo, fail_at
 
 
 def test_deterministic(cuda_lib):
-    n = 600
+    n = 800
     _, _, Fs = spd_problem(623, n)
     a, _ = potrf_crt(cuda_lib, "L", *Fs)
     b, _ = potrf_crt(cuda_lib, "L", *Fs)
@@ -146,7 +147,7 @@ def test_deterministic(cuda_lib):
 
 def test_errors_and_quick_return(cuda_lib):
     mp = cuda_lib
-    n = 600
+    n = 800
     F = dev((np.eye(n), np.zeros((n, n))))
     info = torch.full((1,), 7, dtype=torch.int64, device="cuda")
     need = mp.mp_dd_Rpotrf_crt_workspace(n)
@@ -158,7 +159,7 @@ def test_errors_and_quick_return(cuda_lib):
     assert mp.mp_dd_Rpotrf_crt("U", n, F, n, None, ws, need, check=False) == -5
     assert mp.mp_dd_Rpotrf_crt("U", n, F, n, info, None, 0, check=False) == 2003
     assert mp.mp_dd_Rpotrf_crt("U", n, F, n, info, ws, need - 1, check=False) == 2003
-    # n = 0 resets info; n <= 512 needs no workspace (the FP64-pipe path)
+    # n = 0 resets info; n < 768 needs no workspace (the FP64-pipe path)
     assert mp.mp_dd_Rpotrf_crt("U", 0, F, 1, info, None, 0, check=False) == 0
     assert int(info.item()) == 0
     S = dev((np.eye(300) * 9.0, np.zeros((300, 300))))
