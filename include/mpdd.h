@@ -289,9 +289,11 @@ int mp_dd_Rpotrs(const char *uplo, int64_t n, int64_t nrhs, mp_dd_cmat A, int64_
  * manual), used to advance many independent factorisations in one launch.
  * Descriptor arrays are DEVICE memory. */
 
-/* Unblocked dd Cholesky of one diagonal block (n <= 64) whose top-left
- * element is a_hi/a_lo; lower selects the 'L' storage.  offset is the
- * block's first column in the whole matrix (for info = offset + j + 1). */
+/* Unblocked dd Cholesky of one diagonal block (n <= 64; a larger n is
+ * taken as 64) whose top-left element is a_hi/a_lo; lower selects the 'L'
+ * storage.  offset is the block's first column in the whole matrix (for
+ * info = offset + j + 1).  A launch runs each block on a cluster of up to 8
+ * CTAs (fewer as count grows); the result does not depend on it. */
 typedef struct {
     double *a_hi, *a_lo;
     int64_t lda, n, offset;
@@ -300,7 +302,7 @@ typedef struct {
 } mp_dd_potrf_diag_desc;
 
 /* Solve U^T X = B (trans 1) or U X = B (trans 0) in place, U the n x n
- * (n <= 64) upper factor block at u_hi/u_lo (lower_u: read it from 'L'
+ * (n <= 64; a larger n is taken as 64) upper factor block at u_hi/u_lo (lower_u: read it from 'L'
  * storage), B n x nrhs at b_hi/b_lo (lower_b: B is stored transposed, as
  * the panel of an 'L' factor is).  unit_diag != 0 takes U's diagonal as
  * one without reading it. */

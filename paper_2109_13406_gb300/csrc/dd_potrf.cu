@@ -4,7 +4,7 @@
 // triangular solve Rtrsm (MPBLAS, Sec. 6) on the same two of them:
 //
 //  * diag:  unblocked Cholesky of one nb x nb diagonal block (nb <= 64), in
-//           shared memory, one CTA per block;
+//           registers, on a cluster of up to 8 CTAs per block;
 //  * trsm:  triangular solve with one nb x nb factor block for 4 to 32
 //           right-hand-side columns per CTA (forward with U^T, backward
 //           with U), optionally scaling the right-hand sides by alpha and
@@ -20,9 +20,13 @@
 // of order j is not positive definite.  The first failing pivot is
 // recorded; the launches that follow see info != 0 and leave their matrices
 // untouched.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "dd_arith.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mpdd {
 namespace {
@@ -35,116 +39,162 @@ __host__ __device__ __forceinline__ int64_t uidx(int lower, int64_t i, int64_t j
 }
 
 // Unblocked Cholesky of one nb x nb block (nb <= 64), right-looking, with
-// the block's upper triangle in registers.  The triangle's 2080 entries are
-// numbered row by row (row r holds columns r..63) and thread t holds the
-// entries t + 256 s (s = 0..8) as dd accumulators; the rows that are done
-// form a prefix of that numbering, so a warp whose entries are all done
-// issues nothing.  Step j: the holder of (j, j) takes the square root of its
-// accumulator, with an approximate reciprocal of it; after a barrier the
-// holders of row j divide by it (one binary64 division each, div_rcp) and
-// publish the row in shared memory (two buffers by the parity of j); every
-// FP64 instruction on this chain costs the warp ~64 cycles on GB300, so
-// the chain is kept short.  After a second
-// barrier every entry (r, c) with j < r <= c subtracts U(j, r) U(j, c), with
-// the GEMM kernels' deferred renormalisation (every entry has taken
-// exactly j + 1 updates after step j, so all renormalise at the same steps).
+// the block's upper triangle in registers, on a cluster of CL CTAs.  The
+// triangle's 2080 entries are numbered row by row (row r holds columns
+// r..63) and thread g of the cluster (g = rank * 256 + tid) holds the
+// entries g + 256 CL s as dd accumulators; the rows that are done form a
+// prefix of that numbering, so a warp whose entries are all done issues
+// nothing.  Step j: the holder of (j, j) takes the square root of its
+// accumulator, with an approximate reciprocal of it, and writes both into
+// every CTA's shared memory; after a cluster barrier the holders of row j
+// divide by it (one binary64 division each, div_rcp) and write the row into
+// every CTA (two buffers by the parity of j); after a second barrier every
+// entry (r, c) with j < r <= c subtracts U(j, r) U(j, c), with the GEMM
+// kernels' deferred renormalisation (every entry has taken exactly j + 1
+// updates after step j, so all renormalise at the same steps).
+//
+// Every FP64 instruction costs a warp ~64 cycles on GB300 (2 FP64 lanes per
+// clock per SM), so the square root / division chain is kept short and the
+// update, which is FP64-throughput work, is spread over the CL SMs.
 constexpr int kTri = NB * (NB + 1) / 2;
-constexpr int kSlots = (kTri + NT - 1) / NT;
 
 struct DiagSmem {
     double rh[2][NB], rl[2][NB];   // the pivot row U(j, :)
     double uh, ul, uz;             // U(j, j) and an approximate 1 / U(j, j)
-    int fail;
+    int fail;                      // a pivot failed (or info was set on entry)
 };
 
 __device__ __forceinline__ int tri_start(int r) { return r * NB - (r * (r - 1)) / 2; }
 
 // acc[s] with a run-time s, without local memory
-__device__ __forceinline__ dd pick(const dd (&acc)[kSlots], int s) {
+template <int S>
+__device__ __forceinline__ dd pick(const dd (&acc)[S], int s) {
     dd v = acc[0];
 #pragma unroll
-    for (int q = 1; q < kSlots; ++q)
+    for (int q = 1; q < S; ++q)
         if (q == s) v = acc[q];
     return v;
 }
 
-__device__ __forceinline__ void put(dd (&acc)[kSlots], int s, dd v) {
+template <int S>
+__device__ __forceinline__ void put(dd (&acc)[S], int s, dd v) {
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q)
+    for (int q = 0; q < S; ++q)
         if (q == s) acc[q] = v;
 }
 
+template <int CL>
+struct DiagCluster {
+    DiagSmem *peer[CL];   // every CTA's shared block (peer[rank] is our own)
+    int rank;
+    __device__ DiagCluster(DiagSmem &s) {
+        if constexpr (CL > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            rank = (int)cl.block_rank();
+#pragma unroll
+            for (int r = 0; r < CL; ++r) peer[r] = cl.map_shared_rank(&s, (unsigned)r);
+        } else {
+            rank = 0;
+            peer[0] = &s;
+        }
+    }
+    __device__ void sync() const {
+        if constexpr (CL > 1)
+            cg::this_cluster().sync();
+        else
+            __syncthreads();
+    }
+};
+
+template <int CL>
 __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
-    const int nbe = (int)d.n;
-    const int tid = threadIdx.x;
-    if (d.info != nullptr && *d.info != 0) return;   // an earlier block failed
+    constexpr int G = CL * NT;                       // threads of the cluster
+    constexpr int kSl = (kTri + G - 1) / G;          // entries per thread
+    const int nbe = d.n < NB ? (int)d.n : NB;        // (n > 64 is taken as 64)
+    DiagCluster<CL> cl(s);
+    const int g = cl.rank * NT + (int)threadIdx.x;
+    // one decision for the whole cluster: an earlier block failed
+    cl.sync();                                       // every CTA has started
+    if (g == 0) {
+        const int stop = d.info != nullptr && *d.info != 0;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) cl.peer[r]->fail = stop;
+    }
+    cl.sync();
+    if (s.fail) return;
     // the (row, column) of each entry this thread holds; c = NB marks none
-    int er[kSlots], ec[kSlots];
+    int er[kSl], ec[kSl];
     {
         int r = 0;
 #pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
-            const int e = tid + NT * q;
+        for (int q = 0; q < kSl; ++q) {
+            const int e = g + G * q;
             while (r < NB - 1 && tri_start(r + 1) <= e) ++r;
             const bool ok = e < kTri && r + (e - tri_start(r)) < nbe;
             er[q] = ok ? r : NB;
             ec[q] = ok ? r + (e - tri_start(r)) : NB;
         }
     }
-    dd acc[kSlots];
+    dd acc[kSl];
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) {
+    for (int q = 0; q < kSl; ++q) {
         acc[q] = dd{0.0, 0.0};
         if (ec[q] < NB) {
             const int64_t o = uidx(d.lower, er[q], ec[q], d.lda);
             acc[q] = dd{d.a_hi[o], d.a_lo[o]};
         }
     }
-    if (tid == 0) s.fail = 0;
     int jdone = nbe;
     for (int j = 0; j < nbe; ++j) {
-        const int e0 = tri_start(j);             // (j, j)
-        if (tid == e0 % NT) {
-            const int q = e0 / NT;
+        const int e0 = tri_start(j);                 // (j, j)
+        if (g == e0 % G) {
+            const int q = e0 / G;
             dd p = pick(acc, q);
             if (!(p.hi > 0.0)) {
                 renorm(p);
-                s.fail = 1;
+                put(acc, q, p);
                 if (d.info != nullptr)
                     atomicCAS(reinterpret_cast<unsigned long long *>(d.info), 0ull,
                               (unsigned long long)(d.offset + j + 1));
-                put(acc, q, p);
+#pragma unroll
+                for (int r = 0; r < CL; ++r) cl.peer[r]->fail = 1;
             } else {
                 double z;
                 const dd u = sqrt_dd(p, z);
-                s.uh = u.hi;
-                s.ul = u.lo;
-                s.uz = z;
                 put(acc, q, u);
+#pragma unroll
+                for (int r = 0; r < CL; ++r) {
+                    cl.peer[r]->uh = u.hi;
+                    cl.peer[r]->ul = u.lo;
+                    cl.peer[r]->uz = z;
+                }
             }
         }
-        __syncthreads();
-        if (s.fail) {
+        cl.sync();
+        if (s.fail) {                                // the same in every CTA
             jdone = j;
             break;
         }
         // row j: the entries e0 + 1 .. e0 + nbe - j - 1, at most one per thread
         {
             const int first = e0 + 1, count = nbe - j - 1;
-            const int e = first + (tid - first % NT + NT) % NT;
+            const int e = first + (g - first % G + G) % G;
             if (e < first + count) {
-                const int q = e / NT;
+                const int q = e / G;
                 const dd v = div_rcp(pick(acc, q), dd{s.uh, s.ul}, s.uz);
                 put(acc, q, v);
                 const int c = j + 1 + (e - first);
-                s.rh[j & 1][c] = v.hi;
-                s.rl[j & 1][c] = v.lo;
+#pragma unroll
+                for (int r = 0; r < CL; ++r) {
+                    cl.peer[r]->rh[j & 1][c] = v.hi;
+                    cl.peer[r]->rl[j & 1][c] = v.lo;
+                }
             }
         }
-        __syncthreads();
+        cl.sync();
         const bool renorm_now = (j & (kRenormEvery - 1)) == kRenormEvery - 1;
 #pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
+        for (int q = 0; q < kSl; ++q) {
             if (er[q] > j && ec[q] < NB) {
                 const dd ur{-s.rh[j & 1][er[q]], -s.rl[j & 1][er[q]]};
                 const dd uc{s.rh[j & 1][ec[q]], s.rl[j & 1][ec[q]]};
@@ -156,7 +206,7 @@ __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
     // rows r < jdone hold their final values; a failing pivot leaves the
     // rest partially updated (LAPACK leaves the trailing block unspecified)
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) {
+    for (int q = 0; q < kSl; ++q) {
         if (ec[q] < NB) {
             dd v = acc[q];
             if (er[q] >= jdone) renorm(v);
@@ -165,16 +215,61 @@ __device__ void potrf_diag_one(const mp_dd_potrf_diag_desc &d, DiagSmem &s) {
             d.a_lo[o] = v.lo;
         }
     }
+    cl.sync();   // no CTA leaves while another may still address its shared memory
 }
 
+template <int CL>
 __global__ void __launch_bounds__(NT) potrf_diag_batch_kernel(const mp_dd_potrf_diag_desc *ds) {
     extern __shared__ double smem_d[];
-    potrf_diag_one(ds[blockIdx.x], *reinterpret_cast<DiagSmem *>(smem_d));
+    potrf_diag_one<CL>(ds[blockIdx.x / CL], *reinterpret_cast<DiagSmem *>(smem_d));
 }
 
+template <int CL>
 __global__ void __launch_bounds__(NT) potrf_diag_single_kernel(const mp_dd_potrf_diag_desc d) {
     extern __shared__ double smem_d[];
-    potrf_diag_one(d, *reinterpret_cast<DiagSmem *>(smem_d));
+    potrf_diag_one<CL>(d, *reinterpret_cast<DiagSmem *>(smem_d));
+}
+
+// Cluster size for count diagonal blocks: the largest of 8, 4, 2 that keeps
+// every cluster on its own SMs, else 1.
+int diag_cluster(int64_t count) {
+    const int64_t sms = sm_count() > 0 ? sm_count() : 152;
+    for (int cl = 8; cl >= 2; cl /= 2)
+        if (count * cl <= sms) return cl;
+    return 1;
+}
+
+template <int CL>
+int launch_diag_cl(const mp_dd_potrf_diag_desc *ds, int64_t count,
+                   const mp_dd_potrf_diag_desc &d, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)((ds != nullptr ? count : 1) * CL));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sizeof(DiagSmem);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = ds != nullptr ? cudaLaunchKernelEx(&cfg, potrf_diag_batch_kernel<CL>, ds)
+                                  : cudaLaunchKernelEx(&cfg, potrf_diag_single_kernel<CL>, d);
+    if (e != cudaSuccess) return cuda_fail(e, "potrf diagonal-block launch");
+    return check_launch("potrf_diag_kernel");
+}
+
+// One launch over count diagonal blocks (ds on the device) or of the single
+// block d.
+int launch_diag(const mp_dd_potrf_diag_desc *ds, int64_t count, const mp_dd_potrf_diag_desc &d,
+                cudaStream_t st) {
+    switch (diag_cluster(ds != nullptr ? count : 1)) {
+        case 8: return launch_diag_cl<8>(ds, count, d, st);
+        case 4: return launch_diag_cl<4>(ds, count, d, st);
+        case 2: return launch_diag_cl<2>(ds, count, d, st);
+        default: return launch_diag_cl<1>(ds, count, d, st);
+    }
 }
 
 // ------------------------------------------------------------------ trsm
@@ -213,7 +308,7 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmS
     constexpr int COLS = NT / RG, RPT = NB / RG;
     double *uh = sm, *ul = sm + kTri, *xh = sm + 2 * kTri, *xl = xh + NB * COLS;
     double *rcp = xl + NB * COLS;   // 1 / U(i, i).hi
-    const int n = (int)d.n;
+    const int n = d.n < NB ? (int)d.n : NB;   // (n > 64 is taken as 64)
     const int tid = threadIdx.x;
     if (d.info != nullptr && *d.info != 0) return;
     const int64_t ncol = d.nrhs - c0 < COLS ? d.nrhs - c0 : COLS;
@@ -371,14 +466,7 @@ cudaError_t trsm_attrs() {
 
 int set_attrs() {
     if (g_attr_done) return 0;
-    cudaError_t e = cudaFuncSetAttribute(potrf_diag_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(DiagSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(potrf_diag_single_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(DiagSmem));
-    if (e == cudaSuccess) e = trsm_attrs<8>();
+    cudaError_t e = trsm_attrs<8>();
     if (e == cudaSuccess) e = trsm_attrs<16>();
     if (e == cudaSuccess) e = trsm_attrs<32>();
     if (e == cudaSuccess) e = trsm_attrs<64>();
@@ -394,8 +482,7 @@ int launch_potrf_diag_batch(int64_t count, const mp_dd_potrf_diag_desc *ds, cuda
     int rc = set_attrs();
     if (rc) return rc;
     if (count > 0x7fffffffLL) return fail(MP_DD_ERR_TOO_LARGE, "too many blocks");
-    potrf_diag_batch_kernel<<<(unsigned)count, NT, sizeof(DiagSmem), st>>>(ds);
-    return check_launch("potrf_diag_batch_kernel");
+    return launch_diag(ds, count, mp_dd_potrf_diag_desc{}, st);
 }
 
 int launch_trsm_batch(int64_t count, const mp_dd_trsm_desc *ds, int64_t max_rhs,
@@ -420,8 +507,7 @@ int potrf_blocked(int lower, int64_t n, double *ah, double *al, int64_t lda, int
         int64_t o = uidx(lower, j, j, lda);
         dg.a_hi = ah + o; dg.a_lo = al + o; dg.lda = lda; dg.n = nb; dg.offset = off + j;
         dg.info = info; dg.lower = lower;
-        potrf_diag_single_kernel<<<1, NT, sizeof(DiagSmem), st>>>(dg);
-        if ((rc = check_launch("potrf_diag_single_kernel"))) return rc;
+        if ((rc = launch_diag(nullptr, 1, dg, st))) return rc;
         const int64_t rest = n - j - nb;
         if (rest <= 0) break;
         // panel: U(J, J+1:) := U_JJ^-T A(J, J+1:)

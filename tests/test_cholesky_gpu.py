@@ -177,3 +177,35 @@ def test_server_admission_respects_budget_and_slots(cuda_lib):
     done = srv.serve(reqs)
     assert len(done) == 6 and srv.max_active <= 2 and srv.used == 0
     assert all(r.info == 0 for r in done)
+
+
+@pytest.mark.parametrize("nb", [64, 37])
+def test_diag_batch_independent_of_cluster_size(cuda_lib, nb):
+    """One diagonal block runs on a cluster of 8, 4, 2 or 1 CTAs depending on
+    how many blocks a launch holds; each block's factor is the same bits in
+    every configuration and equals Rpotrf's."""
+    from paper_2109_13406_gb300 import _abi
+
+    mp = cuda_lib
+    _, _, Fs = spd_problem(612, nb)
+    ref, info = gpu_potrf(mp, "L", *Fs)
+    assert info == 0
+    ref = host(ref)
+    for count in (1, 30, 60, 160):              # clusters of 8, 4, 2, 1
+        mats = [dev(Fs) for _ in range(count)]
+        infos = torch.zeros(count, dtype=torch.int64, device="cuda")
+        blob = b""
+        for i, M in enumerate(mats):
+            d = _abi.MpDDPotrfDiagDesc()
+            d.a_hi, d.a_lo = M[0].data_ptr(), M[1].data_ptr()
+            d.lda, d.n, d.offset, d.lower = nb, nb, 0, 1
+            d.info = infos.data_ptr() + 8 * i
+            blob += bytes(d)
+        descs = torch.frombuffer(bytearray(blob), dtype=torch.uint8).cuda()
+        mp.mp_dd_potrf_diag_batch(count, descs)
+        torch.cuda.synchronize()
+        assert not infos.any()
+        for M in (mats[0], mats[-1]):
+            h, l = host(M)
+            assert np.array_equal(np.tril(h), np.tril(ref[0])), count
+            assert np.array_equal(np.tril(l), np.tril(ref[1])), count
