@@ -976,6 +976,9 @@ def run_served_workload(args):
     wall = ranks.max(time.perf_counter() - t0)
     clocks = clk.stop()
     lat = np.array([(r.done_t - r.arrival) * 1e3 for r in done])
+    wait = np.array([(r.admit_t - r.arrival) * 1e3 for r in done])
+    serv = np.array([(r.done_t - r.admit_t) * 1e3 for r in done])
+    big = np.array([r.n >= 1024 for r in done])
     makespan = ranks.max(max(r.done_t for r in done))
     # each replica serves its own copy of the stream: latencies are those of
     # the slowest replica, throughput adds up
@@ -1009,6 +1012,12 @@ def run_served_workload(args):
                    "arrival_rate_per_s": rate, "offered_load": args.load,
                    "solo_rate_solves_per_s": solo_rate},
         "p50_ms": p50, "p99_ms": p99,
+        "admission_wait_ms": {"p50": ranks.max(float(np.percentile(wait, 50))),
+                              "p99": ranks.max(float(np.percentile(wait, 99)))},
+        "service_ms": {"p50": ranks.max(float(np.percentile(serv, 50))),
+                       "p99": ranks.max(float(np.percentile(serv, 99))),
+                       "p50_n_ge_1024": ranks.max(float(np.percentile(serv[big], 50)))
+                       if big.any() else None},
         "mean_ms": float(lat.mean()), "solves_per_s": ranks.whole_job(len(done), makespan),
         "dd_GFlops": ranks.whole_job(flops, makespan) / 1e9, "scheduler_steps": srv.steps,
         "launches": srv.launches, "max_concurrent": srv.max_active,
