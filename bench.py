@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "sliced", "crt", "grouped", "served"])
+                    choices=["plain", "sliced", "crt", "grouped", "served", "potrf"])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--groups", type=int, default=4096)
@@ -353,6 +353,67 @@ def _fp64_line(workload, ms, flops, macs):
                                         "instr/s (derived)"}}
 
 
+def potrf_section(mp, torch, n, info=None, reps=3):
+    """Rpotrf on the FP64 pipe and with the updates on the tensor cores
+    (mp_dd_Rpotrf_crt), uplo 'U', on a diagonally dominant SPD matrix
+    (symmetric U(-1,1) dd + 2n I), each timed with CUDA events (n^3 / 3
+    flops)."""
+    st = torch.cuda.current_stream()
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int64, device="cuda")
+    Sh, Sl = datagen.dd_matrix(datagen.rng(6), n, n)
+    Sh = np.asfortranarray(np.triu(Sh) + np.triu(Sh, 1).T + 2.0 * n * np.eye(n))
+    Sl = np.asfortranarray(np.triu(Sl) + np.triu(Sl, 1).T)
+    S0 = tuple(mp.to_device(x) for x in (Sh, Sl))
+    S = tuple(x.clone() for x in S0)
+
+    def reset_s():
+        for x, y in zip(S, S0):
+            x.copy_(y)
+    out = {}
+    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf("U", n, S, n, info), reset_s, reps)
+    out[f"Rpotrf_U_{n}"] = _fp64_line(f"dd Rpotrf uplo=U, n={n}, diagonally dominant SPD", ms,
+                                      float(n) ** 3 / 3, float(n) ** 3 / 6)
+    out[f"Rpotrf_U_{n}"]["info"] = int(info.item())
+    ws = mp.workspace(max(1, mp.mp_dd_Rpotrf_crt_workspace(n)))
+    ms_c = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf_crt("U", n, S, n, info, ws, ws.numel()),
+                     reset_s, reps)
+    out[f"Rpotrf_crt_U_{n}"] = {
+        "workload": f"dd Rpotrf uplo=U, n={n}, outer steps of 256 columns; panel and trailing "
+                    "updates of >= 512 columns as residue-form Rgemm / Rsyrk on the fp16 tensor "
+                    "cores", "ms": ms_c,
+        "dd_GFlops": float(n) ** 3 / 3 / (ms_c * 1e-3) / 1e9, "speedup_vs_fp64_pipe": ms / ms_c,
+        "info": int(info.item())}
+    return out
+
+
+def run_potrf_workload(args):
+    """--workload potrf: the two Rpotrf forms at --size (default 4096)."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
+    import paper_2109_13406_gb300 as mp
+
+    n = args.size
+    potrf_section(mp, torch, min(n, 512), reps=1)          # warm-up, untimed
+    ranks.barrier()
+    res = potrf_section(mp, torch, n, reps=max(1, args.steps))
+    crt, fp = res[f"Rpotrf_crt_U_{n}"], res[f"Rpotrf_U_{n}"]
+    ms = ranks.max(crt["ms"])
+    line = {"metric": "dd Rpotrf GFlops (tensor-core updates)",
+            "value": ranks.whole_job(float(n) ** 3 / 3 / 1e9, ms * 1e-3), "unit": "dd-GFlop/s",
+            "n_gpus": ranks.world, "steps": max(1, args.steps), "warmup": 1, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PCG64; symmetric U(-1,1) dd + 2n I)",
+            "config": {"workload": crt["workload"], "n": n}, "fp64_pipe": fp,
+            "speedup_vs_fp64_pipe": crt["speedup_vs_fp64_pipe"],
+            "all_info_zero": crt["info"] == 0 and fp["info"] == 0}
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
+
+
 def routines_section(mp, torch, size):
     """The other routines at m = n = k = size, each timed with CUDA events on
     the launching stream: dd Rtrsm (two variants), Rsyr2k, Rsymm, Rgetrf,
@@ -399,31 +460,7 @@ def routines_section(mp, torch, size):
                                     ms, 2.0 * n ** 3 / 3, float(n) ** 3 / 3)
     out[f"Rgetrf_{n}"]["info"] = int(info.item())
     del A, B, C, A0
-    # Rpotrf on the FP64 pipe and with the trailing updates on the tensor
-    # cores, on a diagonally dominant SPD matrix (symmetric U(-1,1) + 2n I)
-    Sh, Sl = datagen.dd_matrix(datagen.rng(6), n, n)
-    Sh = np.asfortranarray(np.triu(Sh) + np.triu(Sh, 1).T + 2.0 * n * np.eye(n))
-    Sl = np.asfortranarray(np.triu(Sl) + np.triu(Sl, 1).T)
-    S0 = dev((Sh, Sl))
-    S = tuple(x.clone() for x in S0)
-
-    def reset_s():
-        for x, y in zip(S, S0):
-            x.copy_(y)
-    ms = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf("U", n, S, n, info), reset_s)
-    out[f"Rpotrf_U_{n}"] = _fp64_line(f"dd Rpotrf uplo=U, n={n}, diagonally dominant SPD", ms,
-                                      float(n) ** 3 / 3, float(n) ** 3 / 6)
-    out[f"Rpotrf_U_{n}"]["info"] = int(info.item())
-    ws = mp.workspace(mp.mp_dd_Rpotrf_crt_workspace(n))
-    ms_c = _event_ms(torch, st, lambda: mp.mp_dd_Rpotrf_crt("U", n, S, n, info, ws, ws.numel()),
-                     reset_s)
-    out[f"Rpotrf_crt_U_{n}"] = {
-        "workload": f"dd Rpotrf uplo=U, n={n}, outer steps of 256 columns; panel and trailing "
-                    "updates of >= 512 columns as residue-form Rgemm / Rsyrk on the fp16 tensor "
-                    "cores", "ms": ms_c,
-        "dd_GFlops": float(n) ** 3 / 3 / (ms_c * 1e-3) / 1e9, "speedup_vs_fp64_pipe": ms / ms_c,
-        "info": int(info.item())}
-    del S0, S, ws
+    out.update(potrf_section(mp, torch, n, info))
     # quad-double Rgemm (117.5 FP64 instructions per qd multiply-add)
     nq = min(n, 1024)
     gq = datagen.rng(5)
@@ -1040,6 +1077,8 @@ def main():
         run_grouped_workload(args)
     elif args.workload == "served":
         run_served_workload(args)
+    elif args.workload == "potrf":
+        run_potrf_workload(args)
     else:
         run_ours(args)
 
