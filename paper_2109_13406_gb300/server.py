@@ -7,13 +7,17 @@ a fixed list of operations on its own device buffers:
     tensor cores (``mp_dd_Rsyrk_crt``, the residue form, upper triangle,
     within the same accuracy bound); for smaller n one FP64 Rsyrk-type
     update of the upper triangle;
-  * the blocked right-looking Cholesky F = U^T U: per block J the diagonal
-    factorisation, the panel solve U_JJ^T X = F(J, J+1:), and the trailing
-    update F(J+1:, J+1:) -= U(J, J+1:)^T U(J, J+1:) on the upper triangle: in
-    FP64, or, once the trailing block has ``crt_min_rest`` rows or more, as
-    one residue-form Rsyrk on the tensor cores, within the same accuracy
-    bound and far faster (a 2048 x 2048 x 64 update: well under 1 ms against
-    ~8 ms);
+  * the blocked Cholesky F = U^T U in groups of ``group`` blocks of 64
+    columns: per block J of a group the update of its row block by the
+    group's earlier blocks (F(J, J:) -= U(G0:J, J)^T U(G0:J, J:), left-looking,
+    depth up to 192), the diagonal factorisation and the panel solve
+    U_JJ^T X = F(J, J+1:); after the group, one update of the trailing
+    matrix by the whole group (depth 256, upper triangle).  Updates of
+    ``crt_min_rest`` columns or more run in residue form on the tensor cores
+    (``mp_dd_Rgemm_crt`` / ``mp_dd_Rsyrk_crt``), within the same accuracy
+    bound and far faster (a 2048 x 2048 x 256 update: 0.4 ms against ~13 ms
+    in FP64); the residue form's cost is mostly per output entry, so one
+    depth-256 trailing update costs about what one of depth 64 does;
   * the solve F X = B: blocked forward (U^T) and backward (U) substitution.
 
 A scheduler step takes the next step of every admitted request -- a short
@@ -39,8 +43,9 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rsyrk_crt, mp_dd_Rsyrk_crt_workspace,
-               mp_dd_trsm_batch, to_device, to_numpy, workspace)
+from . import (_abi, mp_dd_potrf_diag_batch, mp_dd_Rgemm_crt, mp_dd_Rgemm_crt_workspace,
+               mp_dd_Rsyrk_crt, mp_dd_Rsyrk_crt_workspace, mp_dd_trsm_batch, to_device,
+               to_numpy, workspace)
 from . import grouped as gr
 
 
@@ -94,9 +99,10 @@ class SpdServer:
 
     def __init__(self, budget_bytes: float = 120e9, slots: int = 256, nb: int = 64,
                  table: dict | None = None, sliced_min_n: int = 256, crt_min_rest: int = 512,
-                 depth: int = 2):
+                 depth: int = 2, group: int = 4):
         self.sliced_min_n = int(sliced_min_n)
         self.crt_min_rest = int(crt_min_rest)
+        self.group = max(1, int(group))
         self.budget = float(budget_bytes)
         self.slots = int(slots)
         self.nb = int(nb)
@@ -119,9 +125,12 @@ class SpdServer:
 
     def _size(self, r: Request) -> None:
         if r.n >= self.sliced_min_n and r.sliced_ws == 0:
-            # one workspace for F = G G^T (k = 2n) and the trailing updates (k = nb)
+            # one workspace for F = G G^T (k = 2n), the group updates (k =
+            # group nb) and the row-block updates (nb rows, k < group nb)
+            kg = self.group * self.nb
             r.sliced_ws = max(mp_dd_Rsyrk_crt_workspace(r.n, 2 * r.n),
-                              mp_dd_Rsyrk_crt_workspace(r.n, self.nb))
+                              mp_dd_Rsyrk_crt_workspace(r.n, kg),
+                              mp_dd_Rgemm_crt_workspace(self.nb, r.n, max(1, kg - self.nb)))
 
     def admit(self, r: Request, now: float) -> None:
         self._size(r)
@@ -161,7 +170,9 @@ class SpdServer:
             steps.append([("sliced", (G, F))])
         else:
             steps.append([("gemm", ("N", "T", n, n, 2 * n, one, G, G, zero, F, 1))])
-        # blocked Cholesky, upper: block J's step = [update left by J-1,
+        # blocked Cholesky, upper, in groups of `group` blocks: block J's
+        # step = [the group update left by the previous group (first block
+        # of a group) or the row-block update by the group's earlier blocks,
         # diagonal factor J, panel solve J]; the first joins the F step.
         # The forward substitution U^T Y = B runs one block behind in the same
         # steps: block J's solve needs only U_JJ and the updates from blocks
@@ -178,21 +189,34 @@ class SpdServer:
             fwd_upd.append(("gemm", ("T", "N", rest, nrhs, b, mone, _pair(F, j, j + b, b, rest),
                                      _pair(X, j, 0, b, nrhs), one,
                                      _pair(X, j + b, 0, rest, nrhs), 0)) if rest > 0 else None)
+        crt_ok = bool(r.sliced_ws)
         pending = None
         for t, j in enumerate(blocks):
             b = min(nb, n - j)
+            g0 = (t // self.group) * self.group * nb          # the group's first column
             ops = [pending] if pending else []
+            pending = None
+            if j > g0:
+                # F(J, J:) -= U(g0:J, J)^T U(g0:J, J:), depth j - g0
+                cols, k = n - j, j - g0
+                Ut, Pr, Cr = _pair(F, g0, j, k, b), _pair(F, g0, j, k, cols), _pair(F, j, j, b, cols)
+                if crt_ok and cols >= self.crt_min_rest:
+                    ops.append(("crt_gemm", (Ut, Pr, Cr, b, cols, k)))
+                else:
+                    ops.append(("gemm", ("T", "N", b, cols, k, mone, Ut, Pr, one, Cr, 0)))
             ops.append(("diag", (_pair(F, j, j, b, b), b, j)))
             rest = n - j - b
-            pending = None
             if rest > 0:
-                P = _pair(F, j, j + b, b, rest)
-                ops.append(("trsm", (_pair(F, j, j, b, b), P, b, rest, 1)))
-                Ct = _pair(F, j + b, j + b, rest, rest)
-                if r.sliced_ws and rest >= self.crt_min_rest:
-                    pending = ("crt", (P, Ct, rest, b))
-                else:
-                    pending = ("gemm", ("T", "N", rest, rest, b, mone, P, P, one, Ct, 1))
+                ops.append(("trsm", (_pair(F, j, j, b, b), _pair(F, j, j + b, b, rest), b,
+                                     rest, 1)))
+                if t % self.group == self.group - 1:
+                    # the group is done: F(e:, e:) -= U(g0:e, e:)^T U(g0:e, e:)
+                    e, kg = j + b, j + b - g0
+                    P, Ct = _pair(F, g0, e, kg, rest), _pair(F, e, e, rest, rest)
+                    if crt_ok and rest >= self.crt_min_rest:
+                        pending = ("crt", (P, Ct, rest, kg))
+                    else:
+                        pending = ("gemm", ("T", "N", rest, rest, kg, mone, P, P, one, Ct, 1))
             if t >= 2 and fwd_upd[t - 2]:
                 ops.append(fwd_upd[t - 2])
             if t >= 1:
@@ -279,11 +303,18 @@ class SpdServer:
                     mp_dd_Rsyrk_crt("U", "N", n, 2 * n, (1.0, 0.0), G, n, (0.0, 0.0), F, n, ws,
                                     ws.numel())
                     self.launches += 1
-                else:   # "crt"
+                elif kind == "crt":
                     P, Ct, rest, b = args
                     ws = r.dev["ws"]
                     mp_dd_Rsyrk_crt("U", "T", rest, b, (-1.0, 0.0), P, P[0].stride(1),
                                     (1.0, 0.0), Ct, Ct[0].stride(1), ws, ws.numel())
+                    self.launches += 1
+                else:   # "crt_gemm": a row block's update by its group's earlier blocks
+                    Ut, Pr, Cr, b, cols, k = args
+                    ws = r.dev["ws"]
+                    ld = Cr[0].stride(1)
+                    mp_dd_Rgemm_crt("T", "N", b, cols, k, (-1.0, 0.0), Ut, ld, Pr, ld, (1.0, 0.0),
+                                    Cr, ld, ws, ws.numel())
                     self.launches += 1
         if gemm:
             arr = (_abi.MpDDGemmDesc * len(gemm)).from_buffer_copy(b"".join(gemm))

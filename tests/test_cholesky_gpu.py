@@ -150,6 +150,29 @@ def test_server_tensor_core_trailing_updates(cuda_lib):
     assert residual_ratio(Fs, by_id[0].X, B, cuda_lib) < 30
 
 
+@pytest.mark.parametrize("crt_min_rest", [64, 10 ** 9])
+def test_server_group_sizes_agree(cuda_lib, crt_min_rest):
+    """Groups of 4 blocks (row-block updates of depth up to 192, trailing
+    updates of depth 256) and groups of 1 (rank-64 right-looking updates),
+    with the updates in residue form or in FP64: the same solution within
+    what cond(F) ~1e20 allows, and the LAPACK ratio < 30."""
+    from paper_2109_13406_gb300.server import SpdServer, residual_ratio
+
+    n = 520
+    reqs = lambda: make_requests(660, [n])
+    g4 = SpdServer(crt_min_rest=crt_min_rest, group=4).serve(reqs())[0]
+    g1 = SpdServer(crt_min_rest=crt_min_rest, group=1).serve(reqs())[0]
+    assert g4.info == 0 and g1.info == 0
+    rel = np.abs((g1.X[0] - g4.X[0]) + (g1.X[1] - g4.X[1])).max()
+    assert rel <= 1e20 * EPS_DD * 100 * np.abs(g1.X[0]).max()
+    G, B = datagen.spd_request(660, n)
+    F = cuda_lib.dd_empty(n, n, fill=0.0)
+    cuda_lib.mp_dd_Rsyrk("U", "N", n, 2 * n, (1.0, 0.0), dev(G), n, (0.0, 0.0), F, n)
+    fh, fl = host(F)
+    Fs = (np.triu(fh) + np.triu(fh, 1).T, np.triu(fl) + np.triu(fl, 1).T)
+    assert residual_ratio(Fs, g4.X, B, cuda_lib) < 30
+
+
 @pytest.mark.parametrize("n", [130, 300])
 def test_server_matches_single_matrix_routines(cuda_lib, n):
     from paper_2109_13406_gb300.server import SpdServer
