@@ -156,6 +156,18 @@ __device__ __forceinline__ dd div_rcp(dd a, dd b, double y) {
     return q;
 }
 
+// dd reciprocal 1 / b: div(1, b) with the first digit RN(1 / b.hi) from
+// the correctly rounded reciprocal (the same number as the division gives)
+// and the second taken by it as well: one reciprocal, five FP64 operations.
+__device__ __forceinline__ dd rcp_dd(dd b) {
+    const double y = __drcp_rn(b.hi);
+    double r = __fma_rn(-y, b.hi, 1.0);
+    r = __fma_rn(-y, b.lo, r);
+    dd q;
+    fast_two_sum(y, __dmul_rn(r, y), q.hi, q.lo);
+    return q;
+}
+
 // dd square root: x = RN(sqrt(a.hi)), whose remainder a.hi - x^2 is a
 // binary64 number (one FMA gives it exactly), plus one Newton correction
 // (a - x^2) / (2x) with a.lo added, the division taken as a product with

@@ -939,6 +939,58 @@ __global__ void laswp_kernel(double *ah, double *al, int64_t lda, int64_t c0, in
     }
 }
 
+// The interchanges ipiv[k0 .. k1) (k1 - k0 <= 32, one-based, applied in
+// order) on the columns [0, c_skip) and [c_skip + n_skip, n_all) of A.  The
+// rows they touch (at most 64) and where each one's final content comes
+// from are worked out once per CTA; then each thread moves one (row,
+// column) entry: all loads, a barrier, all stores, instead of a chain of
+// dependent swaps per column.
+__global__ void __launch_bounds__(256) laswp_perm_kernel(double *ah, double *al, int64_t lda,
+                                                         int64_t c_skip, int64_t n_skip,
+                                                         int64_t n_all, const int64_t *ipiv,
+                                                         int64_t k0, int64_t k1) {
+    __shared__ int64_t S[64], src[64];
+    __shared__ int ns;
+    if (threadIdx.x == 0) {
+        const int nk = (int)(k1 - k0);
+        int cnt = nk;
+        for (int t = 0; t < nk; ++t) S[t] = src[t] = k0 + t;
+        for (int t = 0; t < nk; ++t) {
+            const int64_t p = ipiv[k0 + t] - 1;
+            int ip = -1;
+            if (p >= k0 && p < k1) {
+                ip = (int)(p - k0);
+            } else {
+                for (int q = nk; q < cnt; ++q)
+                    if (S[q] == p) ip = q;
+                if (ip < 0) {
+                    ip = cnt++;
+                    S[ip] = src[ip] = p;
+                }
+            }
+            const int64_t tmp = src[t];
+            src[t] = src[ip];
+            src[ip] = tmp;
+        }
+        ns = cnt;
+    }
+    __syncthreads();
+    const int i = (int)(threadIdx.x % 64);
+    const int64_t q = (int64_t)blockIdx.x * 4 + threadIdx.x / 64;
+    const int64_t c = q < c_skip ? q : q + n_skip;
+    const bool act = i < ns && c < n_all && src[i] != S[i];
+    double vh = 0.0, vl = 0.0;
+    if (act) {
+        vh = ah[src[i] + c * lda];
+        vl = al[src[i] + c * lda];
+    }
+    __syncthreads();
+    if (act) {
+        ah[S[i] + c * lda] = vh;
+        al[S[i] + c * lda] = vl;
+    }
+}
+
 // C(m x n) -= A(m x k) B(k x n), all column-major, for small k or n: one
 // thread per entry of C, multiply-adds l = 0 .. k-1 straight into C's value.
 // (The 64 x 64 tiles of the Rgemm kernel would compute zero-padded products
@@ -959,11 +1011,237 @@ __global__ void __launch_bounds__(256) small_update_kernel(
 
 constexpr int64_t kSmallUpdate = 16;   // k or n at or below this: small_update_kernel
 
+// ---- panel of up to 32 columns in one cooperative launch
+//
+// getrf_panel_kernel factors the columns [j0, j0 + w) over the rows
+// [j0, m) (dgetf2 on the panel: pivot, interchange within the panel,
+// multipliers by the reciprocal of the pivot, rank-1 update) with every CTA
+// of the grid co-resident.  CTA c owns the rows [j0 + c R, j0 + (c + 1) R).
+// Per column j one grid barrier: before it, every CTA publishes its best
+// candidate (key, the whole panel row, the candidate's dd reciprocal) and
+// the owner of row j publishes row j; after it, every CTA picks the same
+// pivot from the published keys and updates its own rows, the owner of row
+// j taking the pivot row and the owner of row p taking row j's.  The
+// published buffers alternate by the parity of j: a CTA overwrites a
+// buffer only after the next barrier, which every reader of its previous
+// contents has passed.  Interchanges outside the panel follow as one
+// laswp.  Each barrier wait is bounded (~2 s): a CTA that gives up raises
+// an abort flag that ends every CTA's loop, and info is set to -1.
+constexpr int kPanelW = 32;
+constexpr int kPanelMaxG = 256;
+constexpr int kPanelThreads = 256;
+
+struct PanelCand {
+    uint64_t mag;
+    double lo;
+    int64_t row;                 // -1: no candidate in this CTA
+    double rh, rl;               // dd reciprocal of the candidate
+    double vh[kPanelW], vl[kPanelW];
+};
+
+struct PanelWs {
+    unsigned int count;          // grid-barrier arrivals (zeroed before the launch)
+    unsigned int abort;          // a wait gave up
+    double rjh[2][kPanelW], rjl[2][kPanelW];
+    PanelCand cand[2][kPanelMaxG];
+};
+
+// Thread 0 of each CTA: arrive, then wait for all G arrivals of barrier b
+// (b = 1, 2, ...).  false: the wait gave up or another CTA did.
+__device__ bool panel_grid_sync(PanelWs *ws, int G, unsigned int b) {
+    __threadfence();
+    atomicAdd(&ws->count, 1u);
+    const unsigned int target = b * (unsigned int)G;
+    const long long t0 = clock64();
+    volatile unsigned int *cnt = &ws->count, *ab = &ws->abort;
+    while (*cnt < target) {
+        if (*ab) return false;
+        if (clock64() - t0 > 4000000000LL) {
+            atomicExch(&ws->abort, 1u);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// The best pivot key over a warp's lanes, with the slot it came from:
+// every lane ends with the same winner (keys of distinct rows are totally
+// ordered by better()).
+__device__ __forceinline__ void warp_best(PivotKey &k, int &slot) {
+    for (int off = 16; off > 0; off /= 2) {
+        const PivotKey o{__shfl_xor_sync(0xffffffffu, k.mag, off),
+                         __shfl_xor_sync(0xffffffffu, k.lo, off),
+                         __shfl_xor_sync(0xffffffffu, k.row, off)};
+        const int os = __shfl_xor_sync(0xffffffffu, slot, off);
+        if (better(o, k) || (!better(k, o) && o.row == k.row && os < slot)) {
+            k = o;
+            slot = os;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPanelThreads) getrf_panel_kernel(
+    double *ah, double *al, int64_t lda, int64_t m, int64_t j0, int w, int64_t R,
+    int64_t *ipiv, int64_t *info, PanelWs *ws) {
+    __shared__ double lh[1024], ll[1024];      // the multipliers of this CTA's rows (R <= 1024)
+    __shared__ int s_stop;
+    __shared__ int64_t s_p;
+    __shared__ double s_rh, s_rl;
+    __shared__ double pvh[kPanelW], pvl[kPanelW];   // the pivot row
+    __shared__ double jvh[kPanelW], jvl[kPanelW];   // row j before the interchange
+    const int G = (int)gridDim.x, c = (int)blockIdx.x, tid = (int)threadIdx.x;
+    const int lane = tid % 32, warp = tid / 32;
+    const int64_t rs = j0 + (int64_t)c * R;
+    const int64_t re = rs + R < m ? rs + R : m;
+    const int mn = (int)((m - j0) < w ? (m - j0) : w);   // columns that take a pivot
+    double *Ah = ah + j0 * lda, *Al = al + j0 * lda;   // column jj of the panel: + jj * lda
+    for (int jj = 0; jj < mn; ++jj) {
+        const int64_t j = j0 + jj;
+        const int par = jj & 1;
+        // 1. warp 0: this CTA's best candidate in column j (rows max(j, rs) ..
+        //    re) and its publication (key, panel row, dd reciprocal); warp 1:
+        //    row j, by its owner.  The published buffers are written and
+        //    read at L2, past L1: other CTAs write them between our reads.
+        if (warp == 0) {
+            PivotKey best{0, 0.0, -1};
+            int dummy = 0;
+            for (int64_t i = (j > rs ? j : rs) + lane; i < re; i += 32) {
+                const PivotKey k = pivot_key(Ah[i + jj * lda], Al[i + jj * lda], i);
+                if (better(k, best)) best = k;
+            }
+            warp_best(best, dummy);
+            PanelCand &pc = ws->cand[par][c];
+            if (best.row >= 0 && lane < w) {
+                __stcg(&pc.vh[lane], Ah[best.row + lane * lda]);
+                __stcg(&pc.vl[lane], Al[best.row + lane * lda]);
+            }
+            if (lane == 0) {
+                double rh = 0.0, rl = 0.0;
+                if (best.row >= 0) {
+                    const double ph = Ah[best.row + jj * lda], pl = Al[best.row + jj * lda];
+                    if (fabs(ph) >= 0x1p-1021) {
+                        const dd r = rcp_dd(dd{ph, pl});
+                        rh = r.hi;
+                        rl = r.lo;
+                    }
+                }
+                __stcg(&pc.rh, rh);
+                __stcg(&pc.rl, rl);
+                __stcg(reinterpret_cast<unsigned long long *>(&pc.mag),
+                       (unsigned long long)best.mag);
+                __stcg(&pc.lo, best.lo);
+                __stcg(reinterpret_cast<long long *>(&pc.row), (long long)best.row);
+            }
+            __threadfence();
+        } else if (warp == 1) {
+            if (j >= rs && j < re && lane < w) {
+                __stcg(&ws->rjh[par][lane], Ah[j + lane * lda]);
+                __stcg(&ws->rjl[par][lane], Al[j + lane * lda]);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (tid == 0) s_stop = panel_grid_sync(ws, G, (unsigned int)(jj + 1)) ? 0 : 1;
+        __syncthreads();
+        if (s_stop) {
+            if (c == 0 && tid == 0) *info = -1;
+            return;
+        }
+        // 2. warp 0: the pivot, the best published key (the same in every
+        //    CTA), and the pivot row into shared memory; warp 1: row j
+        if (warp == 0) {
+            PivotKey pk{0, 0.0, -1};
+            int win = 0;
+            for (int q = lane; q < G; q += 32) {
+                const PanelCand &o = ws->cand[par][q];
+                const PivotKey k{
+                    (uint64_t)__ldcg(reinterpret_cast<const unsigned long long *>(&o.mag)),
+                    __ldcg(&o.lo), (int64_t)__ldcg(reinterpret_cast<const long long *>(&o.row))};
+                if (better(k, pk)) {
+                    pk = k;
+                    win = q;
+                }
+            }
+            warp_best(pk, win);
+            const PanelCand &wc = ws->cand[par][win];
+            if (lane < w) {
+                pvh[lane] = __ldcg(&wc.vh[lane]);
+                pvl[lane] = __ldcg(&wc.vl[lane]);
+            }
+            if (lane == 0) {
+                s_p = pk.row;
+                s_rh = __ldcg(&wc.rh);
+                s_rl = __ldcg(&wc.rl);
+            }
+        } else if (warp == 1 && lane < w) {
+            jvh[lane] = __ldcg(&ws->rjh[par][lane]);
+            jvl[lane] = __ldcg(&ws->rjl[par][lane]);
+        }
+        __syncthreads();
+        const int64_t p = s_p;               // >= j: every column has rows j .. m-1
+        const double ph = pvh[jj], pl = pvl[jj];
+        if (c == 0 && tid == 0) {
+            ipiv[j] = p + 1;
+            if (ph == 0.0 && pl == 0.0)
+                atomicCAS(reinterpret_cast<unsigned long long *>(info), 0ull,
+                          (unsigned long long)(j + 1));
+        }
+        if (ph == 0.0 && pl == 0.0) continue;   // zero pivot: no interchange, no update
+        const bool recip = fabs(ph) >= 0x1p-1021;
+        const dd rcp{s_rh, s_rl};
+        // 3a. the interchange within the panel and the multipliers of the rows
+        // r > j this CTA owns; row p takes row j's entries
+        const int64_t r0 = (j + 1 > rs ? j + 1 : rs);
+        for (int64_t r = r0 + tid; r < re; r += kPanelThreads) {
+            const bool isp = r == p && p != j;
+            const dd a = isp ? dd{jvh[jj], jvl[jj]} : dd{Ah[r + jj * lda], Al[r + jj * lda]};
+            const dd l = recip ? mul(a, rcp) : div(a, dd{ph, pl});
+            lh[r - rs] = l.hi;
+            ll[r - rs] = l.lo;
+        }
+        if (j >= rs && j < re && p != j && tid < w) {   // row j := the pivot row
+            Ah[j + tid * lda] = pvh[tid];
+            Al[j + tid * lda] = pvl[tid];
+        }
+        if (p != j && p >= rs && p < re && tid < jj) {  // row p's earlier columns := row j's
+            Ah[p + tid * lda] = jvh[tid];
+            Al[p + tid * lda] = jvl[tid];
+        }
+        __syncthreads();
+        // 3b. A(r, j) = l_r; A(r, jj+1 ..) -= l_r * pivot row
+        const int ncol = w - jj;                      // column jj and the ones after it
+        const int64_t nr = re - r0;
+        for (int64_t e = tid; e < nr * ncol; e += kPanelThreads) {
+            const int64_t r = r0 + e / ncol;
+            const int cc = jj + (int)(e % ncol);
+            const dd l{lh[r - rs], ll[r - rs]};
+            const int64_t o = r + cc * lda;
+            if (cc == jj) {
+                Ah[o] = l.hi;
+                Al[o] = l.lo;
+            } else {
+                const bool isp = r == p && p != j;
+                dd a = isp ? dd{jvh[cc], jvl[cc]} : dd{Ah[o], Al[o]};
+                mac(a, dd{-l.hi, -l.lo}, dd{pvh[cc], pvl[cc]});
+                Ah[o] = a.hi;
+                Al[o] = a.lo;
+            }
+        }
+        __syncthreads();
+    }
+    // columns past the last pivot (a panel wider than its rows): nothing left
+}
+
+
 struct LuPlan {
     double *ah, *al;
     int64_t lda, m, n;     // the whole matrix
     int64_t *ipiv, *info;
     cudaStream_t st;
+    PanelWs *panel_ws = nullptr;   // the panel kernel's buffers (null: column leaves)
+    int64_t panel_ctas = 0;        // co-resident CTAs of the panel kernel
 };
 
 int laswp(const LuPlan &P, double *bh, double *bl, int64_t ldb, int64_t c0, int64_t c1,
@@ -981,6 +1259,35 @@ int getrf_rec(const LuPlan &P, int64_t j0, int64_t n) {
     const int64_t rows = P.m - j0;
     if (n <= 0 || rows <= 0) return 0;
     int rc;
+    // the panel kernel: rows spread over at most panel_ctas CTAs, at least 16
+    // and at most 1024 rows each (its multipliers sit in shared memory)
+    int64_t G = ceil_div(rows, (int64_t)16);
+    if (G > P.panel_ctas) G = P.panel_ctas;
+    if (G < 1) G = 1;
+    int64_t R = ceil_div(rows, G);
+    G = ceil_div(rows, R);
+    if (P.panel_ws != nullptr && n <= kPanelW && R <= 1024) {
+        const int w = (int)n;
+        cudaError_t e = cudaMemsetAsync(P.panel_ws, 0, 2 * sizeof(unsigned int), P.st);
+        if (e != cudaSuccess) return cuda_fail(e, "panel barrier reset");
+        double *ah = P.ah, *al = P.al;
+        int64_t lda = P.lda, m = P.m, jj0 = j0;
+        int ww = w;
+        int64_t *ipiv = P.ipiv, *info = P.info;
+        PanelWs *ws = P.panel_ws;
+        void *args[] = {&ah, &al, &lda, &m, &jj0, &ww, &R, &ipiv, &info, &ws};
+        e = cudaLaunchCooperativeKernel((const void *)getrf_panel_kernel, dim3((unsigned)G),
+                                        dim3(kPanelThreads), args, 0, P.st);
+        if (e != cudaSuccess) return cuda_fail(e, "getrf_panel_kernel launch");
+        if ((rc = check_launch("getrf_panel_kernel"))) return rc;
+        // the panel's interchanges on the columns left and right of it
+        const int64_t k1 = j0 + (rows < n ? rows : n);
+        const int64_t other = P.n - n;
+        if (other <= 0) return 0;
+        laswp_perm_kernel<<<(unsigned)ceil_div(other, (int64_t)4), 256, 0, P.st>>>(
+            P.ah, P.al, P.lda, j0, n, P.n, P.ipiv, j0, k1);
+        return check_launch("laswp_perm_kernel");
+    }
     if (n == 1) {
         getrf_pivot_kernel<<<1, LT, 0, P.st>>>(P.ah, P.al, P.lda, P.m, j0, P.ipiv, P.info);
         if ((rc = check_launch("getrf_pivot_kernel"))) return rc;
@@ -1034,7 +1341,24 @@ int run_getrf(int64_t m, int64_t n, double *ah, double *al, int64_t lda, int64_t
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(int64_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "info reset");
     LuPlan P{ah, al, lda, m, n, ipiv, info, st};
-    return getrf_rec(P, 0, n);
+    // the panel kernel needs every CTA resident at once
+    int dev = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, getrf_panel_kernel, kPanelThreads, 0);
+    const int64_t ctas = (int64_t)per_sm * (sm_count() > 0 ? sm_count() : 0);
+    if (coop && ctas > 0) {
+        e = cudaMallocAsync(reinterpret_cast<void **>(&P.panel_ws), sizeof(PanelWs), st);
+        if (e != cudaSuccess) return cuda_fail(e, "panel workspace");
+        P.panel_ctas = ctas < kPanelMaxG ? ctas : kPanelMaxG;
+        if (P.panel_ctas > (sm_count() > 0 ? sm_count() : 1)) P.panel_ctas = sm_count();
+    }
+    rc = getrf_rec(P, 0, n);
+    if (P.panel_ws != nullptr) {
+        e = cudaFreeAsync(P.panel_ws, st);
+        if (rc == 0 && e != cudaSuccess) return cuda_fail(e, "panel workspace");
+    }
+    return rc;
 }
 
 int run_getrs(int trans, int64_t n, int64_t nrhs, const double *ah, const double *al,

@@ -133,3 +133,30 @@ def test_errors_and_empty(cuda_lib):
     assert mp.mp_dd_Rgetrs("N", 8, 1, A, 7, ipiv, A, 8, check=False) == -5
     assert mp.mp_dd_Rgetrs("N", 8, 1, A, 8, None, A, 8, check=False) == -6
     assert mp.mp_dd_Rgetrs("N", 8, 1, A, 8, ipiv, A, 7, check=False) == -8
+
+
+@pytest.mark.parametrize("m,n", [(3000, 40), (2500, 33)])
+def test_tall_panels_over_many_ctas(cuda_lib, m, n):
+    """Panels of up to 32 columns run as one cooperative launch with their
+    rows spread over up to one CTA per SM (here ~150 CTAs of ~20 rows): the
+    oracle's pivots, the LAPACK ratio and the backward bound on sampled
+    entries."""
+    g = datagen.rng(730 + n)
+    A = datagen.dd_matrix(g, m, n)
+    (lh, ll), piv, info = gpu_getrf(cuda_lib, A, m, n)
+    _, _, opiv, oinfo = oracle.dd_getrf(A, m, n)
+    assert info == 0 == oinfo and np.array_equal(piv, opiv)
+    assert lu_residual_ratio(A, (lh, ll), piv, m, n) < 30
+    rows = g.integers(0, m, 2000)
+    cols = g.integers(0, n, 2000)
+    rows[:40], cols[40:80] = m - 1, n - 1
+    assert lu_backward_over_bound(A, (lh, ll), piv, m, n, rows, cols) <= 1.0
+
+
+def test_deterministic(cuda_lib):
+    g = datagen.rng(740)
+    A = datagen.dd_matrix(g, 300, 300)
+    a = gpu_getrf(cuda_lib, A, 300, 300)
+    b = gpu_getrf(cuda_lib, A, 300, 300)
+    assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[0][1], b[0][1])
+    assert np.array_equal(a[1], b[1])
