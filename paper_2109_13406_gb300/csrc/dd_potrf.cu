@@ -807,14 +807,18 @@ int run_trsm(int right, int lower, int trans, int unit, int64_t m, int64_t n, mp
 // of the columns (recursively), solve L11 U12 = A12 (the Rtrsm above, unit
 // lower), update A22 -= L21 U12 (the plain dd Rgemm kernel, or a
 // one-thread-per-entry kernel when k or n is small), factor A22
-// (recursively).  A single column is a leaf: one CTA finds the pivot (the
-// first row of largest |A(i, j)|, compared as dd values) and records it,
-// then a second launch interchanges the two rows across the whole matrix
-// and forms the multipliers, spread over CTAs.  dgetrf2 applies each half's interchanges to the other half
-// as a block afterwards; swapping whole rows at the leaf gives the same
-// matrix, because nothing reads or writes the other half in between, and
-// needs no sequential interchange passes.  The top-level updates are large
-// products; the leaves and the thin updates near them are latency-bound.
+// (recursively).  The leaves are panels of at most 32 columns, each one
+// cooperative launch (getrf_panel_kernel below) followed by one launch that
+// applies its interchanges to the other columns; where that kernel cannot
+// run (no cooperative launch, or more than 1024 rows per CTA) a single
+// column is the leaf: one CTA finds the pivot (the first row of largest
+// |A(i, j)|, compared as dd values) and records it, then a second launch
+// interchanges the two rows across the whole matrix and forms the
+// multipliers.  dgetrf2 applies each half's interchanges to the other half
+// as a block afterwards; applying them to all other columns at the leaf
+// gives the same matrix, because nothing reads or writes the other half in
+// between.  The top-level updates are large products; the leaves and the
+// thin updates near them are latency-bound.
 
 namespace {
 
