@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain",
-                    choices=["plain", "sliced", "crt", "grouped", "served", "potrf"])
+                    choices=["plain", "sliced", "crt", "grouped", "served", "potrf", "sweep"])
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--groups", type=int, default=4096)
@@ -385,6 +385,71 @@ def potrf_section(mp, torch, n, info=None, reps=3):
         "dd_GFlops": float(n) ** 3 / 3 / (ms_c * 1e-3) / 1e9, "speedup_vs_fp64_pipe": ms / ms_c,
         "info": int(info.item())}
     return out
+
+
+def run_sweep_workload(args):
+    """--workload sweep: the plain dd path over the square sizes of the plain
+    configuration (Rgemm NN / TN at m = n = k in {1024, 2048, 4096, 8192},
+    Rsyrk U/N at n = k in {1024, 4096, 8192}; alpha, beta random dd in
+    [0.5, 2]) beside the residue-form (CRT) Rgemm / Rsyrk on the same
+    inputs, each call timed with CUDA events (one untimed call first)."""
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks()
+    import paper_2109_13406_gb300 as mp
+
+    st = torch.cuda.current_stream()
+    dev = lambda pair: tuple(mp.to_device(x) for x in pair)
+    rows = []
+    gemm_sizes = (1024, 2048, 4096, 8192)
+    syrk_sizes = (1024, 4096, 8192)
+    for n in sorted(set(gemm_sizes) | set(syrk_sizes)):
+        g = datagen.rng(11 + n)
+        A, B, C = (dev(datagen.dd_matrix(g, n, n)) for _ in range(3))
+        al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
+        ws = mp.workspace(max(mp.mp_dd_Rgemm_crt_workspace(n, n, n),
+                              mp.mp_dd_Rsyrk_crt_workspace(n, n)))
+        reps = 1 if n >= 8192 else 2
+        calls = []
+        if n in gemm_sizes:
+            for ta in ("N", "T"):
+                calls.append((f"Rgemm_{ta}N", 2.0 * n ** 3, float(n) ** 3,
+                              lambda ta=ta: mp.mp_dd_Rgemm(ta, "N", n, n, n, al, A, n, B, n, be,
+                                                           C, n),
+                              lambda ta=ta: mp.mp_dd_Rgemm_crt(ta, "N", n, n, n, al, A, n, B, n,
+                                                               be, C, n, ws, ws.numel())))
+        if n in syrk_sizes:
+            calls.append(("Rsyrk_UN", float(n) * n * (n + 1), float(n) * n * (n + 1) / 2,
+                          lambda: mp.mp_dd_Rsyrk("U", "N", n, n, al, A, n, be, C, n),
+                          lambda: mp.mp_dd_Rsyrk_crt("U", "N", n, n, al, A, n, be, C, n, ws,
+                                                     ws.numel())))
+        for name, flops, macs, plain, crt in calls:
+            ms = ranks.max(_event_ms(torch, st, plain, reps=reps))
+            ms_c = ranks.max(_event_ms(torch, st, crt, reps=3))
+            line = _fp64_line(f"dd {name} n={n}", ms, flops, macs)
+            rows.append({"call": name, "n": n, "plain_ms": ms,
+                         "plain_dd_GFlops": line["dd_GFlops"],
+                         "plain_fp64_frac": line["roofline"]["frac"], "crt_ms": ms_c,
+                         "crt_dd_GFlops": flops / (ms_c * 1e-3) / 1e9,
+                         "crt_over_plain": ms / ms_c,
+                         "workspace_status": mp.mp_dd_workspace_status(ws)})
+        del A, B, C, ws
+        torch.cuda.empty_cache()
+    big = [r for r in rows if r["call"] == "Rgemm_NN" and r["n"] == max(gemm_sizes)][0]
+    line = {"metric": "dd Rgemm/Rsyrk size sweep: plain FP64-pipe and residue-form dd-GFlop/s",
+            "value": ranks.whole_job(big["plain_dd_GFlops"], 1.0), "unit": "dd-GFlop/s",
+            "n_gpus": ranks.world, "steps": 1, "warmup": 1, "ms_per_step": big["plain_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded PCG64; dd entries hi~U(-1,1), lo=hi*2^-53*U(-1,1) "
+                    "renormalised; alpha,beta random dd in [0.5,2])",
+            "config": {"workload": "plain dd Rgemm NN/TN m=n=k in {1024,2048,4096,8192}, Rsyrk "
+                                   "U/N n=k in {1024,4096,8192}; CRT form on the same inputs",
+                       "value_is": "Rgemm NN 8192, plain"},
+            "sweep": rows}
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
 
 
 def run_potrf_workload(args):
@@ -1079,6 +1144,8 @@ def main():
         run_served_workload(args)
     elif args.workload == "potrf":
         run_potrf_workload(args)
+    elif args.workload == "sweep":
+        run_sweep_workload(args)
     else:
         run_ours(args)
 
