@@ -136,8 +136,15 @@ __device__ __forceinline__ void dd_tile(const mp_dd_gemm_desc &d, int64_t bi, in
             stage();
             __syncthreads();
             if (l0 + BK < kk) load(l0 + BK);
+            // the groups of 4 steps wholly past k only add zero products and
+            // renormalise an already normalised sum: skipping them changes
+            // no bit
+            const int64_t left = kk - l0;
+            const int lend = left >= BK ? BK
+                                        : (int)((left + kRenormEvery - 1) / kRenormEvery) *
+                                              kRenormEvery;
 #pragma unroll 1
-            for (int l4 = 0; l4 < BK; l4 += kRenormEvery) {
+            for (int l4 = 0; l4 < lend; l4 += kRenormEvery) {
 #pragma unroll
                 for (int l = l4; l < l4 + kRenormEvery; ++l) {
                     dd a[RM], b[RN];

@@ -194,10 +194,11 @@ class GroupedGemm:
         self.graph.replay()
 
     def padded_macs(self) -> float:
-        """Multiply-adds including the zero padding of partial tiles."""
+        """Multiply-adds the kernel issues: partial tiles are zero-padded, and
+        k runs in groups of 4 steps."""
         tot = 0.0
         for d in self.descs:
             s = d.tile
             bm, bn = SHAPES.get(s, (64, 64))
-            tot += math.ceil(d.m / bm) * bm * math.ceil(d.n / bn) * bn * d.k
+            tot += math.ceil(d.m / bm) * bm * math.ceil(d.n / bn) * bn * (4 * math.ceil(d.k / 4))
         return tot
