@@ -529,6 +529,27 @@ int mp_dd_sliced_timing(int enable);
 int mp_dd_sliced_phase_ms(float ms[3]);
 
 /* ------------------------------------------------------------------------ */
+/* Elementwise dd arithmetic (the dd format's scalar operations, Sec. 5)      */
+/* ------------------------------------------------------------------------ */
+
+/* z_i := x_i op y_i for i < n on device arrays (hi, lo planes, contiguous),
+ * with the scalar dd operations the kernels use:
+ *   "add"  accurate dd addition (two TwoSums, relative error <= 3u^2+13u^3);
+ *   "mul"  dd product (exact hi*hi by FMA plus the cross products);
+ *   "div"  two-digit long division (first digit RN(x.hi / y.hi), second
+ *          from the exact remainder), relative error below ~11 u^2;
+ *   "divr" the same with the second digit taken by RN(1 / y.hi) (as the
+ *          Cholesky and triangular-solve kernels divide), below ~20 u^2;
+ *   "sqrt" sqrt(x) (y not read): RN(sqrt(x.hi)) plus one Newton step by
+ *          rsqrt; 0 for x <= 0;
+ *   "rcp"  1 / x (y not read), as the LU panels form their multipliers.
+ * u = 2^-53.  div, divr and sqrt are exact when the exact result is a
+ * binary64 number and the operands' lo parts are 0.  Asynchronous on the
+ * current stream.  Errors: -1 unknown op, -2 n < 0, -3/-4/-5 x/y/z NULL
+ * (y only for the binary ops). */
+int mp_dd_elementwise(const char *op, int64_t n, mp_dd_cmat x, mp_dd_cmat y, mp_dd_mat z);
+
+/* ------------------------------------------------------------------------ */
 /* Measured roofline denominators (no counterpart in the manual)             */
 /* ------------------------------------------------------------------------ */
 

@@ -24,7 +24,8 @@ from ._abi import MpDD, MpDDCMat, MpDDMat
 
 __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
-    "mp_dd_peak_fp64", "mp_dd_set_stream", "mp_dd_last_error", "mp_dd_Rgemm_sliced",
+    "mp_dd_peak_fp64", "mp_dd_elementwise", "mp_dd_set_stream", "mp_dd_last_error",
+    "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_Rsyrk_crt",
     "mp_dd_Rsyrk_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
@@ -338,6 +339,14 @@ def mp_dd_trsm_batch(count, descs_dev, max_nrhs, check=True):
     _sync_stream()
     rc = _LIB.mp_dd_trsm_batch(count, _ptr(descs_dev), max_nrhs)
     return _check(rc, "mp_dd_trsm_batch") if check else rc
+
+
+def mp_dd_elementwise(op, n, x, y, z, check=True):
+    _sync_stream()
+    yy = y if y is not None else (None, None)
+    rc = _LIB.mp_dd_elementwise(op.encode() if isinstance(op, str) else op, n, _cm(x), _cm(yy),
+                                _m(z))
+    return _check(rc, "mp_dd_elementwise") if check else rc
 
 
 def mp_dd_peak_fp64() -> float:

@@ -675,6 +675,23 @@ int mp_dd_sliced_phase_ms(float ms[3]) {
     return sliced_timing_read(ms);
 }
 
+int mp_dd_elementwise(const char *op, int64_t n, mp_dd_cmat x, mp_dd_cmat y, mp_dd_mat z) {
+    clear_error();
+    static const char *names[] = {"add", "mul", "div", "divr", "sqrt", "rcp"};
+    int code = -1;
+    for (int i = 0; i < 6 && op != nullptr; ++i)
+        if (strcmp(op, names[i]) == 0) code = i;
+    if (code < 0) return fail(-1, "elementwise: unknown op");
+    if (n < 0) return fail(-2, "elementwise: n < 0");
+    if (n == 0) return 0;
+    if (x.hi == nullptr || x.lo == nullptr) return fail(-3, "elementwise: x is NULL");
+    if (code < 4 && (y.hi == nullptr || y.lo == nullptr)) return fail(-4, "elementwise: y is NULL");
+    if (z.hi == nullptr || z.lo == nullptr) return fail(-5, "elementwise: z is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return run_dd_elementwise(code, n, x.hi, x.lo, y.hi, y.lo, z.hi, z.lo, tls().stream);
+}
+
 int mp_dd_peak_fp64(double *rate) {
     clear_error();
     if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");

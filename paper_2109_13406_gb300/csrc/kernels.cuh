@@ -61,6 +61,8 @@ int grouped_run(void *ws, cudaStream_t stream);
 int run_potrf(int lower, int64_t n, double *ah, double *al, int64_t lda, int64_t *info,
               cudaStream_t stream, void *ws = nullptr, size_t ws_bytes = 0);
 size_t potrf_crt_workspace_bytes(int64_t n);
+int run_dd_elementwise(int op, int64_t n, const double *xh, const double *xl, const double *yh,
+                       const double *yl, double *zh, double *zl, cudaStream_t stream);
 int run_potrs(int lower, int64_t n, int64_t nrhs, const double *ah, const double *al,
               int64_t lda, double *bh, double *bl, int64_t ldb, const int64_t *info,
               cudaStream_t stream);
