@@ -228,9 +228,13 @@ int mp_dd_Rtrsm(const char *side, const char *uplo, const char *transa, const ch
  * of largest dd magnitude.  *info (DEVICE int64, required) receives 0 or
  * j > 0 when U(j, j) is exactly zero (the factorisation completes, as in
  * LAPACK).  Recursive column splitting (LAPACK's dgetrf2): the updates are
- * dd Rtrsm and dd Rgemm products, the single-column leaves one CTA each.
+ * dd Rtrsm and dd Rgemm products, the leaves panels of at most 32 columns,
+ * each one cooperative launch with its rows spread over the SMs.  A
+ * panel's grid-barrier waits are bounded (~2 s, which co-resident CTAs
+ * never reach); a wait that gives up stops the panel and sets *info = -1.
  * Accuracy: the backward error of Gaussian elimination in dd arithmetic
- * (LAPACK test ratio ||P A - L U|| / (n ||A|| 2^-104) < 30).  Asynchronous.
+ * (LAPACK test ratio ||P A - L U|| / (n ||A|| 2^-104) < 30).  Asynchronous
+ * (a small stream-ordered allocation holds the panels' exchange buffers).
  * Errors: -1 m < 0, -2 n < 0, -3 A NULL, -4 lda < max(1, m), -5 ipiv NULL,
  * -6 info NULL. */
 int mp_dd_Rgetrf(int64_t m, int64_t n, mp_dd_mat A, int64_t lda, int64_t *ipiv,
