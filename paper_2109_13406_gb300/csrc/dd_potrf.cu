@@ -371,8 +371,13 @@ __device__ void trsm_one(const mp_dd_trsm_desc &d, int64_t c0, double *sm, TrsmS
                         mac_deferred(acc[q], dd{-uh[base + r], -ul[base + r]}, x);
                 }
                 if ((step & (kRenormEvery - 1)) == kRenormEvery - 1) {
+                    // rows still to be solved only: a solved row holds its
+                    // normalised result, on which renorm changes nothing
 #pragma unroll
-                    for (int q = 0; q < RPT; ++q) renorm(acc[q]);
+                    for (int q = 0; q < RPT; ++q) {
+                        const int r = rg + RG * q;
+                        if (TRANS ? r > i : r < i) renorm(acc[q]);
+                    }
                 }
             }
             ++step;
@@ -415,13 +420,42 @@ __global__ void __launch_bounds__(NT, 2) trsm_single_kernel(const mp_dd_trsm_des
 
 constexpr TrsmScale kNoScale{dd{1.0, 0.0}, 0};
 
-// Row groups for count solves of nrhs columns: the widest CTAs (most
-// columns each) that still give every SM two of them, else 4 columns.
+// Row groups for count solves of nrhs columns.  Measured on GB300 (one
+// 64-row solve of many columns; microseconds for an SM holding k resident
+// CTAs of each width): a wide CTA (32 columns) makes the best use of the
+// FP64 pipe once every SM has two of them, narrow ones win while the
+// columns are too few to fill the SMs.  The cost of a choice is the busiest
+// SM's: ceil(CTAs / SMs) CTAs in waves of the kernel's occupancy.  The
+// cheapest is taken, or a wider one within 5 % of it.
+constexpr int kRgCount = 4;                 // rg = 8, 16, 32, 64
+constexpr float kSolveUs[kRgCount][5] = {
+    {318.f, 552.f, 552.f, 552.f, 552.f},    // 32 columns per CTA (2 resident)
+    {199.f, 311.f, 442.f, 442.f, 442.f},    // 16 (3 resident)
+    {133.f, 186.f, 253.f, 330.f, 330.f},    //  8 (4 resident)
+    {109.f, 147.f, 195.f, 244.f, 300.f},    //  4 (5 resident)
+};
+int g_trsm_occ[kRgCount] = {0, 0, 0, 0};    // resident CTAs per SM (0: not queried)
+
+float trsm_cost(int idx, int64_t per_sm) {
+    int occ = g_trsm_occ[idx];
+    if (occ < 1) occ = 1;
+    if (occ > 5) occ = 5;
+    const int64_t full = per_sm / occ, rem = per_sm % occ;
+    return (float)full * kSolveUs[idx][occ - 1] + (rem ? kSolveUs[idx][rem - 1] : 0.f);
+}
+
 int trsm_row_groups(int64_t count, int64_t nrhs) {
-    const int64_t want = 2 * (int64_t)(sm_count() > 0 ? sm_count() : 152);
-    for (int rg = 8; rg <= 32; rg *= 2)
-        if (count * ceil_div(nrhs, NT / rg) >= want) return rg;
-    return 64;
+    const int64_t sms = sm_count() > 0 ? sm_count() : 152;
+    float cost[kRgCount];
+    int cheapest = 0;
+    for (int idx = 0; idx < kRgCount; ++idx) {
+        const int64_t cols = NT / (8 << idx);
+        cost[idx] = trsm_cost(idx, ceil_div(count * ceil_div(nrhs, cols), sms));
+        if (cost[idx] < cost[cheapest]) cheapest = idx;
+    }
+    for (int idx = 0; idx < cheapest; ++idx)      // wider, nearly as cheap
+        if (cost[idx] <= 1.05f * cost[cheapest]) return 8 << idx;
+    return 8 << cheapest;
 }
 
 // One launch of count solves (ds on the device) or of the single solve d.
@@ -471,6 +505,14 @@ int set_attrs() {
     if (e == cudaSuccess) e = trsm_attrs<32>();
     if (e == cudaSuccess) e = trsm_attrs<64>();
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(potrf kernels)");
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trsm_occ[0], trsm_batch_kernel<8>, NT,
+                                                  trsm_smem_bytes(8));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trsm_occ[1], trsm_batch_kernel<16>, NT,
+                                                  trsm_smem_bytes(16));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trsm_occ[2], trsm_batch_kernel<32>, NT,
+                                                  trsm_smem_bytes(32));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_trsm_occ[3], trsm_batch_kernel<64>, NT,
+                                                  trsm_smem_bytes(64));
     g_attr_done = true;
     return 0;
 }
