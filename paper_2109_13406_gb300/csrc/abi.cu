@@ -3,6 +3,7 @@
 // and error state, and dispatch to the kernels.
 #include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -54,6 +55,38 @@ int require_device() {
                     minor);
     }
     return fail(MP_DD_ERR_NO_DEVICE, "libmpdd is built for sm_103a only");
+}
+
+// The library's own stream-ordered memory pool on each device, for the
+// scratch buffers of the host-buffer forms and the LU panels.  Its release
+// threshold keeps freed memory mapped for the next call (the device's
+// default pool would hand it back to the driver at every synchronisation,
+// and mapping a gigabyte again costs tens of milliseconds).
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(ptr, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (pools[dev] == nullptr) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaError_t e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
 }
 
 int sm_count() {
@@ -139,9 +172,13 @@ bool quick_return(const GemmArgs &p) {
 int copy_plane(void *dst, int64_t dld, const void *src, int64_t sld, int64_t rows,
                int64_t cols, cudaMemcpyKind kind, cudaStream_t st) {
     if (rows == 0 || cols == 0) return 0;
-    cudaError_t e = cudaMemcpy2DAsync(dst, (size_t)dld * 8, src, (size_t)sld * 8,
-                                      (size_t)rows * 8, (size_t)cols, kind, st);
-    return e == cudaSuccess ? 0 : cuda_fail(e, "cudaMemcpy2DAsync");
+    cudaError_t e;
+    if (dld == rows && sld == rows)   // both tight: one contiguous copy
+        e = cudaMemcpyAsync(dst, src, (size_t)rows * cols * 8, kind, st);
+    else
+        e = cudaMemcpy2DAsync(dst, (size_t)dld * 8, src, (size_t)sld * 8, (size_t)rows * 8,
+                              (size_t)cols, kind, st);
+    return e == cudaSuccess ? 0 : cuda_fail(e, "host-device copy");
 }
 
 // Run a validated problem whose A, B, C planes are host memory: stage them
@@ -156,14 +193,14 @@ int run_host(GemmArgs p, int64_t arows, int64_t acols, int64_t brows, int64_t bc
     cudaError_t e;
     bool read_ab = !p.alpha_zero;
     if (read_ab && asz > 0) {
-        e = cudaMallocAsync(&dA, sizeof(double) * 2 * asz, st);
+        e = pool_alloc(reinterpret_cast<void **>(&dA), sizeof(double) * 2 * asz, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A)");
     }
     if (read_ab && bsz > 0) {
-        e = cudaMallocAsync(&dB, sizeof(double) * 2 * bsz, st);
+        e = pool_alloc(reinterpret_cast<void **>(&dB), sizeof(double) * 2 * bsz, st);
         if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocAsync(B)"); goto done; }
     }
-    e = cudaMallocAsync(&dC, sizeof(double) * 2 * csz, st);
+    e = pool_alloc(reinterpret_cast<void **>(&dC), sizeof(double) * 2 * csz, st);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMallocAsync(C)"); goto done; }
     if (read_ab && asz > 0) {
         if ((rc = copy_plane(dA, arows, p.ah, p.lda, arows, acols, cudaMemcpyHostToDevice, st)))

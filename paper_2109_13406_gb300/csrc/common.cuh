@@ -70,5 +70,8 @@ int require_device();
 
 // Number of SMs of the current device (cached).
 int sm_count();
+// Stream-ordered allocation from the library's own pool (freed memory stays
+// mapped for later calls); free with cudaFreeAsync.
+cudaError_t pool_alloc(void **ptr, size_t bytes, cudaStream_t st);
 
 }  // namespace mpdd

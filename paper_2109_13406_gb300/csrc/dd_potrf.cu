@@ -1394,7 +1394,7 @@ int run_getrf(int64_t m, int64_t n, double *ah, double *al, int64_t lda, int64_t
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, getrf_panel_kernel, kPanelThreads, 0);
     const int64_t ctas = (int64_t)per_sm * (sm_count() > 0 ? sm_count() : 0);
     if (coop && ctas > 0) {
-        e = cudaMallocAsync(reinterpret_cast<void **>(&P.panel_ws), sizeof(PanelWs), st);
+        e = pool_alloc(reinterpret_cast<void **>(&P.panel_ws), sizeof(PanelWs), st);
         if (e != cudaSuccess) return cuda_fail(e, "panel workspace");
         P.panel_ctas = ctas < kPanelMaxG ? ctas : kPanelMaxG;
         if (P.panel_ctas > (sm_count() > 0 ? sm_count() : 1)) P.panel_ctas = sm_count();
