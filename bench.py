@@ -694,28 +694,39 @@ def run_e2e(args, mp, torch, nn, tn, syrk, ranks):
     hsy = [pin(syrk["A"]), pin(syrk["C"])]
     steps = max(1, min(args.steps, 3))
 
+    walls = {"Rgemm_NN": [], "Rgemm_TN": [], "Rsyrk_UN": []}
+
     def step():
-        for c, (A, B, C) in ((nn, hnn), (tn, htn)):
+        for nm, c, (A, B, C) in (("Rgemm_NN", nn, hnn), ("Rgemm_TN", tn, htn)):
+            t = time.perf_counter()
             mp.mp_dd_Rgemm_host(c.transa, c.transb, size, size, size, c.alpha, A, size, B, size,
                                 c.beta, C, size)
+            walls[nm].append(time.perf_counter() - t)
+        t = time.perf_counter()
         mp.mp_dd_Rsyrk_host("U", "N", size, size, syrk["alpha"], hsy[0], size, syrk["beta"],
                             hsy[1], size)
+        walls["Rsyrk_UN"].append(time.perf_counter() - t)
 
     step()
     torch.cuda.synchronize()
     ranks.barrier()
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
     dt = ranks.max(time.perf_counter() - t0)
+    clocks = clk.stop()
     per_mat = 16 * size * size
     h2d = 2 * 3 * per_mat + 2 * per_mat      # two GEMMs (A, B, C) + Rsyrk (A, C)
     d2h = 3 * per_mat
     flops = sum(plain_flops(size).values())
     return {"value": ranks.whole_job(flops * steps, dt) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
-            "api": "mp_dd_Rgemm_host / mp_dd_Rsyrk_host (pinned host buffers)"}
+            "api": "mp_dd_Rgemm_host / mp_dd_Rsyrk_host (pinned host buffers)",
+            "per_call_ms": {nm: 1e3 * sum(v[1:]) / max(1, len(v) - 1) for nm, v in walls.items()},
+            "clocks": clocks}
 
 
 # ----------------------------------------------------------------------------
