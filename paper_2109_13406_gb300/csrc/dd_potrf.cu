@@ -1,7 +1,10 @@
 // dd Cholesky factorisation and solve (Rpotrf / Rpotrs, MPLAPACK routine
 // table of the manual's Sec. 6; the Rpotrf benchmark of Sec. 10.5), built as
-// the LAPACK blocked right-looking algorithm on three kernels, and the
-// triangular solve Rtrsm (MPBLAS, Sec. 6) on the same two of them:
+// the LAPACK blocked right-looking algorithm on three kernels (and, with a
+// workspace, in outer steps of 256 columns whose updates are residue-form
+// products on the tensor cores), the triangular solve Rtrsm (MPBLAS,
+// Sec. 6) on the same two of them, and, further below, the LU
+// factorisation Rgetrf / Rgetrs:
 //
 //  * diag:  unblocked Cholesky of one nb x nb diagonal block (nb <= 64), in
 //           registers, on a cluster of up to 8 CTAs per block;
