@@ -105,3 +105,42 @@ def test_host_variants_check_arguments(mp):
                                check=False) == -8
     assert mp.mp_dd_Rsyrk_host("U", "N", 2, 2, (1.0, 0.0), A, 4, (0.0, 0.0), A, 1,
                                check=False) == -10
+
+
+def test_header_and_library_serve_a_plain_c_program(mp, tmp_path):
+    """The boundary is a C ABI: a C99 program that includes only mpdd.h
+    compiles warning-free, links against libmpdd.so and gets DGEMM / DSYRK
+    argument errors and messages back without a GPU."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_mpdd.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "mpdd.h"
+int main(void) {
+    mp_dd one = {1.0, 0.0};
+    mp_dd_cmat A = {0, 0};
+    mp_dd_mat C = {0, 0};
+    if (mp_dd_Rgemm("X", "N", 2, 2, 2, one, A, 2, A, 2, one, C, 2) != -1) return 1;
+    if (strstr(mp_dd_last_error(), "transa") == NULL) return 2;
+    if (mp_dd_Rsyrk("U", "N", -1, 2, one, A, 2, one, C, 2) != -3) return 3;
+    if (mp_dd_Rgemm("N", "N", 0, 2, 2, one, A, 2, A, 2, one, C, 2) != 0) return 4;
+    if (mp_dd_version() <= 0) return 5;
+    printf("ok\n");
+    return 0;
+}
+''')
+    exe = tmp_path / "use_mpdd"
+    pkg = os.path.join(ROOT, "paper_2109_13406_gb300")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", pkg, "-lmpdd", f"-Wl,-rpath,{pkg}"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
