@@ -19,7 +19,7 @@ import os
 import numpy as np
 import torch
 
-from . import _abi, _check, _dd, _ld, _sync_stream, lib, to_device, workspace
+from . import _abi, _check, _dd, _ld, _sync_stream, lib, workspace
 from ._abi import MpDDGemmDesc
 
 SHAPES = {0: (32, 32), 1: (64, 32), 2: (32, 64), 3: (16, 16)}

@@ -36,7 +36,6 @@ bitwise the same alone and in the mix.
 """
 from __future__ import annotations
 
-import ctypes
 import time
 from dataclasses import dataclass, field
 

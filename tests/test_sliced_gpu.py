@@ -15,7 +15,6 @@ import torch
 import datagen
 import oracle
 from oracle import ozaki_ref as oz
-from ddcheck import err_over_bound, gemm_bound_entries, is_normalised
 from gpucase import check_against_exact, dev, host, sample_blocks
 
 pytestmark = pytest.mark.gpu
