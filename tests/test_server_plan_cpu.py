@@ -108,10 +108,19 @@ def run_plan(steps):
                 _apply_batch(batch)
 
 
+@pytest.fixture(scope="module")
+def built():
+    """The package loads libmpdd.so on import: build it first (nvcc
+    cross-compiles; nothing here touches a GPU)."""
+    import __graft_entry__
+
+    __graft_entry__._build_module().build()
+
+
 @pytest.mark.parametrize("n", [64, 100, 300, 600])
 @pytest.mark.parametrize("group", [1, 4])
 @pytest.mark.parametrize("tensor_cores", [False, True])
-def test_plan_solves_the_system(n, group, tensor_cores):
+def test_plan_solves_the_system(built, n, group, tensor_cores):
     from paper_2109_13406_gb300.server import Request, SpdServer
 
     g = np.random.Generator(np.random.PCG64(800 + n))
