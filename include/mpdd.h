@@ -562,6 +562,14 @@ int mp_dd_elementwise(const char *op, int64_t n, mp_dd_cmat x, mp_dd_cmat y, mp_
  * Synchronous (synchronises the current stream).  Returns 0 or an error. */
 int mp_dd_peak_fp64(double *rate);
 
+/* Time a kernel of independent INT8 warp-level tensor instructions
+ * (mma.sync m16n8k32, s8 inputs, s32 accumulation; sm_103a offers no
+ * tcgen05 INT8 form) filling every SM, and report the rate in integer
+ * operations per second (2 per multiply-add) in *rate.  This is the ceiling
+ * of an INT8-slice split-precision product on this GPU, against which the
+ * fp16 tcgen05 path is compared.  Synchronous.  Returns 0 or an error. */
+int mp_dd_peak_imma(double *rate);
+
 #ifdef __cplusplus
 }
 #endif

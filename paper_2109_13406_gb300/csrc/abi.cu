@@ -737,4 +737,12 @@ int mp_dd_peak_fp64(double *rate) {
     return run_peak_fp64(tls().stream, rate);
 }
 
+int mp_dd_peak_imma(double *rate) {
+    clear_error();
+    if (rate == nullptr) return fail(-1, "peak_imma: rate is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return run_peak_imma(tls().stream, rate);
+}
+
 }  // extern "C"

@@ -39,6 +39,8 @@ int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream);
 
 // FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.
 int run_peak_fp64(cudaStream_t stream, double *rate);
+// INT8 warp-level tensor rate (mma.sync m16n8k32 s8); *rate in integer ops/s.
+int run_peak_imma(cudaStream_t stream, double *rate);
 
 // Split-precision (sliced) Rgemm on the fp16 tensor cores.
 constexpr int kDefaultSlices = 14;  // base-256 digits per operand entry

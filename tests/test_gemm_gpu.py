@@ -177,3 +177,9 @@ def test_config1_large_sampled_blocks(cuda_lib, ta):
 def test_fp64_peak_is_positive(cuda_lib):
     r = cuda_lib.mp_dd_peak_fp64()
     assert r > 1e10
+
+
+def test_imma_peak_is_positive(cuda_lib):
+    """The warp-level INT8 tensor rate (mma.sync m16n8k32) is measurable."""
+    r = cuda_lib.mp_dd_peak_imma()
+    assert r > 1e12
