@@ -402,8 +402,25 @@ int mp_qd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, in
 /* Split-precision Rgemm on the tensor cores (no counterpart in the manual)  */
 /* ------------------------------------------------------------------------ */
 
+/* What the last split-precision call on a workspace did (no counterpart in
+ * the manual): the certificate's outcome and a guaranteed error estimate. */
+typedef struct mp_dd_split_info_s {
+    int status;          /* 0, or 2001 when a device wait timed out (C undefined) */
+    int form;            /* 1 digit slices, 2 residues; 0: no product was formed
+                            (alpha = 0 or k = 0: C := beta C) */
+    int width_bits;      /* bits W each operand entry was rounded to (8 S, or
+                            112 / 120 / 128); 0: the plain FP64 kernel computed C */
+    int count;           /* slices S (form 1) or moduli N (form 2); 0 with W = 0 */
+    double max_err_est;  /* upper bound of max_ij |C - C_exact|_ij / bound_ij, the
+                            bound of mp_dd_Rgemm; <= 1 whenever status is 0 */
+    double dmin;         /* the certificate's smallest margin
+                            min_ij (L_ij + |beta/alpha||c_ij|) 2^-(e_i+f_j), L_ij a
+                            lower bound of (|A||B|)_ij (+inf: nothing constrains) */
+} mp_dd_split_info;
+
 /* Workspace bytes mp_dd_Rgemm_sliced needs for an m x n x k product with
- * `slices` digits per operand entry (0 = the default, 14). */
+ * `slices` digits per operand entry (0 = chosen per call, 14 or 15: sized
+ * for 15 when k allows it). */
 size_t mp_dd_Rgemm_sliced_workspace(int64_t m, int64_t n, int64_t k, int slices);
 
 /* Rgemm with the same arguments and result contract as mp_dd_Rgemm
@@ -412,23 +429,28 @@ size_t mp_dd_Rgemm_sliced_workspace(int64_t m, int64_t n, int64_t k, int slices)
  *  - each row of op(A) and column of op(B) is scaled by a power of two so
  *    its entries are below 1/2 in magnitude; every dd entry is then rounded
  *    to a multiple of 2^-8S of that scale (error at most one unit) and cut
- *    into `slices` = S signed base-256 digits in [-128, 128];
+ *    into S signed base-256 digits in [-128, 128];
  *  - the digit products are exact integer GEMMs (fp16 inputs, fp32
  *    accumulation kept exact by draining every 512 products, int32 sums),
  *    grouped by digit significance t + u = b for b < S;
  *  - the band sums are combined exactly in integer arithmetic, rounded once
  *    to dd, scaled back, and alpha/beta are applied in dd arithmetic.
- * Accuracy: per product the truncation error is at most ~4.3 *
- * 2^(e_i + f_j - 8S) with 2^(e_i-1) > max_l |A_il| and 2^(f_j-1) > max_l
- * |B_lj|; S = 14 (the default) keeps the result within the mp_dd_Rgemm
- * bound whenever (|A||B|)_ij >= k 2^(e_i+f_j) 2^-8 (e.g. entries of one
- * row/column within a few binades of its maximum, any scaling between rows
- * and columns).  Larger S (<= 15) tightens it by 2^-8 per slice.
- * Limits: 2 <= slices <= 15; k * slices <= 131071 (int32 band sums).
+ * Accuracy (unconditional): |C - C_exact| <= 4 k 2^-104 (|alpha||A||B| +
+ * |beta||C|) componentwise, as mp_dd_Rgemm.  Per product the error of the
+ * digits is at most C_S 2^(e_i + f_j - 8S) (C_S = 1 + (S-1)/(4 (1 - 2^-8)),
+ * 2^(e_i - 1) > max_l |A_il|, 2^(f_j - 1) > max_l |B_lj|).  Before slicing,
+ * the call certifies this on the device, entry by entry, against a
+ * guaranteed lower bound of |A||B| (one bf16 tensor-core product of the
+ * operands' magnitudes, rounded toward zero); `slices` = 0 lets it take
+ * S = 14 or, if needed, 15 (the narrowest that certifies); a non-zero
+ * `slices` is the only S tried.  When no S certifies the bound, the plain
+ * FP64 kernel of mp_dd_Rgemm computes C instead, within the same call (no
+ * host synchronisation); mp_dd_split_report tells which happened.
+ * Limits: 2 <= slices <= 15; k * S <= 131071 (int32 band sums).
  * `workspace` is device memory of at least
  * mp_dd_Rgemm_sliced_workspace(m, n, k, slices) bytes owned by the caller;
- * its first 4 bytes receive a device status word (0, or 2001 when a device
- * wait timed out), readable with mp_dd_workspace_status after the call.
+ * it begins with a header (status word, certificate) that
+ * mp_dd_workspace_status and mp_dd_split_report read after the call.
  * Calls sharing a workspace must not overlap on the device.  Asynchronous.
  * Errors: as mp_dd_Rgemm, plus -14 slices out of range, -15 workspace NULL,
  * 2003 workspace too small, 2002 k * slices too large. */
@@ -455,28 +477,38 @@ int mp_dd_Rgemm_sliced(const char *transa, const char *transb, int64_t m, int64_
  * capture starts.  All calls share the one array, which keeps the last
  * call's contents: each call clears what must start at zero itself, and
  * calls that overlap on the GPU (different streams or unordered threads)
- * race on it and give wrong results.  The device status word is the first
- * 4 bytes of the array (not readable through mp_dd_workspace_status). */
+ * race on it and give wrong results.  The array begins with the same header
+ * as a workspace: mp_dd_noalloc_report reads it.  The cached address is
+ * looked up again on every call made outside stream capture, so a device
+ * reset (which reloads the library's device code) is picked up. */
 #define MP_DD_NOALLOC_SCRATCH_BYTES (32u << 20)
 int mp_dd_Rgemm_sliced_noalloc(const char *transa, const char *transb, int64_t m, int64_t n,
                                int64_t k, mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B,
                                int64_t ldb, mp_dd beta, mp_dd_mat C, int64_t ldc, int slices);
 
+/* mp_dd_split_report for the built-in scratch array of the current device:
+ * the status word (0, or 2001 when a device wait of the last
+ * mp_dd_Rgemm_sliced_noalloc call timed out) and its certificate.  Waits for
+ * the calling thread's current stream.  Errors: -1 info NULL, 1000 + e. */
+int mp_dd_noalloc_report(mp_dd_split_info *info);
+
 /* Residue (CRT) form of the split-precision Rgemm (no counterpart in the
  * manual).  Same arguments 1-13, result contract and errors as
- * mp_dd_Rgemm_sliced at 14 slices, and the same rounding of the operands
- * (every entry of a row of op(A) / column of op(B) rounded to a multiple of
- * 2^(e-112) of its power-of-two scale, |error| <= one unit), but the exact
- * integer product of the rounded operands is formed through the Chinese
- * remainder theorem: residues modulo N pairwise coprime moduli <= 256 (N
- * about 32 for k = 8192; the product of the moduli exceeds 2 k 2^222), one
- * fp16 tensor-core GEMM per modulus with exact int32 accumulation, and an
- * exact multiword reconstruction rounded once to dd.  About N products
- * instead of S(S+1)/2 = 105, and no truncation of digit pairs: the only
- * error is the operand rounding, at most 2^(e_i + f_j - 112) per product.
- * Limits: k <= 131071.  workspace: device memory of at least
- * mp_dd_Rgemm_crt_workspace(m, n, k) bytes, status word first (read it with
- * mp_dd_workspace_status).  Asynchronous.  Errors: as mp_dd_Rgemm, -14
+ * mp_dd_Rgemm_sliced.  Every entry of a row of op(A) / column of op(B) is
+ * rounded to a multiple of 2^(e - W) of its power-of-two scale (|error| <=
+ * one unit), and the exact integer product of the rounded operands is formed
+ * through the Chinese remainder theorem: residues modulo N pairwise coprime
+ * moduli <= 256 (the product of the moduli at least k 2^(2W)), one fp16
+ * tensor-core GEMM per modulus with exact int32 accumulation, and an exact
+ * multiword reconstruction rounded once to dd.  The only error is the
+ * operand rounding, at most (1 + 2^-W) 2^(e_i + f_j - W) per product.  The
+ * call certifies it on the device as mp_dd_Rgemm_sliced does and takes the
+ * narrowest of W = 112, 120, 128 bits that meets the bound (N = 32, 36, 38
+ * moduli at k = 8192), else computes C with the plain FP64 kernel; so the
+ * mp_dd_Rgemm bound holds unconditionally.  Limits: k <= 131071.
+ * workspace: device memory of at least mp_dd_Rgemm_crt_workspace(m, n, k)
+ * bytes (sized for the widest W), header first (mp_dd_workspace_status,
+ * mp_dd_split_report).  Asynchronous.  Errors: as mp_dd_Rgemm, -14
  * workspace NULL, 2003 workspace too small, 2002 k too large. */
 size_t mp_dd_Rgemm_crt_workspace(int64_t m, int64_t n, int64_t k);
 int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
@@ -495,7 +527,8 @@ int mp_dd_Rgemm_crt(const char *transa, const char *transb, int64_t m, int64_t n
  * the tiles and entries of the triangle are formed: about half the work of
  * mp_dd_Rgemm_crt on (A, A^T).  Every entry of the triangle is bitwise equal
  * to mp_dd_Rgemm_crt(N, T) (trans N) or (T, N) (trans T) on A, A.  Accuracy
- * and limits as mp_dd_Rgemm_crt.  workspace: at least
+ * (certified per call, over the triangle only) and limits as
+ * mp_dd_Rgemm_crt.  workspace: at least
  * mp_dd_Rsyrk_crt_workspace(n, k) bytes.  Asynchronous. */
 size_t mp_dd_Rsyrk_crt_workspace(int64_t n, int64_t k);
 int mp_dd_Rsyrk_crt(const char *uplo, const char *trans, int64_t n, int64_t k, mp_dd alpha,
@@ -507,7 +540,9 @@ int mp_dd_Rsyrk_crt(const char *uplo, const char *trans, int64_t n, int64_t k, m
  * residue planes of op(A) (fp16 [N][m_pad][k_pad]), of op(B)^T (fp16
  * [N][n_pad][k_pad]) and the products reduced mod p_i (uint8
  * [N][n_pad][m_pad]); offsets[5..7] m_pad, n_pad, k_pad; offsets[8..8+N)
- * the moduli; *moduli = N.  Returns 0. */
+ * the moduli; *moduli = N, the planes the workspace holds (the widest
+ * width's count; a call fills the first mp_dd_split_info.count of them).
+ * Returns 0. */
 int mp_dd_crt_layout(int64_t m, int64_t n, int64_t k, size_t offsets[48], int *moduli);
 
 /* Byte offsets of the intermediate arrays inside a sliced-Rgemm workspace
@@ -519,8 +554,26 @@ int mp_dd_crt_layout(int64_t m, int64_t n, int64_t k, size_t offsets[48], int *m
  * n_pad, k_pad.  Returns 0. */
 int mp_dd_sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t offsets[8]);
 
-/* Read the device status word of a workspace (synchronous copy). */
+/* Read the device status word of a workspace (waits for the calling
+ * thread's current stream, then copies). */
 int mp_dd_workspace_status(const void *workspace, int *status);
+
+/* Fill *info from the header of `workspace` after a mp_dd_Rgemm_sliced,
+ * mp_dd_Rgemm_crt or mp_dd_Rsyrk_crt call (waits for the calling thread's
+ * current stream, then copies the header).  A call that returned before any
+ * device work (argument error, BLAS quick return) leaves the header as it
+ * was.  Errors: -1 workspace NULL, -2 info NULL, 1000 + e copy failure. */
+int mp_dd_split_report(const void *workspace, mp_dd_split_info *info);
+
+/* Byte offsets of the certificate's magnitude planes in a workspace (for
+ * inspection and testing): offsets[0] op(A) (bf16 [m_pad][k_pad]: the
+ * largest bf16 not above |hi| 2^-e_i), offsets[1] op(B)^T (bf16
+ * [n_pad][k_pad]; equal to offsets[0] for the Rsyrk form).  form: 1 sliced
+ * (slices as for mp_dd_Rgemm_sliced_workspace), 2 CRT Rgemm, 3 CRT Rsyrk
+ * (m = n).  Returns 0, or -1 form, -2 .. -4 a negative size, -5 slices out
+ * of range, -6 offsets NULL. */
+int mp_dd_magnitude_layout(int form, int64_t m, int64_t n, int64_t k, int slices,
+                           size_t offsets[2]);
 
 /* Per-phase timing of split-precision calls (no counterpart in the manual).
  * With enable != 0, later mp_dd_Rgemm_sliced and mp_dd_Rgemm_crt calls from

@@ -18,6 +18,11 @@ arithmetic (Python ints and ``fractions``), one function per step:
 5. the residue (CRT) form: ``crt_moduli``, ``residue_planes`` (symmetric
    residues of the same integers X), ``crt_products`` (R^A_i R^B_i^T mod p_i)
    and ``crt_reconstruct`` (the textbook CRT sum mapped to (-P/2, P/2]).
+6. the per-call certificate: ``bf16_floor`` / ``magnitude_row`` (the
+   magnitude planes), ``product_error_constant`` (the error of one product
+   of rounded operands, per form), ``exact_margins`` (the margin of every
+   output entry from the exact |A||B|) and ``certified_width`` (the rule
+   that turns the smallest margin into an operand width, 0 = none).
 
 Parity status: pinned by ``tests/test_ozaki_oracle.py`` -- digit expansions
 reproduce X exactly and stay in range, X approximates x within one unit of
@@ -25,7 +30,11 @@ reproduce X exactly and stay in range, X approximates x within one unit of
 documented truncation bound, and it equals the exact product when every
 digit beyond the first band is zero (integer and power-of-two inputs); the
 CRT reconstruction equals the integer product of the rounded operands, and
-the moduli are pairwise coprime.
+the moduli are pairwise coprime; bf16_floor is the largest bf16 below its
+argument (brute force over the neighbouring bf16 values); every product of
+rounded operands stays within its form's constant times 2^(e_i+f_j-W); and a
+certified width keeps the exact error of a call within the bound while the
+default width (112 bits) does not on the stress inputs.
 """
 from __future__ import annotations
 
@@ -181,3 +190,82 @@ def crt_reconstruct(res, moduli):
         s = sum(int(res[(i,) + idx]) * w for i, w in enumerate(weights)) % P
         out[idx] = s - P if 2 * s > P else s
     return out
+
+
+# ----------------------------------------------------------------------------
+# Per-call certificate: the operand width that meets the accuracy bound
+# ----------------------------------------------------------------------------
+
+def bf16_floor(x: Fraction) -> Fraction:
+    """The largest bf16 value not above x >= 0: 8 significant bits for
+    x >= 2^-126, multiples of 2^-133 below (bf16 subnormals)."""
+    x = Fraction(x)
+    if x <= 0:
+        return Fraction(0)
+    E = math.floor(math.log2(x.numerator) - math.log2(x.denominator))
+    while Fraction(2) ** E > x:          # 2^E <= x < 2^(E+1), exactly
+        E -= 1
+    while Fraction(2) ** (E + 1) <= x:
+        E += 1
+    unit = Fraction(2) ** (E - 7) if E >= -126 else Fraction(2) ** -133
+    return math.floor(x / unit) * unit
+
+
+def magnitude_row(hi_row, e: int):
+    """Magnitude plane entries of one row: bf16_floor(|hi| 2^-e)."""
+    return [bf16_floor(abs(Fraction(float(h))) * Fraction(2) ** -e) for h in hi_row]
+
+
+def product_error_constant(form: str, W: int) -> Fraction:
+    """cst with |a b - (the form's product of rounded a, b)| <= cst 2^(e+f-W):
+    "crt": one unit of rounding per factor, (1 + 2^-W); "sliced" (W = 8S):
+    that plus the digit pairs t + u >= S the band sums drop,
+    sum_{h >= 0} (S - 1 - h) 2^-2 256^-h <= (S - 1) / (4 (1 - 2^-8))."""
+    if form == "crt":
+        return 1 + Fraction(2) ** -W
+    S = W // 8
+    return 1 + Fraction(2) ** -W + Fraction(S - 1, 4) / (1 - Fraction(1, 256))
+
+
+def exact_margins(a_rows, b_cols, alpha, beta, C=None, tri: int = 0):
+    """{(i, j): d_ij} with d_ij = ((|A||B|)_ij + |beta/alpha| |c_ij|) 2^-(e_i+f_j)
+    for the rows of op(A) and columns of op(B) given as (hi, lo) row arrays,
+    from the exact dd values; rows or columns that are all zero, and entries
+    outside the requested triangle (tri 1 upper, 2 lower), are left out."""
+    ah, al = a_rows
+    bh, bl = b_cols
+    m, k = ah.shape
+    n = bh.shape[0]
+    ea = [scale_exponent(ah[i]) for i in range(m)]
+    fb = [scale_exponent(bh[j]) for j in range(n)]
+    A = [[abs(Fraction(float(ah[i, l])) + Fraction(float(al[i, l]))) for l in range(k)]
+         for i in range(m)]
+    B = [[abs(Fraction(float(bh[j, l])) + Fraction(float(bl[j, l]))) for l in range(k)]
+         for j in range(n)]
+    ratio = abs(Fraction(beta[0]) + Fraction(beta[1])) / abs(Fraction(alpha[0]) +
+                                                             Fraction(alpha[1]))
+    out = {}
+    for i in range(m):
+        if not any(ah[i]):
+            continue
+        for j in range(n):
+            if not any(bh[j]) or (tri == 1 and i > j) or (tri == 2 and i < j):
+                continue
+            ab = sum(x * y for x, y in zip(A[i], B[j]))
+            cc = 0 if C is None or ratio == 0 else abs(Fraction(float(C[0][i, j])) +
+                                                      Fraction(float(C[1][i, j])))
+            out[(i, j)] = (ab + ratio * cc) * Fraction(2) ** -(ea[i] + fb[j])
+    return out
+
+
+def certified_width(dmin: Fraction, form: str, widths) -> int:
+    """The narrowest W in ``widths`` (ascending) with
+    cst 2^(106 - W) / 12 <= dmin: then every product error, summed over k,
+    is at most 12 k 2^-106 (|A||B| + |beta/alpha||C|)_ij, three quarters of
+    the bound 4 k 2^-104 (...) per unit of |alpha|, the rest left for the
+    final roundings.  0: no width qualifies."""
+    for W in widths:
+        if product_error_constant(form, W) * Fraction(2) ** (106 - W) / 12 <= dmin:
+            return W
+    return 0
+

@@ -29,6 +29,7 @@ __all__ = [
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_Rsyrk_crt",
     "mp_dd_Rsyrk_crt_workspace", "mp_dd_crt_layout", "mp_dd_workspace_status",
+    "mp_dd_split_report", "mp_dd_noalloc_report", "mp_dd_magnitude_layout",
     "mp_dd_Rtrsm", "mp_dd_Rsyr2k", "mp_dd_Rsymm", "mp_qd_Rgemm", "mp_dd_Rgetrf", "mp_dd_Rgetrs", "mp_dd_Rpotrf", "mp_dd_Rpotrf_crt",
     "mp_dd_Rpotrs", "Rgemm", "Rsyrk", "Rtrsm", "Rgemm_sliced",
     "workspace", "dd_empty", "to_device", "to_numpy", "lib",
@@ -206,10 +207,40 @@ def mp_dd_sliced_layout(m, n, k, slices=0) -> dict:
 
 
 def mp_dd_workspace_status(workspace) -> int:
+    _sync_stream()
     st = ctypes.c_int()
     _check(_LIB.mp_dd_workspace_status(_ptr(workspace), ctypes.byref(st)),
            "mp_dd_workspace_status")
     return st.value
+
+
+def _split_info(info) -> dict:
+    return {"status": info.status, "form": info.form, "width_bits": info.width_bits,
+            "count": info.count, "max_err_est": info.max_err_est, "dmin": info.dmin}
+
+
+def mp_dd_split_report(workspace) -> dict:
+    """The certificate of the last split-precision call on ``workspace``:
+    status, form, width_bits (0: the plain kernel computed C), count,
+    max_err_est (guaranteed bound of max err / bound) and dmin."""
+    _sync_stream()
+    info = _abi.MpDDSplitInfo()
+    _check(_LIB.mp_dd_split_report(_ptr(workspace), ctypes.byref(info)), "mp_dd_split_report")
+    return _split_info(info)
+
+
+def mp_dd_noalloc_report() -> dict:
+    """mp_dd_split_report for the built-in scratch array of the current device."""
+    _sync_stream()
+    info = _abi.MpDDSplitInfo()
+    _check(_LIB.mp_dd_noalloc_report(ctypes.byref(info)), "mp_dd_noalloc_report")
+    return _split_info(info)
+
+
+def mp_dd_magnitude_layout(form, m, n, k, slices=0) -> dict:
+    off = (ctypes.c_size_t * 2)()
+    _check(_LIB.mp_dd_magnitude_layout(form, m, n, k, slices, off), "mp_dd_magnitude_layout")
+    return {"magnitude_a": off[0], "magnitude_b": off[1]}
 
 
 def mp_dd_sliced_timing(enable: bool) -> None:

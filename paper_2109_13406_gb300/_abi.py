@@ -71,6 +71,13 @@ class MpDDTrsmDesc(ctypes.Structure):
                 ("trans", ctypes.c_int32), ("lower_u", ctypes.c_int32),
                 ("lower_b", ctypes.c_int32), ("unit_diag", ctypes.c_int32)]
 
+class MpDDSplitInfo(ctypes.Structure):
+    """``mp_dd_split_info``: outcome of a split-precision call's certificate."""
+    _fields_ = [("status", ctypes.c_int), ("form", ctypes.c_int),
+                ("width_bits", ctypes.c_int), ("count", ctypes.c_int),
+                ("max_err_est", ctypes.c_double), ("dmin", ctypes.c_double)]
+
+
 _c = ctypes.c_char_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -105,6 +112,10 @@ SIGNATURES = {
     "mp_dd_crt_layout": (_int, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_size_t),
                                 ctypes.POINTER(ctypes.c_int)]),
     "mp_dd_workspace_status": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mp_dd_split_report": (_int, [_vp, ctypes.POINTER(MpDDSplitInfo)]),
+    "mp_dd_noalloc_report": (_int, [ctypes.POINTER(MpDDSplitInfo)]),
+    "mp_dd_magnitude_layout": (_int, [_int, _i64, _i64, _i64, _int,
+                                      ctypes.POINTER(ctypes.c_size_t)]),
     "mp_dd_sliced_timing": (_int, [_int]),
     "mp_dd_Rpotrf": (_int, [_c, _i64, MpDDMat, _i64, _vp]),
     "mp_dd_Rpotrs": (_int, [_c, _i64, _i64, MpDDCMat, _i64, MpDDMat, _i64, _vp]),

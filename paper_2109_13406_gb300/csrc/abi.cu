@@ -517,6 +517,36 @@ int mp_dd_workspace_status(const void *workspace, int *status) {
     return read_status(workspace, status);
 }
 
+int mp_dd_split_report(const void *workspace, mp_dd_split_info *info) {
+    clear_error();
+    if (workspace == nullptr) return fail(-1, "split_report: workspace is NULL");
+    if (info == nullptr) return fail(-2, "split_report: info is NULL");
+    return split_report(workspace, info);
+}
+
+int mp_dd_noalloc_report(mp_dd_split_info *info) {
+    clear_error();
+    if (info == nullptr) return fail(-1, "noalloc_report: info is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return noalloc_report(info);
+}
+
+int mp_dd_magnitude_layout(int form, int64_t m, int64_t n, int64_t k, int slices,
+                           size_t offsets[2]) {
+    clear_error();
+    if (offsets == nullptr) return fail(-6, "magnitude_layout: offsets is NULL");
+    if (m < 0 || n < 0 || k < 0) return fail(-2, "magnitude_layout: negative size");
+    switch (form) {
+        case 1:
+            if (slices < 0 || slices > kMaxSlices) return fail(-5, "magnitude_layout: slices");
+            return sliced_magnitude_offsets(m, n, k, slices, offsets);
+        case 2: return crt_magnitude_offsets(m, n, k, false, offsets);
+        case 3: return crt_magnitude_offsets(n, n, k, true, offsets);
+        default: return fail(-1, "magnitude_layout: form must be 1, 2 or 3");
+    }
+}
+
 int mp_dd_Rpotrf(const char *uplo, int64_t n, mp_dd_mat A, int64_t lda, int64_t *info) {
     clear_error();
     int ul = uplo_flag(uplo);

@@ -1,10 +1,10 @@
 // Residue (CRT) form of the split-precision dd Rgemm on the fp16 tensor cores.
 //
-// The same exact integers as the sliced form -- X = RNE(hi 2^(112 - e)) +
-// RNE(lo 2^(112 - e)) for an entry x = hi + lo of a row of op(A) with scale
-// e (and likewise for the columns of op(B)), |X| <= 2^111 -- are multiplied
-// exactly through the Chinese remainder theorem instead of through digit
-// pairs:
+// The exact integers of the sliced form at a width of W = 8D bits --
+// X = RNE(hi 2^(W - e)) + RNE(lo 2^(W - e)) for an entry x = hi + lo of a row
+// of op(A) with scale e (and likewise for the columns of op(B)),
+// |X| < 2^(W-1) -- are multiplied exactly through the Chinese remainder
+// theorem instead of through digit pairs:
 //
 //  1. residues: r_i = X mod p_i in the symmetric range (|r_i| <= 128) for
 //     N pairwise coprime moduli p_i <= 256, stored as exact fp16 planes;
@@ -13,14 +13,17 @@
 //     stored reduced mod p_i (one byte);
 //  3. reconstruction: C' = sum_i c_i w_i mod P with P = prod p_i and the CRT
 //     weights w_i = (P/p_i) ((P/p_i)^-1 mod p_i), in multiword integer
-//     arithmetic, mapped to the symmetric range; since P > 2 k 2^222 >=
-//     2 |A' B'|, C' is exactly the integer product A'B'; it is rounded once
-//     to dd, scaled by 2^(e_i + f_j - 224), and alpha/beta are applied in dd.
+//     arithmetic, mapped to the symmetric range; since P >= k 2^(2W) >
+//     4 |A' B'|, C' is exactly the integer product A'B'; it is rounded once
+//     to dd, scaled by 2^(e_i + f_j - 2W), and alpha/beta are applied in dd.
 //
-// N is the smallest count with P > k 2^223 (32 moduli for k = 8192), against
-// S(S+1)/2 = 105 pair products of the 14-digit form, for the same rounding
-// of the operands; the only error is the rounding of A and B to 112 bits
-// (at most 2^(e_i + f_j - 112) per product).
+// The only error is the rounding of A and B to W bits: at most
+// (1 + 2^-W) 2^(e_i + f_j - W) per product.  Each call certifies it against
+// the accuracy bound before choosing W (ozaki_common.cuh): 112 bits (D = 14
+// digits, 32 moduli at k = 8192) when that suffices, else 120 or 128 bits
+// (more moduli), else the plain FP64 kernel computes the product.  N is the
+// smallest even count with P >= k 2^(2W), against S(S+1)/2 = 105 pair
+// products of the 14-digit sliced form at W = 112.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -35,7 +38,8 @@
 namespace mpdd {
 namespace {
 
-constexpr int kDigits = 14;          // X is formed as 14 base-256 digits (112 bits)
+constexpr int kMinDigits = 14;        // X has D base-256 digits, W = 8 D bits
+constexpr int kMaxDigits = 16;        // |X| < 2^127: a signed 128-bit integer
 constexpr int kMaxMod = 40;
 constexpr int kWords = 11;           // 32-bit words for sums below 2^352
 // pairwise coprime moduli <= 256, largest first: 2^8, 3*5*17, 11*23, 13*19
@@ -48,9 +52,10 @@ __host__ __device__ constexpr int modulus(int i) {
     return m[i];
 }
 
-// 256^(kDigits-1-t) mod p_i as exact floats (< 256), and 1/p_i.
+// 256^(kMaxDigits-1-u) mod p_i as exact floats (< 256), and 1/p_i.  Digit t
+// of a D-digit expansion has the weight w[i][kMaxDigits - D + t].
 struct ModWeights {
-    float w[kMaxMod][kDigits];
+    float w[kMaxMod][kMaxDigits];
     float inv[kMaxMod];
 };
 
@@ -59,7 +64,7 @@ constexpr ModWeights make_mod_weights() {
     for (int i = 0; i < kMaxMod; ++i) {
         const int p = modulus(i);
         int v = 1;
-        for (int t = kDigits - 1; t >= 0; --t) {
+        for (int t = kMaxDigits - 1; t >= 0; --t) {
             mw.w[i][t] = (float)v;
             v = (v * 256) % p;
         }
@@ -73,23 +78,24 @@ __constant__ ModWeights c_mod_weights = make_mod_weights();
 // 4 threads per (row, 16 consecutive k), 4 entries each, one 8-byte store
 // per residue plane and thread (a quad of lanes writes one 32-byte sector).
 // Residues from the balanced digits d_t of X on the FP32 pipe:
-// s = sum_t d_t (256^(13-t) mod p) is an integer below 14 * 128 * 255 < 2^24,
+// s = sum_t d_t (256^(D-1-t) mod p) is an integer below 16 * 128 * 255 < 2^24,
 // so every partial sum is exact in fp32, and r = s - p rint(s / p) is the
 // residue in [-(p-1)/2, (p-1)/2] for odd p: the fp32 quotient is within
 // |s / p| 2^-23 < 1e-3 of s / p, while s / p, an integer over an odd p, is
 // never within 1 / (2 p) > 0.0019 of a half-integer.  For p = 256 the
-// lowest digit, in [-128, 127], is the residue.
-template <int NP>
-__global__ void __launch_bounds__(128) residue_kernel(
+// lowest digit, in [-128, 127], is the residue.  The first N planes are
+// written (N and D from the call's certificate).
+template <int NP, int DG>
+__device__ __forceinline__ void residue_body(
     const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
-    const unsigned long long *__restrict__ rmax, __half *__restrict__ R) {
+    const unsigned long long *__restrict__ rmax, __half *__restrict__ R, int N) {
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 4) + threadIdx.x / 4;
     if (r >= rows_pad) return;
     const int64_t l0 = (int64_t)blockIdx.y * 16 + 4 * (threadIdx.x & 3);
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
-    const int shift = 8 * kDigits - e;
-    float df[4][kDigits];
+    const int shift = 8 * DG - e;
+    float df[4][DG];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int64_t l = l0 + q;
@@ -99,31 +105,33 @@ __global__ void __launch_bounds__(128) residue_kernel(
             hi = Xh[off];
             lo = Xl[off];
         }
-        int dg[kDigits];
-        dd_digits<kDigits>(hi, lo, shift, dg);
+        int dg[DG];
+        dd_digits<DG>(hi, lo, shift, dg);
         // d as a float without a conversion instruction: the bits of 2^23 + 128 + d
         // (exact, d in [-128, 128]) minus 2^23 + 128
 #pragma unroll
-        for (int t = 0; t < kDigits; ++t)
+        for (int t = 0; t < DG; ++t)
             df[q][t] = __fsub_rn(__int_as_float(0x4B000000 + 128 + dg[t]), 8388736.0f);
     }
     // plane 0 (p = 256): the lowest digits; two fp16 per conversion
     {
-        const __half2 h01 = __floats2half2_rn(df[0][kDigits - 1], df[1][kDigits - 1]);
-        const __half2 h23 = __floats2half2_rn(df[2][kDigits - 1], df[3][kDigits - 1]);
+        const __half2 h01 = __floats2half2_rn(df[0][DG - 1], df[1][DG - 1]);
+        const __half2 h23 = __floats2half2_rn(df[2][DG - 1], df[3][DG - 1]);
         *reinterpret_cast<uint2 *>(R + r * k_pad + l0) =
             make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
                        *reinterpret_cast<const uint32_t *>(&h23));
     }
 #pragma unroll
     for (int i = 1; i < 2 * NP; ++i) {
+        if (i >= N) break;
         const float p = (float)modulus(i), inv = c_mod_weights.inv[i];
         float res[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float s = 0.0f;
 #pragma unroll
-            for (int t = 0; t < kDigits; ++t) s = __fmaf_rn(df[q][t], c_mod_weights.w[i][t], s);
+            for (int t = 0; t < DG; ++t)
+                s = __fmaf_rn(df[q][t], c_mod_weights.w[i][kMaxDigits - DG + t], s);
             // rint(s / p) by the 1.5 2^23 shift (|s / p| < 2^22), then the residue
             const float qn = __fsub_rn(__fmaf_rn(s, inv, 12582912.0f), 12582912.0f);
             res[q] = __fmaf_rn(-p, qn, s);
@@ -136,10 +144,39 @@ __global__ void __launch_bounds__(128) residue_kernel(
     }
 }
 
+template <int NP>
+__global__ void __launch_bounds__(128) residue_kernel(
+    const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
+    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+    const unsigned long long *__restrict__ rmax, __half *__restrict__ R, const SplitPlan plan) {
+    const PlanPick pk = plan_choice(plan);
+    if (pk.c < 0) return;
+    const int N = pk.count;
+    switch (pk.width) {
+        case 8 * 14:
+            residue_body<NP, 14>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            break;
+        case 8 * 15:
+            residue_body<NP, 15>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            break;
+        default:
+            residue_body<NP, 16>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            break;
+    }
+}
+
 // ------------------------------------------------------------------ CRT
 
+// Reconstruction constants of one moduli count N.
+struct CrtTables {
+    uint32_t P[kWords];                   // product of the moduli
+    uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
+    float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
+};
+
 struct CrtArgs {
-    int N;
+    SplitPlan plan;                       // N and W of the call (tab[c] for candidate c)
+    CrtTables tab[kMaxCand];
     int64_t m, n, m_pad, n_pad;
     const uint8_t *res;                   // [N][n_pad][m_pad] products mod p_i
     const unsigned long long *rmax, *cmax;
@@ -147,10 +184,6 @@ struct CrtArgs {
     int alpha_one, beta_zero;
     double *ch, *cl;
     int64_t ldc;
-    int moduli[kMaxMod];
-    uint32_t P[kWords];                   // product of the moduli
-    uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
-    float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
     int tri;                              // 0: all of C; 1 / 2: upper / lower triangle
     const int64_t *info;                  // optional: non-zero -> leave C as is
 };
@@ -266,6 +299,9 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale
 template <int NW>
 __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
     if (p.info != nullptr && *p.info != 0) return;   // an earlier step failed
+    const PlanPick pk = plan_choice(p.plan);
+    if (pk.c < 0) return;                            // the plain kernel computes C
+    const int c = pk.c, N = pk.count, W = pk.width;
     const int64_t total = p.m * p.n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -280,22 +316,22 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
 #pragma unroll
         for (int t = 0; t < NW; ++t) acc[t] = 0;
         float qf = 0.0f;
-        for (int b0 = 0; b0 < p.N; b0 += 8) {
+        for (int b0 = 0; b0 < N; b0 += 8) {
             uint32_t cv[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) cv[u] = b0 + u < p.N ? res[(b0 + u) * plane] : 0u;
+            for (int u = 0; u < 8; ++u) cv[u] = b0 + u < N ? res[(b0 + u) * plane] : 0u;
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int b = b0 + u < p.N ? b0 + u : 0;   // cv[u] = 0 past N
+                const int b = b0 + u < N ? b0 + u : 0;   // cv[u] = 0 past N
 #pragma unroll
-                for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * p.w[b][t];
-                qf = __fmaf_rn((float)cv[u], p.frac[b], qf);
+                for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * p.tab[c].w[b][t];
+                qf = __fmaf_rn((float)cv[u], p.tab[c].frac[b], qf);
             }
         }
         // The symmetric representative is Z = S - q P with q the integer
-        // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| <= k 2^222 < P / 4,
-        // and the fp32 sum of the 32 fractions (each term below 256, the sum
-        // below 8192) is off by less than 0.02, so rounding it gives q.
+        // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| < k 2^(2W-2) <= P / 4,
+        // and the fp32 sum of the N <= 40 fractions (each term below 256, the
+        // sum below 10240) is off by less than 0.03, so rounding it gives q.
         const uint64_t q = (uint64_t)(int64_t)rintf(qf);
         // Z = S - q P in two's complement over NW words (exact: |Z| < 2^(32 NW - 1))
         uint32_t S[NW];
@@ -305,7 +341,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
             for (int t = 0; t < NW; ++t) {
                 const uint64_t v = acc[t] + carry;
                 carry = v >> 32;
-                const uint64_t prod = q * p.P[t] + mc;
+                const uint64_t prod = q * p.tab[c].P[t] + mc;
                 mc = prod >> 32;
                 const uint64_t d = (uint64_t)(uint32_t)v - (uint32_t)prod - borrow;
                 S[t] = (uint32_t)d;
@@ -323,7 +359,7 @@ __global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
                 c2 = v >> 32;
             }
         }
-        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * 8 * kDigits;
+        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * W;
         uint32_t rem[NW], rem2[NW];
         bool rem_neg, unused;
         double vh = round_words(S, sc, rem, rem_neg);
@@ -396,21 +432,38 @@ uint32_t inv_mod(uint32_t a, uint32_t p) {   // a^-1 mod p (gcd(a, p) = 1)
     return (uint32_t)t;
 }
 
-// Smallest moduli count with P > k 2^223 (= 2 max |A' B'|, |A'|, |B'| <= 2^111).
-int moduli_count(int64_t k) {
-    const int need = 223 + (int)std::ceil(std::log2((double)(k > 1 ? k : 1))) + 1;
+// Smallest even moduli count with P >= k 2^(2W) > 4 max |A' B'| (|A'|,
+// |B'| < 2^(W-1)); -1 when the 40 moduli do not reach it.
+int moduli_count(int64_t k, int W) {
+    const int need = 2 * W + (int)std::ceil(std::log2((double)(k > 1 ? k : 1)));
     Big P{1};
     for (int N = 1; N <= kMaxMod; ++N) {
         P = big_mul_small(P, modulus(N - 1));
-        if (big_bits(P) > need) return N % 2 ? N + 1 : N;   // residues come in pairs
+        if (big_bits(P) > need) {                        // P >= 2^need
+            const int even = N % 2 ? N + 1 : N;          // residues come in pairs
+            return even <= kMaxMod ? even : -1;
+        }
     }
     return -1;
 }
 
+// Candidate widths of a call: 112, 120 and 128 bits, with their moduli counts.
+int crt_candidates(int64_t k, int *widths, int *counts) {
+    int nc = 0;
+    for (int D = kMinDigits; D <= kMaxDigits; ++D) {
+        const int N = moduli_count(k, 8 * D);
+        if (N < 0) break;
+        widths[nc] = 8 * D;
+        counts[nc] = N;
+        ++nc;
+    }
+    return nc;
+}
+
 struct CrtLayout {
-    int N;
+    int N;                                 // moduli the workspace holds (the widest candidate)
     int64_t m_pad, n_pad, k_pad;
-    size_t off_rowmax, off_colmax, off_ra, off_rb, off_res, total;
+    size_t off_rowmax, off_colmax, off_ra, off_rb, off_res, off_ma, off_mb, total;
 };
 
 size_t align1k(size_t x) { return (x + 1023) / 1024 * 1024; }
@@ -429,7 +482,9 @@ int crt_band_tn(int64_t m, int64_t n, int N) {
 // residue planes serves both operands, padded alike (m_pad = n_pad).
 CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
     CrtLayout L{};
-    L.N = moduli_count(k);
+    int widths[kMaxCand], counts[kMaxCand];
+    const int nc = crt_candidates(k, widths, counts);
+    L.N = nc > 0 ? counts[nc - 1] : -1;
     const int TN = crt_band_tn(m, n, L.N);
     L.n_pad = ceil_div(imax(n, 1), TN) * TN;
     L.m_pad = sym ? L.n_pad : ceil_div(imax(m, 1), kBandTM) * kBandTM;
@@ -443,6 +498,9 @@ CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
     L.off_rb = sym ? L.off_ra : o;
     if (!sym) o = align1k(o + 2 * N * L.n_pad * L.k_pad);
     L.off_res = o; o = align1k(o + N * L.n_pad * L.m_pad);
+    L.off_ma = o; o = align1k(o + 2 * (size_t)L.m_pad * L.k_pad);
+    L.off_mb = sym ? L.off_ma : o;
+    if (!sym) o = align1k(o + 2 * (size_t)L.n_pad * L.k_pad);
     L.total = o;
     return L;
 }
@@ -450,25 +508,50 @@ CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
 template <int NP>
 void launch_residues_np(const double *Xh, const double *Xl, int64_t ld, int rc, int64_t rows,
                         int64_t k, int64_t rows_pad, int64_t k_pad,
-                        const unsigned long long *rmax, __half *R, cudaStream_t st) {
+                        const unsigned long long *rmax, __half *R, const SplitPlan &plan,
+                        cudaStream_t st) {
     dim3 grid((unsigned)ceil_div(rows_pad, 32), (unsigned)(k_pad / 16));
-    residue_kernel<NP><<<grid, 128, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R);
+    residue_kernel<NP><<<grid, 128, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R,
+                                             plan);
 }
 
-int launch_residues(int N, const double *Xh, const double *Xl, int64_t ld, int rc,
+// Residues for up to Nmax moduli (the plan's widest candidate).
+int launch_residues(int Nmax, const double *Xh, const double *Xl, int64_t ld, int rc,
                     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
-                    const unsigned long long *rmax, __half *R, cudaStream_t st) {
+                    const unsigned long long *rmax, __half *R, const SplitPlan &plan,
+                    cudaStream_t st) {
     if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for residues");
-    switch (N / 2) {
-#define MPDD_RES_CASE(NP) \
-    case NP: launch_residues_np<NP>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R, st); break;
+    switch (Nmax / 2) {
+#define MPDD_RES_CASE(NP)                                                                 \
+    case NP:                                                                              \
+        launch_residues_np<NP>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R, plan, st); \
+        break;
         MPDD_RES_CASE(14) MPDD_RES_CASE(15) MPDD_RES_CASE(16) MPDD_RES_CASE(17)
         MPDD_RES_CASE(18) MPDD_RES_CASE(19) MPDD_RES_CASE(20)
 #undef MPDD_RES_CASE
         default:
-            return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [28, 40]", N);
+            return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [28, 40]", Nmax);
     }
     return check_launch("residue_kernel");
+}
+
+// Reconstruction constants for the first N moduli.
+int crt_tables(int N, CrtTables &T, int *nwords) {
+    Big P{1};
+    for (int i = 0; i < N; ++i) P = big_mul_small(P, modulus(i));
+    if ((int)P.size() > kWords - 1) return fail(MP_DD_ERR_TOO_LARGE, "moduli product too wide");
+    for (int t = 0; t < kWords; ++t) T.P[t] = t < (int)P.size() ? P[t] : 0;
+    for (int i = 0; i < N; ++i) {
+        uint32_t mi_mod = 0;
+        Big Mi = big_div_small(P, modulus(i), nullptr);
+        big_div_small(Mi, modulus(i), &mi_mod);
+        const uint32_t inv = inv_mod(mi_mod, modulus(i));
+        Big wi = big_mul_small(Mi, inv);
+        for (int t = 0; t < kWords; ++t) T.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
+        T.frac[i] = (float)((double)inv / (double)modulus(i));
+    }
+    *nwords = (int)P.size() + 1;
+    return 0;
 }
 
 }  // namespace
@@ -492,6 +575,13 @@ int crt_layout_query(int64_t m, int64_t n, int64_t k, size_t *off, int *count) {
     return 0;
 }
 
+int crt_magnitude_offsets(int64_t m, int64_t n, int64_t k, bool sym, size_t *off) {
+    CrtLayout L = crt_layout(m, n, k, sym);
+    off[0] = L.off_ma;
+    off[1] = L.off_mb;
+    return 0;
+}
+
 int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (p.k > ((int64_t)1 << 17) - 1)
         return fail(MP_DD_ERR_TOO_LARGE, "k = %lld exceeds 131071 (int32 products)",
@@ -501,34 +591,53 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (sym && (p.m != p.n || p.ah != p.bh || p.al != p.bl || p.lda != p.ldb || p.ta == p.tb))
         return fail(MP_DD_ERR_TOO_LARGE, "CRT Rsyrk: operands are not A and A^T");
     CrtLayout L = crt_layout(p.m, p.n, p.k, sym);
-    if (L.N < 0 || L.N > kMaxMod) return fail(MP_DD_ERR_TOO_LARGE, "k too large for the moduli");
+    int widths[kMaxCand], counts[kMaxCand];
+    const int ncand = crt_candidates(p.k, widths, counts);
+    if (ncand < 1 || L.N < 0 || L.N > kMaxMod)
+        return fail(MP_DD_ERR_TOO_LARGE, "k too large for the moduli");
     if (ws == nullptr || ws_bytes < L.total)
         return fail(MP_DD_ERR_WORKSPACE, "CRT Rgemm needs %zu workspace bytes, got %zu",
                     L.total, ws_bytes);
     if ((int64_t)L.N * L.m_pad > 0x7fffffffLL || (int64_t)L.N * L.n_pad > 0x7fffffffLL)
         return fail(MP_DD_ERR_TOO_LARGE, "matrix too large for the CRT path");
-    if (p.alpha_zero) return launch_gemm_plain(p, st);
     const int TN = crt_band_tn(p.m, p.n, L.N);
 
     uint8_t *w = static_cast<uint8_t *>(ws);
-    cudaError_t e = cudaMemsetAsync(w, 0, L.off_ra, st);
+    cudaError_t e = cudaMemsetAsync(w, 0, L.off_ra, st);   // header (form 0) and maxima
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p.alpha_zero) return launch_gemm_plain(p, st);
     auto *rmax = reinterpret_cast<unsigned long long *>(w + L.off_rowmax);
     auto *cmax = reinterpret_cast<unsigned long long *>(w + L.off_colmax);
     auto *RA = reinterpret_cast<__half *>(w + L.off_ra);
     auto *RB = reinterpret_cast<__half *>(w + L.off_rb);
     auto *RES = reinterpret_cast<uint8_t *>(w + L.off_res);
+    auto *hdr = reinterpret_cast<SplitHeader *>(w);
+
+    double cst[kMaxCand];
+    for (int c = 0; c < ncand; ++c) cst[c] = 1.0 + 0x1p-50;   // (1 + 2^-W), rounded up
+    SplitHeader init;
+    const SplitPlan plan = make_plan(&init, &hdr->dmin, 2, p.k, ncand, widths, counts, cst);
+
     const int a_rc = p.ta ? 0 : 1, b_rc = p.tb ? 1 : 0;
     int rc;
     sliced_timing_mark(0, st);
     if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
+    if (!sym && (rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
+    if ((rc = launch_magnitude(p.ah, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
+                               w + L.off_ma, hdr, &init, st)))
+        return rc;
+    if (!sym && (rc = launch_magnitude(p.bh, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax,
+                                       w + L.off_mb, hdr, nullptr, st)))
+        return rc;
+    if ((rc = launch_certificate(p, w + L.off_ma, w + L.off_mb, L.m_pad, L.n_pad, L.k_pad, TN,
+                                 rmax, cmax, hdr, st)))
+        return rc;
     if ((rc = launch_residues(L.N, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
-                              RA, st)))
+                              RA, plan, st)))
         return rc;
     if (!sym) {   // (the Rsyrk form reuses the maxima and planes of op(A))
-        if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
         if ((rc = launch_residues(L.N, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad,
-                                  cmax, RB, st)))
+                                  cmax, RB, plan, st)))
             return rc;
     }
 
@@ -545,48 +654,39 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ba.n_pad = L.n_pad;
     ba.P = nullptr;
     ba.R = RES;
-    ba.status = reinterpret_cast<int *>(w);
+    ba.status = &hdr->status;
     ba.diag = 1;
     ba.tri = p.tri;
+    ba.plan = plan;
     for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
     if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
     sliced_timing_mark(2, st);
 
-    // CRT constants
+    // CRT constants of every candidate
     CrtArgs ca{};
-    ca.N = L.N;
+    ca.plan = plan;
     ca.m = p.m; ca.n = p.n; ca.m_pad = L.m_pad; ca.n_pad = L.n_pad;
-    ca.res = RES; ca.rmax = rmax; ca.cmax = cmax;
+    ca.res = RES; ca.rmax = rmax; ca.cmax = sym ? rmax : cmax;
     ca.alpha = p.alpha; ca.beta = p.beta;
     ca.alpha_one = p.alpha_one; ca.beta_zero = p.beta_zero;
     ca.ch = p.ch; ca.cl = p.cl; ca.ldc = p.ldc;
     ca.tri = p.tri;
     ca.info = p.info;
-    Big P{1};
-    for (int i = 0; i < L.N; ++i) {
-        ca.moduli[i] = modulus(i);
-        P = big_mul_small(P, modulus(i));
-    }
-    if ((int)P.size() > kWords - 1) return fail(MP_DD_ERR_TOO_LARGE, "moduli product too wide");
-    for (int t = 0; t < kWords; ++t) ca.P[t] = t < (int)P.size() ? P[t] : 0;
-    for (int i = 0; i < L.N; ++i) {
-        uint32_t mi_mod = 0;
-        Big Mi = big_div_small(P, modulus(i), nullptr);
-        big_div_small(Mi, modulus(i), &mi_mod);
-        const uint32_t inv = inv_mod(mi_mod, modulus(i));
-        Big wi = big_mul_small(Mi, inv);
-        for (int t = 0; t < kWords; ++t) ca.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
-        ca.frac[i] = (float)((double)inv / (double)modulus(i));
+    int nw = 0;
+    for (int c = 0; c < ncand; ++c) {
+        int nwc = 0;
+        if ((rc = crt_tables(counts[c], ca.tab[c], &nwc))) return rc;
+        nw = nwc > nw ? nwc : nw;
     }
     const int64_t total = p.m * p.n;
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
-    const int nw = (int)P.size() + 1;
     if (nw <= 8) crt_kernel<8><<<(unsigned)blocks, 256, 0, st>>>(ca);
     else if (nw == 9) crt_kernel<9><<<(unsigned)blocks, 256, 0, st>>>(ca);
     else if (nw == 10) crt_kernel<10><<<(unsigned)blocks, 256, 0, st>>>(ca);
     else crt_kernel<11><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    rc = check_launch("crt_kernel");
+    if ((rc = check_launch("crt_kernel"))) return rc;
+    rc = launch_plain_fallback(p, plan, st);
     sliced_timing_mark(3, st);
     return rc;
 }

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "dd_arith.cuh"
 #include "kernels.cuh"
+#include "ozaki_common.cuh"
 
 namespace mpdd {
 namespace {
@@ -79,6 +80,10 @@ template <int TA, int TB, int R>
 __device__ __forceinline__ void plain_body(const GemmArgs &p, PlainSmem<R> &s) {
     constexpr int BM = 16 * R, BN = 16 * R;
     if (p.info != nullptr && *p.info != 0) return;  // an earlier step failed
+    // behind a split-precision call: compute only when its certificate failed
+    if (p.gate != nullptr &&
+        *reinterpret_cast<const volatile unsigned long long *>(p.gate) >= p.gate_below)
+        return;
     int64_t bi, bj;
     tile_coords<BM, BN>(p, bi, bj);
     const int t = threadIdx.x, tx = t % 16, ty = t / 16;
@@ -258,6 +263,16 @@ int plain_tile_r(const GemmArgs &p) {
         if (best_t < 0 || t < best_t) { best_t = t; best = r; }
     }
     return best;
+}
+
+// The plain kernel behind a split-precision call: the same launch, gated on
+// the call's certificate (every CTA returns at once when a width certified
+// the bound).
+int launch_plain_fallback(const GemmArgs &p, const SplitPlan &plan, cudaStream_t stream) {
+    GemmArgs q = p;
+    q.gate = plan.dmin;
+    q.gate_below = plan.thr[plan.ncand - 1];
+    return launch_gemm_plain(q, stream);
 }
 
 int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream) {

@@ -22,16 +22,23 @@
 //     2^(e_i + f_j - 8S - 8); the alpha/beta epilogue is dd arithmetic.
 //
 // Error: per product |a b - sum_{t+u<S} d_t d'_u 256^-(t+u+2) 2^(e_i+f_j)|
-// <= ~4.3 2^(e_i + f_j - 8S); with S = 14 and entries whose row/column
-// maxima are within a few binades of the entries themselves this is a
-// small fraction of the bound 4 k 2^-104 (|alpha||A||B| + |beta||C|).
+// <= C_S 2^(e_i + f_j - 8S) with C_S = 1 + (S - 1) / (4 (1 - 2^-8)) (one unit
+// of operand rounding per factor, and the dropped pairs t + u >= S).  Before
+// slicing, every call certifies this against the bound
+// 4 k 2^-104 (|alpha||A||B| + |beta||C|) entry by entry (ozaki_common.cuh):
+// a bf16 tensor-core product of the magnitude planes gives a lower bound of
+// |A||B|, the smallest margin picks S (14 or 15 when the caller passes 0,
+// else the caller's S), and when no S certifies the bound the plain FP64
+// kernel computes C instead.
 //
 // Only the scaling epilogue uses the FP64 pipe (about 30 instructions per
 // output entry); slicing and recombination are integer arithmetic, and the
 // O(mnk) work runs on the tensor cores.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -79,7 +86,7 @@ namespace {
 
 struct Layout {
     int64_t m, n, k, S, m_pad, n_pad, k_pad;
-    size_t off_rowmax, off_colmax, off_da, off_db, off_p, total;
+    size_t off_rowmax, off_colmax, off_da, off_db, off_p, off_ma, off_mb, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -97,9 +104,31 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int S) {
     L.off_da = o; o = align_up(o + 2 * (size_t)S * L.m_pad * L.k_pad, 1024);
     L.off_db = o; o = align_up(o + 2 * (size_t)S * L.n_pad * L.k_pad, 1024);
     L.off_p = o; o = align_up(o + 4 * (size_t)S * L.n_pad * L.m_pad, 1024);
+    L.off_ma = o; o = align_up(o + 2 * (size_t)L.m_pad * L.k_pad, 1024);
+    L.off_mb = o; o = align_up(o + 2 * (size_t)L.n_pad * L.k_pad, 1024);
     L.total = o;
     return L;
 }
+
+// Candidate slice counts of a call: the caller's S, or (slices = 0) 14 and,
+// when k 15 stays within the int32 band sums, 15.
+int slice_candidates(int slices, int64_t k, int *cand) {
+    if (slices != 0) {
+        cand[0] = slices;
+        return 1;
+    }
+    cand[0] = kDefaultSlices;
+    if ((int64_t)(kDefaultSlices + 1) * k <= ((int64_t)1 << 17) - 1 &&
+        kDefaultSlices + 1 <= kMaxSlices) {
+        cand[1] = kDefaultSlices + 1;
+        return 2;
+    }
+    return 1;
+}
+
+// Per-product error constant of S digit slices: one unit of operand
+// rounding plus the dropped pairs, sum_{h >= 0} (S - 1 - h) 2^-2 2^-8h.
+double slice_constant(int S) { return 1.0 + 0x1p-50 + (S - 1) / (4.0 * (1.0 - 0x1p-8)); }
 
 // ------------------------------------------------------------------ step 1
 
@@ -167,18 +196,66 @@ __device__ __forceinline__ void slice8(const double *__restrict__ Xh,
 // i of the block and k halves l0 .. l0+7 and l0+8 .. l0+15, so every 32-byte
 // sector of a digit plane is written whole by one store instruction, and the
 // row_contig reads of 16 consecutive rows per k column coalesce.
-template <int S>
+// The slice count comes from the call's certificate (plan): SA or SB digits
+// (SA == SB for a caller-chosen S); no certified S: nothing to slice.
+template <int SA, int SB>
 __global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ Xh,
                                                     const double *__restrict__ Xl, int64_t ld,
                                                     int row_contig, int64_t rows, int64_t k,
                                                     int64_t rows_pad, int64_t k_pad,
                                                     const unsigned long long *__restrict__ rmax,
-                                                    __half *__restrict__ D) {
+                                                    __half *__restrict__ D, const SplitPlan plan) {
+    const PlanPick pk = plan_choice(plan);
+    if (pk.c < 0) return;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 2) + threadIdx.x / 2;
     if (r >= rows_pad) return;
     const int64_t l0 = (int64_t)blockIdx.y * 16 + 8 * (threadIdx.x & 1);
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
-    slice8<S>(Xh, Xl, ld, row_contig, r, rows, l0, k, 8 * S - e, D, rows_pad, k_pad);
+    if (SA == SB || pk.count == SA)
+        slice8<SA>(Xh, Xl, ld, row_contig, r, rows, l0, k, 8 * SA - e, D, rows_pad, k_pad);
+    else
+        slice8<SB>(Xh, Xl, ld, row_contig, r, rows, l0, k, 8 * SB - e, D, rows_pad, k_pad);
+}
+
+// x 2^s for x >= 0, exact while the result is normal; in two steps so that
+// every power of two is a normal binary64.  rd: round toward zero when the
+// result leaves the normal range (a lower bound, as the certificate needs).
+__device__ __forceinline__ double pow2_step(int s) {
+    return __longlong_as_double((long long)(s + 1023) << 52);   // -1022 <= s <= 1023
+}
+__device__ __forceinline__ double scale2_rd(double x, int s) {
+    const int s1 = s / 2, s2 = s - s1;
+    return __dmul_rd(__dmul_rd(x, pow2_step(s1)), pow2_step(s2));
+}
+
+// Magnitude planes of the certificate: M[r][l] = the largest bf16 not above
+// |hi_rl| 2^-e_r (zero in the padding), K-major like the digit planes.  Two
+// threads per (row, 16 consecutive k), eight entries and one 16-byte store
+// each.  Block (0, 0) of the launch given `hdr` first writes the call's
+// header image (plan, dmin = +inf); the magnitude product runs after it.
+__global__ void __launch_bounds__(128) magnitude_kernel(
+    const double *__restrict__ Xh, int64_t ld, int row_contig, int64_t rows, int64_t k,
+    int64_t rows_pad, int64_t k_pad, const unsigned long long *__restrict__ rmax,
+    __nv_bfloat16 *__restrict__ M, SplitHeader *hdr, const SplitHeader init) {
+    if (hdr != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *hdr = init;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x / 2) + threadIdx.x / 2;
+    if (r >= rows_pad) return;
+    const int64_t l0 = (int64_t)blockIdx.y * 16 + 8 * (threadIdx.x & 1);
+    const int e = r < rows ? scale_exponent(rmax[r]) : 0;
+    __nv_bfloat16 out[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int64_t l = l0 + q;
+        double v = 0.0;
+        if (r < rows && l < k)
+            v = fabs(Xh[row_contig ? (r + l * ld) : (l + r * ld)]);
+        // |hi| 2^-e < 1/2: exact unless subnormal, where it rounds toward zero;
+        // then two roundings toward zero to fp32 and to bf16
+        out[q] = __float2bfloat16_rz(__double2float_rz(scale2_rd(v, -e)));
+    }
+    uint4 w;
+    memcpy(&w, out, 16);
+    *reinterpret_cast<uint4 *>(M + r * k_pad + l0) = w;
 }
 
 // ------------------------------------------------------------------ step 3
@@ -203,11 +280,11 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
 // Tiles entirely outside the requested triangle (Rsyrk form) get an empty
 // band range, so every role skips them alike.
 template <int TN>
-__device__ __forceinline__ void item_coords(const BandArgs &p, int item, int num_tiles, int &tm,
-                                            int &tn, int &b0, int &b1) {
+__device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, int num_tiles,
+                                            int &tm, int &tn, int &b0, int &b1) {
     int tile = item;
     b0 = 0;
-    b1 = p.S;
+    b1 = S;
     if (p.diag) {
         b0 = item / num_tiles;
         b1 = b0 + 1;
@@ -218,10 +295,64 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int item, int num
     if ((p.tri == 1 && r0 > c0 + TN - 1) || (p.tri == 2 && r0 + TM - 1 < c0)) b1 = b0;
 }
 
-template <int TN>
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+// Certificate margin of the entries (i, j0 .. j0 + kEpiCols - 1) from their
+// fp32 magnitude sums s_ij (bit patterns in acc):
+//   d_ij = s_ij c1 + r |c_ij| 2^-(e_i + f_j),  r <= |beta / alpha|,
+// each step rounded toward zero, so d_ij is at most the exact margin of a
+// lower bound of (|A||B|)_ij.  Rows or columns that are all zero (exact in
+// every form), entries outside C or the requested triangle, and NaN margins
+// (a NaN in C, whose result is NaN anyway) do not constrain.  The minimum
+// over the warp goes to *dmin_out with one atomic.
+__device__ __forceinline__ void certificate_margin(const BandArgs &p,
+                                                   const int32_t (&acc)[kEpiCols], int64_t i,
+                                                   int64_t j0) {
+    unsigned long long dm = kInfBits;
+    if (i < p.m) {
+        const unsigned long long rm = p.rmax[i];
+        const int ei = scale_exponent(rm);
+#pragma unroll
+        for (int jj = 0; jj < kEpiCols; ++jj) {
+            const int64_t j = j0 + jj;
+            const bool inside = rm != 0 && j < p.n && !(p.tri == 1 && i > j) &&
+                                !(p.tri == 2 && i < j);
+            if (!inside) continue;
+            const unsigned long long cm = p.cmax[j];
+            if (cm == 0) continue;
+            double d = __dmul_rd((double)__int_as_float(acc[jj]), p.c1);
+            if (p.ba_ratio > 0.0) {
+                const double t = __dmul_rd(fabs(p.ch[i + j * p.ldc]), p.ba_ratio);
+                d = __dadd_rd(d, scale2_rd(t, -(ei + scale_exponent(cm))));
+            }
+            const unsigned long long db = (unsigned long long)__double_as_longlong(d);
+            if (d >= 0.0 && db < dm) dm = db;
+        }
+    }
+    const unsigned mask = __activemask();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(mask, dm, o);
+        dm = v < dm ? v : dm;
+    }
+    if ((threadIdx.x & 31) == 0 && dm != kInfBits) atomicMin(p.dmin_out, dm);
+}
+
+// MAG: the certificate's magnitude product (bf16 operands, fp32 sums, the
+// margin d_ij of every entry reduced to its minimum); otherwise the integer
+// band products with the band count taken from the call's plan.
+template <int TN, bool MAG>
 __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const BandArgs p) {
+    int S = p.S;
+    if (!MAG && p.plan.dmin != nullptr) {
+        // the same decision in every thread of every CTA: a word written by
+        // an earlier launch of this call
+        const PlanPick pk = plan_choice(p.plan);
+        if (pk.c < 0) return;
+        S = pk.count;
+    }
     using Cfg = BandCfg<TN>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr uint32_t kStageBytes = Cfg::STAGE_BYTES;
@@ -264,7 +395,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
 
     const int num_tiles = p.tiles_m * p.tiles_n;
     const int KB = p.kb_count;
-    const int num_items = p.diag ? num_tiles * p.S : num_tiles;
+    const int num_items = p.diag ? num_tiles * S : num_tiles;
 
     if (warp == 0) {
         // ---------------- TMA producer
@@ -275,7 +406,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             bool ok = true;
             for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
                 int tm, tn, b0, b1;
-                item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b)
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
@@ -308,12 +439,12 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16_f32(TM, TN);
+            const uint32_t idesc = MAG ? idesc_bf16_f32(TM, TN) : idesc_f16_f32(TM, TN);
             uint32_t it = 0, chunk = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
                 int tm, tn, b0, b1;
-                item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b) {
                     const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
@@ -369,7 +500,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         bool ok = true;
         for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
             int tm, tn, b0, b1;
-            item_coords<TN>(p, item, num_tiles, tm, tn, b0, b1);
+            item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
             for (int b = b0; b < b1 && ok; ++b) {
                 int32_t acc[kEpiCols];
 #pragma unroll
@@ -389,13 +520,24 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                         tmem_ld_32x32b_x16(tmem + lane_base + buf * TN + col0 + cc * 16, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            acc[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                        for (int j = 0; j < 16; ++j) {
+                            if (MAG)   // fp32 sums of non-negative products
+                                acc[cc * 16 + j] = __float_as_int(
+                                    __fadd_rn(__int_as_float(acc[cc * 16 + j]),
+                                              __uint_as_float(r[j])));
+                            else
+                                acc[cc * 16 + j] += __float2int_rn(__uint_as_float(r[j]));
+                        }
                     }
                     tc_fence_before();
                     mbar_arrive(&acce[buf]);
                 }
                 if (!ok) break;
+                if (MAG) {
+                    certificate_margin(p, acc, (int64_t)tm * TM + row,
+                                       (int64_t)tn * TN + col0);
+                    continue;
+                }
                 const int64_t off = ((int64_t)b * p.n_pad + (int64_t)tn * TN + col0) * p.m_pad +
                                     (int64_t)tm * TM + row;
                 if (p.diag) {
@@ -425,7 +567,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
 // ------------------------------------------------------------------ step 4
 
 struct RecArgs {
-    int S;
+    SplitPlan plan;   // the slice count (no certified count: nothing to do)
     int64_t m, n, m_pad, n_pad;
     const int32_t *P;
     const unsigned long long *rmax, *cmax;
@@ -471,6 +613,9 @@ __device__ __forceinline__ double i128_to_double(__int128 v) {
 }
 
 __global__ void __launch_bounds__(256) recombine_kernel(const RecArgs p) {
+    const PlanPick pk = plan_choice(p.plan);
+    if (pk.c < 0) return;
+    const int S = pk.count;
     const int64_t total = p.m * p.n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -478,7 +623,7 @@ __global__ void __launch_bounds__(256) recombine_kernel(const RecArgs p) {
         // V = sum_b P_b 256^(S-1-b) in 192-bit two's complement (hi:lo)
         unsigned __int128 lo = 0;
         long long hi = 0;
-        for (int b = 0; b < p.S; ++b) {
+        for (int b = 0; b < S; ++b) {
             const int32_t v = p.P[((int64_t)b * p.n_pad + j) * p.m_pad + i];
             hi = (long long)(((unsigned long long)hi << 8) | (unsigned long long)(lo >> 120));
             lo <<= 8;
@@ -499,7 +644,7 @@ __global__ void __launch_bounds__(256) recombine_kernel(const RecArgs p) {
         if (w2) pbit = 128 + msb64(w2);
         else if (w1) pbit = 64 + msb64(w1);
         else if (w0) pbit = msb64(w0);
-        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 8 * p.S - 8;
+        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 8 * S - 8;
         if (pbit >= 0 && pbit <= 52) {
             vh = mul_pow2(__ull2double_rn(w0), sc);
         } else if (pbit > 52) {
@@ -555,15 +700,17 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-// Tensor map of a [rows][k_pad] fp16 digit array, box 64 (k) x box_rows.
-int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows) {
+// Tensor map of a [rows][k_pad] fp16 (elem 0) or bf16 (elem 1) array, box
+// 64 (k) x box_rows.
+int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows, int elem) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(MP_DD_ERR_NO_DEVICE, "cuTensorMapEncodeTiled unavailable");
     cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
     cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
+    CUresult r = fn(m, elem ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                    2, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
@@ -583,30 +730,41 @@ int launch_absmax(const double *X, int64_t ld, int row_contig, int64_t rows, int
 
 namespace {
 
-template <int S>
+template <int SA, int SB>
 void launch_slice_s(const double *Xh, const double *Xl, int64_t ld, int row_contig,
                     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
-                    const unsigned long long *rmax, __half *D, cudaStream_t st) {
+                    const unsigned long long *rmax, __half *D, const SplitPlan &plan,
+                    cudaStream_t st) {
     dim3 grid((unsigned)ceil_div(rows_pad, 64), (unsigned)(k_pad / 16));
-    slice_kernel<S><<<grid, 128, 0, st>>>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad,
-                                          rmax, D);
+    slice_kernel<SA, SB><<<grid, 128, 0, st>>>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad,
+                                               rmax, D, plan);
 }
 
-int launch_slice(int S, const double *Xh, const double *Xl, int64_t ld, int row_contig,
-                 int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+// Slice with the certified count among the plan's candidates (one fixed S,
+// or 14 / 15).
+int launch_slice(const SplitPlan &plan, const double *Xh, const double *Xl, int64_t ld,
+                 int row_contig, int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
                  const unsigned long long *rmax, __half *D, cudaStream_t st) {
     if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for slicing");
-#define MPDD_SLICE_CASE(SS)                                                                 \
-    case SS:                                                                                \
-        launch_slice_s<SS>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, D, st); \
+    if (plan.ncand == 2) {
+        if (plan.count[0] != 14 || plan.count[1] != 15)
+            return fail(MP_DD_ERR_TOO_LARGE, "unexpected slice candidates");
+        launch_slice_s<14, 15>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, D, plan,
+                               st);
+        return check_launch("slice_kernel");
+    }
+#define MPDD_SLICE_CASE(SS)                                                                  \
+    case SS:                                                                                 \
+        launch_slice_s<SS, SS>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, D, plan, \
+                               st);                                                          \
         break;
-    switch (S) {
+    switch (plan.count[0]) {
         MPDD_SLICE_CASE(2) MPDD_SLICE_CASE(3) MPDD_SLICE_CASE(4) MPDD_SLICE_CASE(5)
         MPDD_SLICE_CASE(6) MPDD_SLICE_CASE(7) MPDD_SLICE_CASE(8) MPDD_SLICE_CASE(9)
         MPDD_SLICE_CASE(10) MPDD_SLICE_CASE(11) MPDD_SLICE_CASE(12) MPDD_SLICE_CASE(13)
         MPDD_SLICE_CASE(14) MPDD_SLICE_CASE(15)
         default:
-            return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, 15]", S);
+            return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, 15]", plan.count[0]);
     }
 #undef MPDD_SLICE_CASE
     return check_launch("slice_kernel");
@@ -649,14 +807,23 @@ int sliced_timing_read(float *ms) {
     return 0;
 }
 
+namespace {
+
+// Slices the workspace holds: the caller's S, or the widest auto candidate.
+int slices_allocated(int slices, int64_t k) {
+    int cand[kMaxCand];
+    const int nc = slice_candidates(slices, k, cand);
+    return cand[nc - 1];
+}
+
+}  // namespace
+
 size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int S) {
-    if (S == 0) S = kDefaultSlices;
-    return make_layout(m, n, k, S).total;
+    return make_layout(m, n, k, slices_allocated(S, k)).total;
 }
 
 int sliced_layout(int64_t m, int64_t n, int64_t k, int S, size_t *offsets) {
-    if (S == 0) S = kDefaultSlices;
-    Layout L = make_layout(m, n, k, S);
+    Layout L = make_layout(m, n, k, slices_allocated(S, k));
     offsets[0] = L.off_rowmax;
     offsets[1] = L.off_colmax;
     offsets[2] = L.off_da;
@@ -668,32 +835,134 @@ int sliced_layout(int64_t m, int64_t n, int64_t k, int S, size_t *offsets) {
     return 0;
 }
 
-int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t st) {
-    if (S == 0) S = kDefaultSlices;
-    if (S < 2 || S > kMaxSlices)
-        return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, %d]", S, kMaxSlices);
+int sliced_magnitude_offsets(int64_t m, int64_t n, int64_t k, int S, size_t *offsets) {
+    Layout L = make_layout(m, n, k, slices_allocated(S, k));
+    offsets[0] = L.off_ma;
+    offsets[1] = L.off_mb;
+    return 0;
+}
+
+// ------------------------------------------------------------------ certificate (host)
+
+SplitPlan make_plan(SplitHeader *h, unsigned long long *dmin_dev, int form, int64_t k,
+                    int ncand, const int *widths, const int *counts, const double *cst) {
+    SplitPlan pl{};
+    pl.dmin = dmin_dev;
+    pl.ncand = ncand;
+    *h = SplitHeader{};
+    h->form = form;
+    h->ncand = ncand;
+    h->k = k;
+    h->dmin = 0x7FF0000000000000ull;   // +inf until the magnitude product lowers it
+    for (int c = 0; c < ncand; ++c) {
+        // cst 2^(106 - W) / 12, rounded up: the power of two is exact, the
+        // quotient is within 2^-53 of itself, and 1 + 2^-50 covers that
+        double t = std::ldexp(cst[c], 106 - widths[c]) / 12.0 * (1.0 + 0x1p-50);
+        unsigned long long bits;
+        memcpy(&bits, &t, 8);
+        pl.thr[c] = h->thr[c] = bits;
+        pl.count[c] = h->count[c] = counts[c];
+        pl.width[c] = h->width[c] = widths[c];
+    }
+    return pl;
+}
+
+int launch_magnitude(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
+                     int64_t rows_pad, int64_t k_pad, const unsigned long long *rmax, void *M,
+                     SplitHeader *hdr, const SplitHeader *init, cudaStream_t st) {
+    if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for the certificate");
+    dim3 grid((unsigned)ceil_div(rows_pad, 64), (unsigned)(k_pad / 16));
+    magnitude_kernel<<<grid, 128, 0, st>>>(X, ld, row_contig, rows, k, rows_pad, k_pad, rmax,
+                                          static_cast<__nv_bfloat16 *>(M),
+                                          init ? hdr : nullptr, init ? *init : SplitHeader{});
+    return check_launch("magnitude_kernel");
+}
+
+namespace {
+
+// A lower bound of |beta| / |alpha| for dd scalars: |x| >= |x.hi| (1 - 2^-53)
+// for a normalised dd, the binary64 quotient is within 2^-53 of the exact
+// one, and the factor (1 - 2^-49) absorbs both.
+double ratio_lower(mp_dd beta, mp_dd alpha) {
+    return std::fabs(beta.hi) / std::fabs(alpha.hi) * (1.0 - 0x1p-49);
+}
+
+}  // namespace
+
+int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int64_t n_pad,
+                       int64_t k_pad, int TN, const unsigned long long *rmax,
+                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st) {
+    // 128-wide tiles whatever the product's own width (n_pad is a multiple
+    // of 128 either way): the margin epilogue then has registers to spare
+    (void)TN;
+    TN = 128;
+    int rc;
+    CUtensorMap tmA, tmB;
+    if ((rc = make_tmap(&tmA, MA, m_pad, k_pad, TM, 1))) return rc;
+    if ((rc = make_tmap(&tmB, MB, n_pad, k_pad, TN, 1))) return rc;
+    BandArgs ba{};
+    ba.S = 1;
+    ba.kb_count = (int)(k_pad / TK);
+    ba.tiles_m = (int)(m_pad / TM);
+    ba.tiles_n = (int)(n_pad / TN);
+    ba.m_pad = m_pad;
+    ba.n_pad = n_pad;
+    ba.status = &hdr->status;
+    ba.diag = 1;
+    ba.tri = p.tri;
+    ba.mag = 1;
+    ba.m = p.m;
+    ba.n = p.n;
+    ba.ldc = p.ldc;
+    ba.rmax = rmax;
+    ba.cmax = cmax;
+    ba.ch = p.ch;
+    ba.ba_ratio = p.beta_zero ? 0.0 : ratio_lower(p.beta, p.alpha);
+    // the fp32 sums of non-negative products are at most (1 + k 2^-21) above
+    // the exact sums of the bf16 products (see the accumulation argument of
+    // the certificate), and |hi| is within 2^-53 of |hi + lo|
+    ba.c1 = 1.0 - (double)(p.k + 1) * 0x1p-20;
+    ba.dmin_out = &hdr->dmin;
+    return launch_band(tmA, tmB, ba, TN, st);
+}
+
+int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (slices != 0 && (slices < 2 || slices > kMaxSlices))
+        return fail(MP_DD_ERR_TOO_LARGE, "slices = %d outside [2, %d]", slices, kMaxSlices);
+    int cand[kMaxCand];
+    const int ncand = slice_candidates(slices, p.k, cand);
     // |P_b| <= (b + 1) k 2^14 must stay below 2^31 for the int32 band sums
-    if ((int64_t)S * p.k > ((int64_t)1 << 17) - 1)
+    if ((int64_t)cand[0] * p.k > ((int64_t)1 << 17) - 1)
         return fail(MP_DD_ERR_TOO_LARGE, "k * slices = %lld exceeds 131071",
-                    (long long)(S * p.k));
+                    (long long)(cand[0] * p.k));
+    const int S = cand[ncand - 1];   // planes the workspace holds
     Layout L = make_layout(p.m, p.n, p.k, S);
     if (ws == nullptr || ws_bytes < L.total)
         return fail(MP_DD_ERR_WORKSPACE, "sliced Rgemm needs %zu workspace bytes, got %zu",
                     L.total, ws_bytes);
     if (L.n_pad * (int64_t)S > 0x7fffffffLL || L.m_pad * (int64_t)S > 0x7fffffffLL)
         return fail(MP_DD_ERR_TOO_LARGE, "matrix too large for the sliced path");
-    if (p.alpha_zero) return launch_gemm_plain(p, st);  // C := beta C only
     const int TN = band_tn(p.m, p.n);
 
     uint8_t *w = static_cast<uint8_t *>(ws);
-    cudaError_t e = cudaMemsetAsync(w, 0, L.off_da, st);  // status word and maxima
+    cudaError_t e = cudaMemsetAsync(w, 0, L.off_da, st);  // header (form 0) and maxima
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (p.alpha_zero) return launch_gemm_plain(p, st);  // C := beta C only
     auto *rmax = reinterpret_cast<unsigned long long *>(w + L.off_rowmax);
     auto *cmax = reinterpret_cast<unsigned long long *>(w + L.off_colmax);
     auto *DA = reinterpret_cast<__half *>(w + L.off_da);
     auto *DB = reinterpret_cast<__half *>(w + L.off_db);
     auto *P = reinterpret_cast<int32_t *>(w + L.off_p);
-    int *status = reinterpret_cast<int *>(w);
+    auto *hdr = reinterpret_cast<SplitHeader *>(w);
+
+    int widths[kMaxCand];
+    double cst[kMaxCand];
+    for (int c = 0; c < ncand; ++c) {
+        widths[c] = 8 * cand[c];
+        cst[c] = slice_constant(cand[c]);
+    }
+    SplitHeader init;
+    const SplitPlan plan = make_plan(&init, &hdr->dmin, 1, p.k, ncand, widths, cand, cst);
 
     // op(A) rows: A[i + l lda] when transa = N; op(B) columns as rows: B[l + j ldb]
     // when transb = N (contiguous in l), B[j + l ldb] when transb = T.
@@ -702,10 +971,19 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     timer().mark(0, st);
     if ((rc = launch_absmax(p.ah, p.lda, a_rc, p.m, p.k, rmax, st))) return rc;
     if ((rc = launch_absmax(p.bh, p.ldb, b_rc, p.n, p.k, cmax, st))) return rc;
-    if ((rc = launch_slice(S, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax, DA,
+    if ((rc = launch_magnitude(p.ah, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
+                               w + L.off_ma, hdr, &init, st)))
+        return rc;
+    if ((rc = launch_magnitude(p.bh, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax,
+                               w + L.off_mb, hdr, nullptr, st)))
+        return rc;
+    if ((rc = launch_certificate(p, w + L.off_ma, w + L.off_mb, L.m_pad, L.n_pad, L.k_pad, TN,
+                                 rmax, cmax, hdr, st)))
+        return rc;
+    if ((rc = launch_slice(plan, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax, DA,
                            st)))
         return rc;
-    if ((rc = launch_slice(S, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax, DB,
+    if ((rc = launch_slice(plan, p.bh, p.bl, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax, DB,
                            st)))
         return rc;
 
@@ -723,12 +1001,13 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     ba.P = P;
     ba.R = nullptr;
     ba.diag = 0;
-    ba.status = status;
+    ba.status = &hdr->status;
+    ba.plan = plan;
     if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
     timer().mark(2, st);
 
     RecArgs ra{};
-    ra.S = S;
+    ra.plan = plan;
     ra.m = p.m; ra.n = p.n; ra.m_pad = L.m_pad; ra.n_pad = L.n_pad;
     ra.P = P; ra.rmax = rmax; ra.cmax = cmax;
     ra.alpha = p.alpha; ra.beta = p.beta;
@@ -738,35 +1017,93 @@ int run_sliced(const GemmArgs &p, int S, void *ws, size_t ws_bytes, cudaStream_t
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
     recombine_kernel<<<(unsigned)blocks, 256, 0, st>>>(ra);
-    rc = check_launch("recombine_kernel");
+    if ((rc = check_launch("recombine_kernel"))) return rc;
+    rc = launch_plain_fallback(p, plan, st);
     timer().mark(3, st);
     return rc;
 }
+
+namespace {
+
+template <bool MAG>
+void set_band_attrs() {
+    cudaFuncSetAttribute(band_gemm_kernel<128, MAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BandCfg<128>::SMEM);
+    cudaFuncSetAttribute(band_gemm_kernel<256, MAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)BandCfg<256>::SMEM);
+}
+
+template <bool MAG>
+void launch_band_t(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
+                   int grid, cudaStream_t st) {
+    if (TN == 256)
+        band_gemm_kernel<256, MAG><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(
+            tmA, tmB, ba);
+    else
+        band_gemm_kernel<128, MAG><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
+            tmA, tmB, ba);
+}
+
+}  // namespace
 
 int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
                 cudaStream_t st) {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
-        cudaFuncSetAttribute(band_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BandCfg<128>::SMEM);
-        cudaFuncSetAttribute(band_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BandCfg<256>::SMEM);
+        set_band_attrs<false>();
+        set_band_attrs<true>();
     });
     const int tiles = ba.tiles_m * ba.tiles_n;
-    const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords
+    const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords (S: the most bands)
     const int grid = items < sm_count() ? items : sm_count();
-    if (TN == 256)
-        band_gemm_kernel<256><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(tmA, tmB,
-                                                                                      ba);
-    else
-        band_gemm_kernel<128><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(tmA, tmB,
-                                                                                      ba);
+    if (ba.mag) launch_band_t<true>(tmA, tmB, ba, TN, grid, st);
+    else launch_band_t<false>(tmA, tmB, ba, TN, grid, st);
     return check_launch("band_gemm_kernel");
 }
 
 int read_status(const void *ws, int *status) {
-    cudaError_t e = cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaStreamSynchronize(tls().stream);
+    if (e == cudaSuccess) e = cudaMemcpy(status, ws, sizeof(int), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? 0 : cuda_fail(e, "status read");
+}
+
+// The header of the last split-precision call on a workspace, interpreted:
+// the certified width (or the plain kernel), and the guaranteed bound of
+// max |C - C_exact| / bound.
+int split_report(const void *ws, mp_dd_split_info *info) {
+    SplitHeader h;
+    cudaError_t e = cudaStreamSynchronize(tls().stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, ws, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "split report read");
+    *info = mp_dd_split_info{};
+    info->status = h.status;
+    info->form = h.form;
+    double dmin;
+    memcpy(&dmin, &h.dmin, 8);
+    info->dmin = dmin;
+    if (h.form == 0 || h.ncand < 1 || h.ncand > kMaxCand) {
+        info->max_err_est = 0.0;   // no product formed: C := beta C, as the plain path
+        return 0;
+    }
+    const double fin = 0.25 / (double)(h.k > 0 ? h.k : 1);   // final roundings
+    int c = -1;
+    for (int q = 0; q < h.ncand && c < 0; ++q)
+        if (h.dmin >= h.thr[q]) c = q;
+    if (c < 0) {
+        // the plain kernel: within half the bound (its per-step error, read
+        // from its dd multiply-add), plus the final roundings
+        info->width_bits = 0;
+        info->count = 0;
+        info->max_err_est = 0.5 + fin;
+        return 0;
+    }
+    double thr;
+    memcpy(&thr, &h.thr[c], 8);
+    info->width_bits = h.width[c];
+    info->count = h.count[c];
+    // operand rounding: cst 2^(106 - W) / (16 dmin) = (3/4) thr / dmin
+    info->max_err_est = (dmin > 0.0 ? 0.75 * thr / dmin : 0.0) + fin;
+    return 0;
 }
 
 }  // namespace mpdd

@@ -32,6 +32,11 @@ struct GemmArgs {
     // Rsymm: op(A) (sym_a) or op(B) (sym_b) is symmetric with one triangle
     // stored: 0 = no, 1 = upper stored, 2 = lower stored (transpose flag 0).
     int sym_a = 0, sym_b = 0;
+    // Fallback of a split-precision call: when gate != nullptr the kernel
+    // computes C only if *gate (the call's certificate margin, as bits) is
+    // below gate_below, i.e. when no operand width certified the bound.
+    const unsigned long long *gate = nullptr;
+    unsigned long long gate_below = 0;
 };
 
 // Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).
@@ -49,6 +54,11 @@ size_t sliced_workspace_bytes(int64_t m, int64_t n, int64_t k, int slices);
 int sliced_layout(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
 int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStream_t stream);
 int read_status(const void *ws, int *status);
+// The certificate and width of the last split-precision call on `ws`.
+int split_report(const void *ws, mp_dd_split_info *info);
+// Byte offsets of the certificate's magnitude planes (op(A), op(B)^T).
+int sliced_magnitude_offsets(int64_t m, int64_t n, int64_t k, int slices, size_t *offsets);
+int crt_magnitude_offsets(int64_t m, int64_t n, int64_t k, bool sym, size_t *offsets);
 void sliced_timing_enable(int on);
 void sliced_timing_mark(int phase, cudaStream_t stream);  // phases 0..3 of a timed call
 int sliced_timing_read(float *ms);
@@ -97,5 +107,6 @@ int run_qd_gemm(int ta, int tb, int64_t m, int64_t n, int64_t k, const double *a
 // Sliced Rgemm on the library's built-in scratch array (no allocation).
 size_t noalloc_scratch_bytes();
 int run_sliced_noalloc(const GemmArgs &p, int slices, cudaStream_t stream);
+int noalloc_report(mp_dd_split_info *info);
 
 }  // namespace mpdd

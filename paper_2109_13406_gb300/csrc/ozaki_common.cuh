@@ -1,6 +1,8 @@
 // Device helpers shared by the split-precision Rgemm forms (slices and
 // residues): the power-of-two row/column scale, the exact rounding of a dd
-// entry to a 128-bit integer, and its balanced base-256 digits.
+// entry to a 128-bit integer, its balanced base-256 digits, and the per-call
+// accuracy certificate (magnitude planes, the header it is kept in, and the
+// rule that turns it into a width).
 #pragma once
 
 #include <cuda.h>
@@ -10,10 +12,77 @@
 
 namespace mpdd {
 
+// ------------------------------------------------------------------ certificate
+//
+// Every split-precision call first bounds, per output entry, the error its
+// rounded operands can cause against the accuracy target
+// 4 k 2^-104 (|alpha||A||B| + |beta||C|)_ij, and only then picks the operand
+// width (or hands the product to the plain FP64 kernel).  With e_i, f_j the
+// row / column scales and W the width in bits, every product of rounded
+// operands is off by at most cst 2^(e_i + f_j - W) (cst per form), so the
+// call meets the target with a quarter of it left for the final roundings
+// when
+//
+//   cst 2^(106 - W) / 12  <=  d_ij := L_ij 2^-(e_i+f_j) + |beta/alpha||c_ij| 2^-(e_i+f_j)
+//
+// for every entry, L_ij a lower bound of (|A||B|)_ij.  L comes from one
+// tensor-core product of magnitude planes |hi| 2^-e rounded toward zero to
+// bf16, accumulated in fp32 and scaled by (1 - (k+1) 2^-20) (see the
+// magnitude kernel and the band kernel's magnitude mode); the smallest d_ij
+// of the call is kept in the workspace header (its bit pattern: non-negative
+// doubles order like their bits).  Every later kernel of the call derives
+// the same decision from it with plan_choice().
+constexpr int kMaxCand = 3;
+
+// Workspace header (the first bytes of every split-precision workspace).
+struct SplitHeader {
+    int status;                        // 0, or 2001 when a device wait timed out
+    int form;                          // 1 digit slices, 2 residues; 0: no product formed
+    int ncand;                         // candidate widths, ascending
+    int reserved;
+    unsigned long long dmin;           // bits of min_ij d_ij (+inf: no entry constrains)
+    long long k;
+    unsigned long long thr[kMaxCand];  // bits of cst_c 2^(106 - W_c) / 12, rounded up
+    int count[kMaxCand];               // slices or moduli of candidate c
+    int width[kMaxCand];               // W_c in bits
+};
+
+// The decision rule as kernel arguments: candidate c is taken when dmin is at
+// least thr[c] (the first such c, i.e. the narrowest width); -1: none, the
+// plain kernel computes the product.
+struct SplitPlan {
+    const unsigned long long *dmin;    // header word; nullptr: no certificate (count[0])
+    unsigned long long thr[kMaxCand];
+    int count[kMaxCand];
+    int width[kMaxCand];
+    int ncand;
+};
+
+struct PlanPick {
+    int c, count, width;   // c = -1: no candidate certifies the bound
+};
+
+// (Every index below is a constant after unrolling, so the plan stays in the
+// kernel's parameter space instead of being copied to local memory.)
+__device__ __forceinline__ PlanPick plan_choice(const SplitPlan &pl) {
+    if (pl.dmin == nullptr) return PlanPick{0, pl.count[0], pl.width[0]};
+    const unsigned long long d = *reinterpret_cast<const volatile unsigned long long *>(pl.dmin);
+    PlanPick r{-1, 0, 0};
+#pragma unroll
+    for (int c = kMaxCand - 1; c >= 0; --c)
+        if (c < pl.ncand && d >= pl.thr[c]) r = PlanPick{c, pl.count[c], pl.width[c]};
+    return r;
+}
+
 // One band-product launch.  Triangle mode (diag = 0): band b sums the pairs
 // (t, b - t) of digit planes and is stored as int32 in P.  Diagonal mode
 // (diag = 1): band b is the single product of planes (b, b) -- the residue
-// form -- and is stored reduced modulo moduli[b] as uint8 in R.
+// form -- and is stored reduced modulo moduli[b] as uint8 in R.  Magnitude
+// mode (mag = 1, diagonal, one band): the bf16 product of the magnitude
+// planes, summed in fp32, turned into the certificate margin d_ij of every
+// entry and reduced to its minimum in *dmin_out.  With plan.dmin set, the
+// band count is plan.count[plan_choice(plan)] and a failed choice makes the
+// launch return at once.
 constexpr int kMaxBands = 48;
 struct BandArgs {
     int S, kb_count, tiles_m, tiles_n;
@@ -22,18 +91,48 @@ struct BandArgs {
     uint8_t *R;   // [S][n_pad][m_pad] (diagonal mode)
     int *status;
     int diag;
-    int tri;      // diagonal mode: 1 / 2 = only tiles meeting the upper / lower triangle
+    int tri;      // diagonal / magnitude mode: 1 / 2 = only the upper / lower triangle
     int moduli[kMaxBands];
+    SplitPlan plan;
+    // magnitude mode
+    int mag;
+    int64_t m, n, ldc;
+    const unsigned long long *rmax, *cmax;
+    const double *ch;          // hi plane of C (read when ba_ratio > 0)
+    double ba_ratio;           // lower bound of |beta| / |alpha|, 0 when beta = 0
+    double c1;                 // 1 - (k + 1) 2^-20: the fp32 sums' safety factor
+    unsigned long long *dmin_out;
 };
 
 // Host launchers shared by the two forms (defined in dd_sliced.cu).
-int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows);
+// elem: 0 = fp16, 1 = bf16 elements.
+int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_rows,
+              int elem = 0);
 int launch_absmax(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
                   unsigned long long *out, cudaStream_t st);
 int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
                 cudaStream_t st);
 constexpr int kBandTM = 128, kBandTK = 64;
 int band_tn(int64_t m, int64_t n);
+
+// Magnitude planes and the certificate (dd_sliced.cu).  form: 1 slices, 2
+// residues; widths[c] / counts[c] / cst[c] the candidates (ascending width)
+// and their per-product error constants.  make_plan also fills the header
+// image that the first magnitude launch writes (init != nullptr).
+SplitPlan make_plan(SplitHeader *hdr_image, unsigned long long *dmin_dev, int form, int64_t k,
+                    int ncand, const int *widths, const int *counts, const double *cst);
+int launch_magnitude(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
+                     int64_t rows_pad, int64_t k_pad, const unsigned long long *rmax, void *M,
+                     SplitHeader *hdr, const SplitHeader *init, cudaStream_t st);
+// The magnitude product and its reduction into the header (MA [m_pad][k_pad],
+// MB [n_pad][k_pad] bf16).
+struct GemmArgs;
+int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int64_t n_pad,
+                       int64_t k_pad, int TN, const unsigned long long *rmax,
+                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st);
+// The plain kernel behind the split-precision call: runs only when the
+// certificate fails (plan_choice < 0).
+int launch_plain_fallback(const GemmArgs &p, const SplitPlan &plan, cudaStream_t st);
 
 // e with max |x| < 2^(e-1): from the biased exponent E of the maximum,
 // max in [2^(E-1023), 2^(E-1022)) -> e = E - 1021 (E = 0, subnormal: same).

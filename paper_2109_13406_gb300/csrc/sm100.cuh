@@ -188,5 +188,10 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with bf16 A and B (A/B format 1 in bits 7-9 and 10-12).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return idesc_f16_f32(M, N) | (1u << 7) | (1u << 10);
+}
+
 }  // namespace sm100
 }  // namespace mpdd

@@ -37,16 +37,18 @@ def test_crt_intermediates_bit_exact(cuda_lib, ta, tb):
     c = datagen.gemm_case(700 + "NT".index(ta) * 2 + "NT".index(tb), ta, tb, m, n, k, pad=1)
     got, ws = run_crt(cuda_lib, c)
     L = cuda_lib.mp_dd_crt_layout(m, n, k)
-    mods = L["moduli"]
-    assert mods == oz.crt_moduli(len(mods))
+    assert L["moduli"] == oz.crt_moduli(len(L["moduli"]))
+    rep = cuda_lib.mp_dd_split_report(ws)
+    N, W = rep["count"], rep["width_bits"]
+    assert W == 112 and N <= len(L["moduli"])   # well-scaled inputs: the narrowest width
+    mods = L["moduli"][:N]
     P = 1
     for p in mods:
         P *= p
-    assert P > k * 2 ** 223            # the reconstruction is exact
+    assert P >= k * 2 ** (2 * W)       # the reconstruction is exact
     mp_, np_, kp = L["m_pad"], L["n_pad"], L["k_pad"]
-    RA, _ = oz.residue_planes(*oz.op_rows(c.A, ta == "T", m, k), mods)
-    RB, _ = oz.residue_planes(*oz.op_cols(c.B, tb == "T", k, n), mods)
-    N = len(mods)
+    RA, _ = oz.residue_planes(*oz.op_rows(c.A, ta == "T", m, k), mods, W // 8)
+    RB, _ = oz.residue_planes(*oz.op_cols(c.B, tb == "T", k, n), mods, W // 8)
     ra = view(ws, L["residues_a"], N * mp_ * kp, np.float16).reshape(N, mp_, kp)
     rb = view(ws, L["residues_b"], N * np_ * kp, np.float16).reshape(N, np_, kp)
     assert np.array_equal(ra[:, :m, :k].astype(np.int64), RA)
@@ -88,7 +90,9 @@ def test_crt_wide_tiles_and_ill_scaled(cuda_lib):
     c = datagen.gemm_case(730, "N", "N", m, n, k, ill="outer")
     got, ws = run_crt(cuda_lib, c)
     L = cuda_lib.mp_dd_crt_layout(m, n, k)
-    mods = L["moduli"]
+    rep = cuda_lib.mp_dd_split_report(ws)
+    assert rep["width_bits"] == 112
+    mods = L["moduli"][:rep["count"]]
     g = datagen.rng(731)
     rows = np.concatenate([[0, m - 1], g.integers(0, m, 10)])
     cols = np.concatenate([[0, 255, 256, n - 1], g.integers(0, n, 8)])
@@ -108,7 +112,9 @@ def test_crt_wide_tiles_and_ill_scaled(cuda_lib):
 def test_crt_config2_2048(cuda_lib, ill):
     n = 2048
     c = datagen.gemm_case(2, "N", "N", n, n, n, ill=ill)
-    got, _ = run_crt(cuda_lib, c)
+    got, ws = run_crt(cuda_lib, c)
+    rep = cuda_lib.mp_dd_split_report(ws)
+    assert rep["width_bits"] == 112 and rep["count"] == 32 and rep["max_err_est"] < 0.01
     rr, cc = sample_blocks(n, n, bs=16, count=8)
     assert check_against_exact(c, got, rr, cc) <= 1.0
 

@@ -132,3 +132,171 @@ def test_crt_form_error_is_the_operand_rounding_only():
         for j in range(n):
             v = Fraction(int(rec[i, j])) * Fraction(2) ** (int(ea[i]) + int(fb[j]) - 224)
             assert abs(v - exact[i][j]) <= k * Fraction(2) ** (int(ea[i]) + int(fb[j]) - 112)
+
+
+# ---------------------------------------------------------------------------
+# per-call certificate
+# ---------------------------------------------------------------------------
+
+def _bf16_neighbours(y: Fraction):
+    """y as a float32 bit pattern (asserting it is a bf16) and the next bf16 above."""
+    f = np.float32(float(y))
+    assert Fraction(float(f)) == y, "not a float32"
+    bits = int(np.array(f).view(np.uint32))
+    assert bits & 0xFFFF == 0, "not a bf16"
+    up = np.array(bits + 0x10000, dtype=np.uint32).view(np.float32)
+    return bits, Fraction(float(up))
+
+
+def test_bf16_floor_is_the_largest_bf16_not_above():
+    """Brute force over the neighbouring bf16 values (numpy's float32 bits)."""
+    g = datagen.rng(40)
+    xs = [Fraction(0), Fraction(1, 3), Fraction(1, 2) - Fraction(1, 2 ** 60),
+          Fraction(2) ** -126, Fraction(2) ** -133, Fraction(3, 2) * Fraction(2) ** -134,
+          Fraction(2) ** -127 * Fraction(5, 3)]
+    for _ in range(400):
+        xs.append(Fraction(float(g.uniform(0.0, 0.5))) * Fraction(2) ** int(g.integers(-140, 0)))
+    for x in xs:
+        y = oz.bf16_floor(x)
+        assert 0 <= y <= x
+        if x == 0:
+            continue
+        bits, nxt = _bf16_neighbours(y)
+        assert nxt > x
+    # exact bf16 values map to themselves
+    for v in (0.25, 0.1875, 2.0 ** -126, 2.0 ** -133, 3 * 2.0 ** -133):
+        assert oz.bf16_floor(Fraction(v)) == Fraction(v)
+
+
+def _stress_rows(seed, rows, k, spread):
+    """dd rows whose entries spread over 2^-spread .. 1 of the row maximum."""
+    g = datagen.rng(seed)
+    h = g.uniform(-1, 1, (rows, k)) * np.ldexp(1.0, g.integers(-spread, 1, (rows, k)))
+    h, l = datagen.dd_lo_for(h, g)
+    return h, l
+
+
+@pytest.mark.parametrize("W", [112, 120, 128])
+def test_crt_product_error_within_its_constant(W):
+    """|a b - a' b'| <= (1 + 2^-W) 2^(e + f - W) for every product of the
+    rounded operands of the residue form, entries over 60 binades."""
+    ah, al = _stress_rows(41, 3, 40, 60)
+    bh, bl = _stress_rows(42, 3, 40, 60)
+    cst = oz.product_error_constant("crt", W)
+    for i in range(3):
+        XA, e = oz.scaled_integers(ah[i], al[i], W // 8)
+        for j in range(3):
+            XB, f = oz.scaled_integers(bh[j], bl[j], W // 8)
+            for l in range(40):
+                a = Fraction(float(ah[i, l])) + Fraction(float(al[i, l]))
+                b = Fraction(float(bh[j, l])) + Fraction(float(bl[j, l]))
+                ap = XA[l] * Fraction(2) ** (e - W)
+                bp = XB[l] * Fraction(2) ** (f - W)
+                assert abs(a * b - ap * bp) <= cst * Fraction(2) ** (e + f - W)
+
+
+@pytest.mark.parametrize("S", [10, 14, 15])
+def test_sliced_product_error_within_its_constant(S):
+    """One product through the digit bands (pairs t + u < S only) stays within
+    product_error_constant("sliced", 8S) 2^(e + f - 8S)."""
+    ah, al = _stress_rows(43, 40, 1, 0)
+    bh, bl = _stress_rows(44, 40, 1, 0)
+    cst = oz.product_error_constant("sliced", 8 * S)
+    for q in range(40):
+        DA, ea = oz.split_matrix(ah[q:q + 1], al[q:q + 1], S)
+        DB, fb = oz.split_matrix(bh[q:q + 1], bl[q:q + 1], S)
+        V = oz.recombine_exact(oz.band_products(DA, DB), ea, fb)[0][0]
+        a = Fraction(float(ah[q, 0])) + Fraction(float(al[q, 0]))
+        b = Fraction(float(bh[q, 0])) + Fraction(float(bl[q, 0]))
+        unit = Fraction(2) ** (int(ea[0]) + int(fb[0]) - 8 * S)
+        assert abs(a * b - V) <= cst * unit
+
+
+def _crt_error_ratio(c, W, m, n, k):
+    """max over entries of |alpha| |sum a'b' - sum ab| / (12 k 2^-106 (|alpha||A||B| +
+    |beta||C|)): at most 1 is what a certified width promises."""
+    ah, al = oz.op_rows(c.A, c.transa == "T", m, k)
+    bh, bl = oz.op_cols(c.B, c.transb == "T", k, n)
+    alpha = abs(Fraction(c.alpha[0]) + Fraction(c.alpha[1]))
+    beta = abs(Fraction(c.beta[0]) + Fraction(c.beta[1]))
+    worst = Fraction(0)
+    for i in range(m):
+        XA, e = oz.scaled_integers(ah[i], al[i], W // 8)
+        for j in range(n):
+            XB, f = oz.scaled_integers(bh[j], bl[j], W // 8)
+            err, ab = Fraction(0), Fraction(0)
+            for l in range(k):
+                a = Fraction(float(ah[i, l])) + Fraction(float(al[i, l]))
+                b = Fraction(float(bh[j, l])) + Fraction(float(bl[j, l]))
+                err += a * b - XA[l] * XB[l] * Fraction(2) ** (e + f - 2 * W)
+                ab += abs(a) * abs(b)
+            cc = abs(Fraction(float(c.C[0][i, j])) + Fraction(float(c.C[1][i, j])))
+            worst = max(worst, alpha * abs(err) /
+                        (12 * k * Fraction(2) ** -106 * (alpha * ab + beta * cc)))
+    return worst
+
+
+def test_certified_width_keeps_the_error_within_the_bound():
+    """Inner-scaled operands (exponents spread along k): the rule picks 128
+    bits, and the exact error of the rounded product then stays within three
+    quarters of the bound; at the default 112 bits it does not."""
+    m, n, k = 3, 3, 400
+    c = datagen.gemm_case(45, "N", "N", m, n, k, ill="inner")
+    d = oz.exact_margins(oz.op_rows(c.A, False, m, k), oz.op_cols(c.B, False, k, n), c.alpha,
+                         c.beta, c.C)
+    W = oz.certified_width(min(d.values()), "crt", [112, 120, 128])
+    assert W == 128
+    assert _crt_error_ratio(c, 128, m, n, k) <= 1
+    assert _crt_error_ratio(c, 112, m, n, k) > 1
+
+
+def test_adversarial_operands_certify_no_width():
+    """Rows of A with 0.9 in column 0 and entries of size 2^-40 elsewhere, row 0
+    of B zero: the
+    margin is the closed form sum_{l >= 1} |a_l||b_l| 2^-(e+f), no width up to
+    128 bits qualifies, and at 128 bits the error does exceed the bound."""
+    k = 64
+    g = datagen.rng(46)
+    ah = g.uniform(0.5, 1.0, (2, k)) * 2.0 ** -40
+    ah[:, 0] = 0.9
+    bh = g.uniform(-1, 1, (k, 2))
+    bh[0, :] = 0.0
+    ah, al = datagen.dd_lo_for(ah, g)        # full dd entries: 106-bit values
+    bh, bl = datagen.dd_lo_for(bh, g)
+    A = (np.asfortranarray(ah), np.asfortranarray(al))
+    B = (np.asfortranarray(bh), np.asfortranarray(bl))
+    C = (np.zeros((2, 2), order="F"), np.zeros((2, 2), order="F"))
+    c = datagen.GemmCase("N", "N", 2, 2, k, (1.0, 0.0), A, B, (0.0, 0.0), C)
+    d = oz.exact_margins(oz.op_rows(A, False, 2, k), oz.op_cols(B, False, k, 2), c.alpha,
+                         c.beta)
+    for (i, j), v in d.items():
+        e, f = oz.scale_exponent(ah[i]), oz.scale_exponent(bh[:, j])
+        want = sum((Fraction(float(ah[i, l])) + Fraction(float(al[i, l]))) *
+                   abs(Fraction(float(bh[l, j])) + Fraction(float(bl[l, j])))
+                   for l in range(1, k))
+        assert v == want * Fraction(2) ** -(e + f)
+    assert oz.certified_width(min(d.values()), "crt", [112, 120, 128]) == 0
+    assert oz.certified_width(min(d.values()), "sliced", [112, 120]) == 0
+    assert _crt_error_ratio(c, 128, 2, 2, k) > 1
+
+
+def test_margins_cover_beta_c_and_skip_zero_rows():
+    g = datagen.rng(47)
+    A = datagen.dd_matrix(g, 3, 5)
+    B = datagen.dd_matrix(g, 5, 2)
+    A[0][1, :] = 0.0
+    A[1][1, :] = 0.0
+    C = datagen.dd_matrix(g, 3, 2)
+    d0 = oz.exact_margins(oz.op_rows(A, False, 3, 5), oz.op_cols(B, False, 5, 2), (1.0, 0.0),
+                          (0.0, 0.0))
+    d1 = oz.exact_margins(oz.op_rows(A, False, 3, 5), oz.op_cols(B, False, 5, 2), (2.0, 0.0),
+                          (1.0, 0.0), C)
+    assert (1, 0) not in d0 and (1, 1) not in d0 and len(d0) == 4
+    for key, v in d0.items():
+        i, j = key
+        e, f = oz.scale_exponent(A[0][i]), oz.scale_exponent(B[0][:, j])
+        cc = abs(Fraction(float(C[0][i, j])) + Fraction(float(C[1][i, j])))
+        assert d1[key] == v + Fraction(1, 2) * cc * Fraction(2) ** -(e + f)
+    up = oz.exact_margins(oz.op_rows(A, False, 3, 5), oz.op_rows(A, False, 3, 5), (1.0, 0.0),
+                          (0.0, 0.0), tri=1)
+    assert all(i <= j for i, j in up)

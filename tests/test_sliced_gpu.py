@@ -115,7 +115,9 @@ def test_config2_sampled_blocks_2048(cuda_lib, ill):
     the exact tier, and the plain path on the same inputs for comparison."""
     n = 2048
     c = datagen.gemm_case(2, "N", "N", n, n, n, ill=ill)
-    got, _ = run_sliced(cuda_lib, c)
+    got, ws = run_sliced(cuda_lib, c)
+    rep = cuda_lib.mp_dd_split_report(ws)
+    assert rep["width_bits"] == 112 and rep["count"] == 14 and rep["max_err_est"] < 0.05
     rows, cols = sample_blocks(n, n, bs=16, count=8)
     ratio = check_against_exact(c, got, rows, cols)
     assert ratio <= 1.0
