@@ -19,7 +19,10 @@ hi + lo of binary64 numbers with |lo| <= ulp(hi)/2):
 * SPD requests: G (n x 2n) = U [diag(s) 0] V^T with s geometric from 1 to
   1e-10 and random orthogonal U, V (products of Householder reflectors with
   Gaussian vectors), formed in binary64; G's lo plane follows the dd entry
-  recipe.  F = G G^T then has condition ~1e20.
+  recipe.  F = G G^T then has condition ~1e20.  ``spd_request`` draws it
+  with numpy on the host; ``spd_request_device`` with torch's seeded
+  generator on the GPU (the served benchmark, so that admission never waits
+  for host-side generation), the same construction with other random bits.
 """
 from __future__ import annotations
 
@@ -260,3 +263,41 @@ def poisson_arrivals(seed: int, count: int, rate_per_s: float) -> np.ndarray:
     """Arrival times (s) of a Poisson stream: cumulative exponential gaps."""
     g = rng(seed)
     return np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
+
+
+def spd_request_device(seed: int, n: int, nrhs: int = 4, smin: float = 1e-10):
+    """The served-solve recipe of ``spd_request`` generated on the current
+    CUDA device with torch's seeded generator: G = U [diag(s) 0] V^T (s
+    geometric from 1 to smin, U and V products of three Householder
+    reflectors with Gaussian vectors), lo planes hi 2^-53 U(-1, 1)
+    renormalised, B entries U(-1, 1) dd.  Returns ((G_hi, G_lo), (B_hi,
+    B_lo)) as column-major float64 device tensors."""
+    import torch
+
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    dev = "cuda"
+    s = torch.logspace(0.0, float(np.log10(smin)), n, dtype=torch.float64, device=dev)
+    G = torch.zeros((n, 2 * n), dtype=torch.float64, device=dev)
+    G[torch.arange(n), torch.arange(n)] = s
+    for side in ("left", "right"):
+        for _ in range(3):
+            dim = n if side == "left" else 2 * n
+            v = torch.randn(dim, dtype=torch.float64, device=dev, generator=gen)
+            v /= torch.linalg.norm(v)
+            if side == "left":
+                G -= 2.0 * torch.outer(v, v @ G)
+            else:
+                G -= 2.0 * torch.outer(G @ v, v)
+
+    def dd_pair(H):
+        lo = H * 2.0 ** -53 * (2 * torch.rand(H.shape, dtype=torch.float64, device=dev,
+                                               generator=gen) - 1)
+        hi = H + lo
+        lo = lo - (hi - H)
+        # column-major (shape rows x cols, strides (1, rows))
+        return hi.t().contiguous().t(), lo.t().contiguous().t()
+
+    Bh = 2 * torch.rand((n, nrhs), dtype=torch.float64, device=dev, generator=gen) - 1
+    return dd_pair(G), dd_pair(Bh)
+

@@ -576,14 +576,20 @@ int mp_dd_magnitude_layout(int form, int64_t m, int64_t n, int64_t k, int slices
                            size_t offsets[2]);
 
 /* Per-phase timing of split-precision calls (no counterpart in the manual).
- * With enable != 0, later mp_dd_Rgemm_sliced and mp_dd_Rgemm_crt calls from
- * this thread record CUDA events around their three phases on the current
- * stream; mp_dd_sliced_phase_ms waits for the last timed call and writes the
- * milliseconds of (0) scaling and slicing (or residues), (1) the tensor-core
- * products, (2) recombination (or CRT reconstruction) and epilogue.  Returns
- * 2002 if no call was timed. */
+ * With enable != 0, later mp_dd_Rgemm_sliced, mp_dd_Rgemm_crt and
+ * mp_dd_Rsyrk_crt calls from this thread record CUDA events around their
+ * three phases on the current stream: (0) scaling, certificate and slicing
+ * (or residues), (1) the tensor-core products, (2) recombination (or CRT
+ * reconstruction), epilogue and the plain fallback launch.  Enabling (again)
+ * starts a new log of up to 4096 calls.  mp_dd_sliced_phase_ms waits for the
+ * last timed call and writes its three milliseconds (2002 if no call was
+ * timed); mp_dd_sliced_phase_log waits for the first max_calls logged calls,
+ * writes their times to ms[3 c + phase] and the number of logged calls to
+ * *calls (errors: -1 ms NULL with max_calls > 0, -2 max_calls < 0, -3 calls
+ * NULL). */
 int mp_dd_sliced_timing(int enable);
 int mp_dd_sliced_phase_ms(float ms[3]);
+int mp_dd_sliced_phase_log(float *ms, int max_calls, int *calls);
 
 /* ------------------------------------------------------------------------ */
 /* Elementwise dd arithmetic (the dd format's scalar operations, Sec. 5)      */

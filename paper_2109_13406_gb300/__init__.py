@@ -254,6 +254,16 @@ def mp_dd_sliced_phase_ms() -> list:
     return [float(x) for x in ms]
 
 
+def mp_dd_sliced_phase_log(max_calls: int = 4096) -> list:
+    """Per-call phase times [[scale_split, products, recombine], ...] of the
+    calls timed since mp_dd_sliced_timing(True)."""
+    ms = (ctypes.c_float * (3 * max_calls))()
+    n = ctypes.c_int()
+    _check(_LIB.mp_dd_sliced_phase_log(ms, max_calls, ctypes.byref(n)), "mp_dd_sliced_phase_log")
+    k = min(n.value, max_calls)
+    return [[ms[3 * c], ms[3 * c + 1], ms[3 * c + 2]] for c in range(k)]
+
+
 def workspace(nbytes: int, device="cuda") -> torch.Tensor:
     """A device byte buffer for the calls that take a workspace."""
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)

@@ -139,6 +139,8 @@ SIGNATURES = {
     "mp_dd_Rgemm_grouped_prepare": (_int, [_i64, ctypes.POINTER(MpDDGemmDesc), _vp, _sz]),
     "mp_dd_Rgemm_grouped_run": (_int, [_vp]),
     "mp_dd_sliced_phase_ms": (_int, [ctypes.POINTER(ctypes.c_float)]),
+    "mp_dd_sliced_phase_log": (_int, [ctypes.POINTER(ctypes.c_float), _int,
+                                      ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None

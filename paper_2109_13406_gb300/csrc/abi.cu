@@ -736,6 +736,14 @@ int mp_dd_sliced_timing(int enable) {
     return 0;
 }
 
+int mp_dd_sliced_phase_log(float *ms, int max_calls, int *calls) {
+    clear_error();
+    if (max_calls < 0) return fail(-2, "sliced_phase_log: max_calls < 0");
+    if (ms == nullptr && max_calls > 0) return fail(-1, "sliced_phase_log: ms is NULL");
+    if (calls == nullptr) return fail(-3, "sliced_phase_log: calls is NULL");
+    return sliced_timing_log(ms, max_calls, calls);
+}
+
 int mp_dd_sliced_phase_ms(float ms[3]) {
     clear_error();
     if (ms == nullptr) return fail(-1, "sliced_phase_ms: ms is NULL");

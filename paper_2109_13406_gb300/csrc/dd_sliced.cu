@@ -41,6 +41,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "dd_arith.cuh"
@@ -770,17 +771,26 @@ int launch_slice(const SplitPlan &plan, const double *Xh, const double *Xl, int6
     return check_launch("slice_kernel");
 }
 
-// Optional per-phase CUDA-event timing of sliced calls made by this thread
-// (scaling + slicing, band products, recombination).
+// Optional per-phase CUDA-event timing of split-precision calls made by this
+// thread (scaling, certificate and splitting; tensor-core products;
+// recombination or reconstruction): four events per call, kept for every
+// call since timing was enabled (up to kMaxTimedCalls).
+constexpr int kMaxTimedCalls = 4096;
+
 struct PhaseTimer {
     bool on = false;
-    bool recorded = false;
-    cudaEvent_t ev[4] = {};
+    int calls = 0;              // completed timed calls since enabling
+    std::vector<cudaEvent_t> ev;  // 4 per call slot
     void mark(int i, cudaStream_t st) {
-        if (!on) return;
-        if (ev[i] == nullptr) cudaEventCreate(&ev[i]);
-        cudaEventRecord(ev[i], st);
-        if (i == 3) recorded = true;
+        if (!on || calls >= kMaxTimedCalls) return;
+        const size_t slot = (size_t)calls * 4 + (size_t)i;
+        while (ev.size() <= slot) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[slot], st);
+        if (i == 3) ++calls;
     }
 };
 
@@ -795,15 +805,30 @@ void sliced_timing_mark(int phase, cudaStream_t st) { timer().mark(phase, st); }
 
 void sliced_timing_enable(int on) {
     timer().on = on != 0;
-    timer().recorded = false;
+    timer().calls = 0;
 }
 
 int sliced_timing_read(float *ms) {
     PhaseTimer &t = timer();
-    if (!t.recorded) return fail(MP_DD_ERR_TOO_LARGE, "no timed sliced call on this thread");
-    cudaError_t e = cudaEventSynchronize(t.ev[3]);
+    if (t.calls == 0) return fail(MP_DD_ERR_TOO_LARGE, "no timed sliced call on this thread");
+    const size_t b = (size_t)(t.calls - 1) * 4;
+    cudaError_t e = cudaEventSynchronize(t.ev[b + 3]);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], t.ev[i], t.ev[i + 1]);
+    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], t.ev[b + i], t.ev[b + i + 1]);
+    return 0;
+}
+
+int sliced_timing_log(float *ms, int max_calls, int *calls) {
+    PhaseTimer &t = timer();
+    const int n = t.calls < max_calls ? t.calls : max_calls;
+    for (int c = 0; c < n; ++c) {
+        const size_t b = (size_t)c * 4;
+        cudaError_t e = cudaEventSynchronize(t.ev[b + 3]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        for (int i = 0; i < 3; ++i)
+            cudaEventElapsedTime(&ms[3 * c + i], t.ev[b + i], t.ev[b + i + 1]);
+    }
+    *calls = t.calls;
     return 0;
 }
 

@@ -62,6 +62,7 @@ int crt_magnitude_offsets(int64_t m, int64_t n, int64_t k, bool sym, size_t *off
 void sliced_timing_enable(int on);
 void sliced_timing_mark(int phase, cudaStream_t stream);  // phases 0..3 of a timed call
 int sliced_timing_read(float *ms);
+int sliced_timing_log(float *ms, int max_calls, int *calls);
 
 // Grouped dd Rgemm (one persistent launch over many problems).
 size_t grouped_workspace_bytes(int64_t count, const mp_dd_gemm_desc *descs);

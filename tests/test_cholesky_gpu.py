@@ -232,3 +232,40 @@ def test_diag_batch_independent_of_cluster_size(cuda_lib, nb):
             h, l = host(M)
             assert np.array_equal(np.tril(h), np.tril(ref[0])), count
             assert np.array_equal(np.tril(l), np.tril(ref[1])), count
+
+
+def _oracle_residual_ratio(Fs, X, B):
+    """LAPACK ratio ||B - F X||_1 / (||F||_1 ||X||_1 eps_dd) with the residual
+    from the oracle's exact tier (F symmetric, both triangles given)."""
+    n, nrhs = X[0].shape
+    rr, cc = np.meshgrid(np.arange(n), np.arange(nrhs), indexing="ij")
+    R = oracle.exact_gemm_entries("N", "N", n, (-1.0, 0.0), Fs, X, (1.0, 0.0), B, rr.ravel(),
+                                  cc.ravel())
+    fn = np.abs(Fs[0]).sum(axis=0).max()
+    xn = np.abs(X[0]).sum(axis=0).max()
+    return np.abs(R[0].reshape(n, nrhs)).sum(axis=0).max() / (fn * xn * EPS_DD)
+
+
+@pytest.mark.parametrize("crt_min_rest", [512, 64])
+def test_served_solutions_against_the_oracle(cuda_lib, crt_min_rest):
+    """Requests served in one mix -- F = G G^T on the tensor cores for
+    n >= 256, trailing updates in residue form for 512+ (or, forced, 64+)
+    columns and on the FP64 pipe below -- checked against the oracle: the
+    residual of each served solution by the exact tier (LAPACK ratio < 30,
+    the manual's LAPACK test threshold) with the oracle's own F, and the
+    oracle's own factor-and-solve within cond(F) eps (cond ~1e20)."""
+    from paper_2109_13406_gb300.server import SpdServer
+
+    sizes = [96, 300, 640]
+    done = SpdServer(slots=3, crt_min_rest=crt_min_rest).serve(make_requests(670, sizes))
+    by_id = {r.rid: r for r in done}
+    for i, n in enumerate(sizes):
+        r = by_id[i]
+        assert r.info == 0
+        G, B, Fs = spd_problem(670 + i, n)
+        assert _oracle_residual_ratio(Fs, r.X, B) < 30
+        oh, ol, oinfo = oracle.dd_potrf("U", Fs)
+        assert oinfo == 0
+        Xo = oracle.dd_potrs("U", (oh, ol), B)
+        rel = np.abs((r.X[0] - Xo[0]) + (r.X[1] - Xo[1])).max() / np.abs(Xo[0]).max()
+        assert rel < 1e20 * EPS_DD * 100
