@@ -182,6 +182,8 @@ struct CrtArgs {
     const unsigned long long *rmax, *cmax;
     mp_dd alpha, beta;
     int alpha_one, beta_zero;
+    int ab_mode;                          // 0 general; alpha = +-1 and beta = 0 (1) or 1 (2)
+    int alpha_neg;                        // alpha = -1 (modes 1, 2)
     double *ch, *cl;
     int64_t ldc;
     int tri;                              // 0: all of C; 1 / 2: upper / lower triangle
@@ -294,91 +296,122 @@ __device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale
     return mant_pow2(mant, q + scale);   // mant <= 2^53: exact
 }
 
+// One output entry (i, j) from the N products reduced mod p_b: the CRT sum,
+// its symmetric representative, the rounding to dd and the alpha/beta
+// epilogue.  T is a reference into the kernel's parameter block and every
+// modulus index below is a constant after unrolling, so the weights are
+// read straight from the constant bank (no per-term load).
 // NW: 32-bit words of the sums (P < 2^(32 (NW - 1)), and the sum of N
 // residues < 256 times the weights < P stays below 2^(32 NW)).
 template <int NW>
-__global__ void __launch_bounds__(256) crt_kernel(const CrtArgs p) {
-    if (p.info != nullptr && *p.info != 0) return;   // an earlier step failed
-    const PlanPick pk = plan_choice(p.plan);
-    if (pk.c < 0) return;                            // the plain kernel computes C
-    const int c = pk.c, N = pk.count, W = pk.width;
+__device__ __forceinline__ void crt_entry(const CrtArgs &p, const CrtTables &T, int N, int W,
+                                          int64_t i, int64_t j) {
+    // S = sum_b c_b w_b with 64-bit column sums, then carries; the products
+    // are read 8 moduli at a time, the 8 loads in flight together
+    const uint8_t *res = p.res + j * p.m_pad + i;
+    const int64_t plane = p.n_pad * p.m_pad;
+    // (and, for the quotient below, qf = sum_b c_b (inv_b / p_b) in fp32)
+    uint64_t acc[NW];
+#pragma unroll
+    for (int t = 0; t < NW; ++t) acc[t] = 0;
+    float qf = 0.0f;
+#pragma unroll
+    for (int b0 = 0; b0 < kMaxMod; b0 += 8) {
+        if (b0 >= N) break;
+        uint32_t cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cv[u] = b0 + u < N ? res[(b0 + u) * plane] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int b = b0 + u;                     // cv[u] = 0 past N
+#pragma unroll
+            for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * T.w[b][t];
+            qf = __fmaf_rn((float)cv[u], T.frac[b], qf);
+        }
+    }
+    // The symmetric representative is Z = S - q P with q the integer
+    // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| < k 2^(2W-2) <= P / 4,
+    // and the fp32 sum of the N <= 40 fractions (each term below 256, the
+    // sum below 10240) is off by less than 0.03, so rounding it gives q.
+    const uint64_t q = (uint64_t)(int64_t)rintf(qf);
+    // Z = S - q P in two's complement over NW words (exact: |Z| < 2^(32 NW - 1))
+    uint32_t S[NW];
+    {
+        uint64_t carry = 0, mc = 0, borrow = 0;
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            const uint64_t v = acc[t] + carry;
+            carry = v >> 32;
+            const uint64_t prod = q * T.P[t] + mc;
+            mc = prod >> 32;
+            const uint64_t d = (uint64_t)(uint32_t)v - (uint32_t)prod - borrow;
+            S[t] = (uint32_t)d;
+            borrow = (d >> 63) & 1;
+        }
+    }
+    // magnitude and sign
+    const bool negative = (S[NW - 1] & 0x80000000u) != 0;
+    if (negative) {
+        uint64_t c2 = 1;
+#pragma unroll
+        for (int t = 0; t < NW; ++t) {
+            const uint64_t v = (uint64_t)(uint32_t)~S[t] + c2;
+            S[t] = (uint32_t)v;
+            c2 = v >> 32;
+        }
+    }
+    const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * W;
+    uint32_t rem[NW], rem2[NW];
+    bool rem_neg, unused;
+    double vh = round_words(S, sc, rem, rem_neg);
+    double vl = round_words(rem, sc, rem2, unused);
+    if (rem_neg) vl = -vl;
+    if (negative) {
+        vh = -vh;
+        vl = -vl;
+    }
+    dd v{vh, vl};
+    const int64_t off = i + j * p.ldc;
+    switch (p.ab_mode) {
+        case 1:   // alpha = +-1, beta = 0: the product itself
+            if (p.alpha_neg) v = dd{-v.hi, -v.lo};
+            break;
+        case 2: {   // alpha = +-1, beta = 1 (every Cholesky update): one dd addition
+            const dd av = p.alpha_neg ? dd{-v.hi, -v.lo} : v;
+            v = add_sloppy(dd{p.ch[off], p.cl[off]}, av);
+            break;
+        }
+        default:
+            if (!p.beta_zero)
+                v = axpby_dd(dd{p.alpha.hi, p.alpha.lo}, v, dd{p.beta.hi, p.beta.lo},
+                             dd{p.ch[off], p.cl[off]});
+            else if (!p.alpha_one)
+                v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
+    }
+    p.ch[off] = v.hi;
+    p.cl[off] = v.lo;
+}
+
+template <int NW>
+__device__ __forceinline__ void crt_loop(const CrtArgs &p, const CrtTables &T, int N, int W) {
     const int64_t total = p.m * p.n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx % p.m, j = idx / p.m;
         if ((p.tri == 1 && i > j) || (p.tri == 2 && i < j)) continue;
-        // S = sum_b c_b w_b with 64-bit column sums, then carries; the
-        // products are read 8 moduli at a time, the 8 loads in flight together
-        const uint8_t *res = p.res + j * p.m_pad + i;
-        const int64_t plane = p.n_pad * p.m_pad;
-        // (and, for the quotient below, qf = sum_b c_b (inv_b / p_b) in fp32)
-        uint64_t acc[NW];
-#pragma unroll
-        for (int t = 0; t < NW; ++t) acc[t] = 0;
-        float qf = 0.0f;
-        for (int b0 = 0; b0 < N; b0 += 8) {
-            uint32_t cv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) cv[u] = b0 + u < N ? res[(b0 + u) * plane] : 0u;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int b = b0 + u < N ? b0 + u : 0;   // cv[u] = 0 past N
-#pragma unroll
-                for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * p.tab[c].w[b][t];
-                qf = __fmaf_rn((float)cv[u], p.tab[c].frac[b], qf);
-            }
-        }
-        // The symmetric representative is Z = S - q P with q the integer
-        // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| < k 2^(2W-2) <= P / 4,
-        // and the fp32 sum of the N <= 40 fractions (each term below 256, the
-        // sum below 10240) is off by less than 0.03, so rounding it gives q.
-        const uint64_t q = (uint64_t)(int64_t)rintf(qf);
-        // Z = S - q P in two's complement over NW words (exact: |Z| < 2^(32 NW - 1))
-        uint32_t S[NW];
-        {
-            uint64_t carry = 0, mc = 0, borrow = 0;
-#pragma unroll
-            for (int t = 0; t < NW; ++t) {
-                const uint64_t v = acc[t] + carry;
-                carry = v >> 32;
-                const uint64_t prod = q * p.tab[c].P[t] + mc;
-                mc = prod >> 32;
-                const uint64_t d = (uint64_t)(uint32_t)v - (uint32_t)prod - borrow;
-                S[t] = (uint32_t)d;
-                borrow = (d >> 63) & 1;
-            }
-        }
-        // magnitude and sign
-        const bool negative = (S[NW - 1] & 0x80000000u) != 0;
-        if (negative) {
-            uint64_t c2 = 1;
-#pragma unroll
-            for (int t = 0; t < NW; ++t) {
-                const uint64_t v = (uint64_t)(uint32_t)~S[t] + c2;
-                S[t] = (uint32_t)v;
-                c2 = v >> 32;
-            }
-        }
-        const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * W;
-        uint32_t rem[NW], rem2[NW];
-        bool rem_neg, unused;
-        double vh = round_words(S, sc, rem, rem_neg);
-        double vl = round_words(rem, sc, rem2, unused);
-        if (rem_neg) vl = -vl;
-        if (negative) {
-            vh = -vh;
-            vl = -vl;
-        }
-        dd v{vh, vl};
-        const int64_t off = i + j * p.ldc;
-        if (!p.beta_zero)
-            v = axpby_dd(dd{p.alpha.hi, p.alpha.lo}, v, dd{p.beta.hi, p.beta.lo},
-                         dd{p.ch[off], p.cl[off]});
-        else if (!p.alpha_one)
-            v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
-        p.ch[off] = v.hi;
-        p.cl[off] = v.lo;
+        crt_entry<NW>(p, T, N, W, i, j);
     }
+}
+
+// NW0..NW2: words of the sums for the three candidate widths.
+template <int NW0, int NW1, int NW2>
+__global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtArgs p) {
+    if (p.info != nullptr && *p.info != 0) return;   // an earlier step failed
+    const PlanPick pk = plan_choice(p.plan);
+    if (pk.c < 0) return;                            // the plain kernel computes C
+    if (pk.c == 0) crt_loop<NW0>(p, p.tab[0], pk.count, pk.width);
+    else if (pk.c == 1) crt_loop<NW1>(p, p.tab[1], pk.count, pk.width);
+    else crt_loop<NW2>(p, p.tab[2], pk.count, pk.width);
 }
 
 // ------------------------------------------------------------------ host
@@ -672,19 +705,26 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ca.ch = p.ch; ca.cl = p.cl; ca.ldc = p.ldc;
     ca.tri = p.tri;
     ca.info = p.info;
-    int nw = 0;
-    for (int c = 0; c < ncand; ++c) {
-        int nwc = 0;
-        if ((rc = crt_tables(counts[c], ca.tab[c], &nwc))) return rc;
-        nw = nwc > nw ? nwc : nw;
+    {
+        const bool a_pm1 = p.alpha.lo == 0.0 && (p.alpha.hi == 1.0 || p.alpha.hi == -1.0);
+        const bool b_one = p.beta.hi == 1.0 && p.beta.lo == 0.0;
+        ca.ab_mode = a_pm1 && p.beta_zero ? 1 : (a_pm1 && b_one ? 2 : 0);
+        ca.alpha_neg = p.alpha.hi < 0.0;
     }
+    int nw[kMaxCand] = {0, 0, 0};
+    for (int c = 0; c < ncand; ++c)
+        if ((rc = crt_tables(counts[c], ca.tab[c], &nw[c]))) return rc;
+    for (int c = ncand; c < kMaxCand; ++c) nw[c] = nw[ncand - 1];   // (never chosen)
     const int64_t total = p.m * p.n;
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
-    if (nw <= 8) crt_kernel<8><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    else if (nw == 9) crt_kernel<9><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    else if (nw == 10) crt_kernel<10><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    else crt_kernel<11><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    // the word counts that occur for k < 2^17: 9 at 112 bits, 9 or 10 at
+    // 120 bits, 10 at 128 bits (fewer words than allocated are zero-padded)
+    if (nw[0] > 9 || nw[1] > 10 || nw[2] > 10)
+        return fail(MP_DD_ERR_TOO_LARGE, "CRT word counts %d/%d/%d beyond the kernel's", nw[0],
+                    nw[1], nw[2]);
+    if (nw[1] <= 9) crt_kernel<9, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    else crt_kernel<9, 10, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
     if ((rc = check_launch("crt_kernel"))) return rc;
     rc = launch_plain_fallback(p, plan, st);
     sliced_timing_mark(3, st);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void plain_body(const GemmArgs &p, PlainSmem<R> &s) {
     if (p.info != nullptr && *p.info != 0) return;  // an earlier step failed
     // behind a split-precision call: compute only when its certificate failed
     if (p.gate != nullptr &&
-        *reinterpret_cast<const volatile unsigned long long *>(p.gate) >= p.gate_below)
+        *reinterpret_cast<const volatile unsigned int *>(p.gate) >= p.gate_below)
         return;
     int64_t bi, bj;
     tile_coords<BM, BN>(p, bi, bj);
@@ -272,6 +272,11 @@ int launch_plain_fallback(const GemmArgs &p, const SplitPlan &plan, cudaStream_t
     GemmArgs q = p;
     q.gate = plan.dmin;
     q.gate_below = plan.thr[plan.ncand - 1];
+    // with the gate closed every CTA returns at once, so the launch costs
+    // about its CTA count: take the 64 x 64 tiles whenever they fill the
+    // SMs twice (the result does not depend on the tile size)
+    const int64_t sms = sm_count() > 0 ? sm_count() : 152;
+    if (tile_count(q, 64) >= 2 * sms) return launch_r<4>(q, stream);
     return launch_gemm_plain(q, stream);
 }
 

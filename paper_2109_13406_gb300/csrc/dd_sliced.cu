@@ -40,6 +40,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <vector>
 
@@ -56,6 +57,10 @@ using namespace sm100;
 
 constexpr int TM = 128, TK = 64;            // tile rows and k-block
 constexpr int CHUNK_KB = 8;                 // k-blocks per exact fp32 run (512 products)
+// The magnitude product needs no exact runs (its fp32 sums only have to stay
+// within the certificate's safety factor): one run over the whole k.
+template <bool MAG>
+__host__ __device__ constexpr int chunk_kb() { return MAG ? (1 << 30) : CHUNK_KB; }
 constexpr int GROUP_N = 8;                  // tile columns per rasterisation group
 constexpr int kEpiCols = 64;                // accumulator columns per epilogue thread
 
@@ -218,15 +223,28 @@ __global__ void __launch_bounds__(128) slice_kernel(const double *__restrict__ X
         slice8<SB>(Xh, Xl, ld, row_contig, r, rows, l0, k, 8 * SB - e, D, rows_pad, k_pad);
 }
 
-// x 2^s for x >= 0, exact while the result is normal; in two steps so that
-// every power of two is a normal binary64.  rd: round toward zero when the
-// result leaves the normal range (a lower bound, as the certificate needs).
-__device__ __forceinline__ double pow2_step(int s) {
-    return __longlong_as_double((long long)(s + 1023) << 52);   // -1022 <= s <= 1023
-}
-__device__ __forceinline__ double scale2_rd(double x, int s) {
-    const int s1 = s / 2, s2 = s - s1;
-    return __dmul_rd(__dmul_rd(x, pow2_step(s1)), pow2_step(s2));
+// The largest bf16 not above |v| 2^-e, as its bit pattern, for finite v
+// with |v| 2^-e < 1/2, from the binary64 fields with integer operations
+// only (the FP64 pipe is the slow one): truncate the significand to 8 bits
+// (bf16 normal range, exponents >= -126) or to a multiple of 2^-133 (bf16
+// subnormals; 0 below).
+__device__ __forceinline__ uint16_t bf16_floor_scaled(double v, int e) {
+    const unsigned long long u =
+        (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+    if (u == 0) return 0;
+    int E = (int)(u >> 52);
+    unsigned long long m = u & ((1ull << 52) - 1);
+    if (E == 0) {                               // binary64 subnormal: normalise
+        const int sh = __clzll((long long)m) - 11;
+        m <<= sh;
+        E = 1 - sh;
+    } else {
+        m |= 1ull << 52;
+    }
+    const int x = E - 1023 - e;                 // |v| 2^-e = m 2^(x - 52), m in [2^52, 2^53)
+    if (x >= -126) return (uint16_t)(((x + 127) << 7) | (int)((m >> 45) & 0x7F));
+    const int s = -81 - x;                      // 52 - (x + 133): multiples of 2^-133
+    return s >= 53 ? (uint16_t)0 : (uint16_t)(m >> s);
 }
 
 // Magnitude planes of the certificate: M[r][l] = the largest bf16 not above
@@ -243,16 +261,13 @@ __global__ void __launch_bounds__(128) magnitude_kernel(
     if (r >= rows_pad) return;
     const int64_t l0 = (int64_t)blockIdx.y * 16 + 8 * (threadIdx.x & 1);
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
-    __nv_bfloat16 out[8];
+    uint16_t out[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int64_t l = l0 + q;
         double v = 0.0;
-        if (r < rows && l < k)
-            v = fabs(Xh[row_contig ? (r + l * ld) : (l + r * ld)]);
-        // |hi| 2^-e < 1/2: exact unless subnormal, where it rounds toward zero;
-        // then two roundings toward zero to fp32 and to bf16
-        out[q] = __float2bfloat16_rz(__double2float_rz(scale2_rd(v, -e)));
+        if (r < rows && l < k) v = Xh[row_contig ? (r + l * ld) : (l + r * ld)];
+        out[q] = bf16_floor_scaled(v, e);
     }
     uint4 w;
     memcpy(&w, out, 16);
@@ -296,47 +311,79 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, 
     if ((p.tri == 1 && r0 > c0 + TN - 1) || (p.tri == 2 && r0 + TM - 1 < c0)) b1 = b0;
 }
 
-constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+constexpr unsigned int kInfBits32 = 0x7F800000u;   // +inf as fp32 bits
+
+// A lower bound of |c| 2^-s (c a finite binary64, s an integer) as an fp32:
+// the significand truncated to 24 bits and the exponent shifted; 0 below
+// the fp32 normal range, the largest finite fp32 above it; +inf for an
+// infinite or NaN c (such an entry does not constrain the certificate).
+__device__ __forceinline__ float scaled_floor_f32(double c, int s) {
+    const unsigned long long u =
+        (unsigned long long)__double_as_longlong(c) & 0x7FFFFFFFFFFFFFFFull;
+    const int E = (int)(u >> 52);
+    if (E == 0x7FF) return __int_as_float(0x7F800000);
+    if (E == 0) return 0.0f;                    // subnormal c: its part is dropped
+    const int x = E - 1023 - s;                 // exponent of |c| 2^-s
+    if (x < -126) return 0.0f;
+    if (x > 127) return __int_as_float(0x7F7FFFFF);
+    return __int_as_float(((x + 127) << 23) | (int)((u >> 29) & 0x7FFFFF));
+}
 
 // Certificate margin of the entries (i, j0 .. j0 + kEpiCols - 1) from their
 // fp32 magnitude sums s_ij (bit patterns in acc):
 //   d_ij = s_ij c1 + r |c_ij| 2^-(e_i + f_j),  r <= |beta / alpha|,
-// each step rounded toward zero, so d_ij is at most the exact margin of a
-// lower bound of (|A||B|)_ij.  Rows or columns that are all zero (exact in
-// every form), entries outside C or the requested triangle, and NaN margins
-// (a NaN in C, whose result is NaN anyway) do not constrain.  The minimum
-// over the warp goes to *dmin_out with one atomic.
+// in fp32 with every step rounded toward zero, so d_ij is at most the exact
+// margin of a lower bound of (|A||B|)_ij.  Rows or columns that are all zero
+// (exact in every form), entries outside C or the requested triangle, and
+// entries whose C is infinite or NaN (then so is the result) do not
+// constrain.  Called by all 32 lanes of an epilogue warp (rows i of the
+// lanes, the same 64 columns): each lane loads two column maxima and the
+// warp shares them by shuffles; C is read in groups of 16 independent loads.
+// The minimum over the warp goes to *dmin_out with one atomic.
 __device__ __forceinline__ void certificate_margin(const BandArgs &p,
                                                    const int32_t (&acc)[kEpiCols], int64_t i,
                                                    int64_t j0) {
-    unsigned long long dm = kInfBits;
-    if (i < p.m) {
-        const unsigned long long rm = p.rmax[i];
-        const int ei = scale_exponent(rm);
+    static_assert(kEpiCols == 64, "two column maxima per lane");
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    int fcol[2];
+    bool zcol[2];
 #pragma unroll
-        for (int jj = 0; jj < kEpiCols; ++jj) {
+    for (int h = 0; h < 2; ++h) {
+        const int64_t j = j0 + 32 * h + lane;
+        const unsigned long long cm = j < p.n ? p.cmax[j] : 0ull;
+        zcol[h] = cm == 0;
+        fcol[h] = scale_exponent(cm);
+    }
+    const unsigned long long rm = i < p.m ? p.rmax[i] : 0ull;
+    const bool row_ok = rm != 0;
+    const int ei = scale_exponent(rm);
+    const bool use_c = p.ba_ratio32 > 0.0f;
+    unsigned int dm = kInfBits32;
+#pragma unroll
+    for (int g = 0; g < kEpiCols / 16; ++g) {
+        double cv[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int64_t j = j0 + 16 * g + u;
+            cv[u] = (use_c && row_ok && j < p.n) ? p.ch[i + j * p.ldc] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int jj = 16 * g + u;
             const int64_t j = j0 + jj;
-            const bool inside = rm != 0 && j < p.n && !(p.tri == 1 && i > j) &&
+            const int fj = __shfl_sync(mask, fcol[jj / 32], jj % 32);
+            const bool zj = __shfl_sync(mask, (int)zcol[jj / 32], jj % 32) != 0;
+            float d = __fmul_rz(__int_as_float(acc[jj]), p.c1);
+            if (use_c) d = __fadd_rz(d, __fmul_rz(scaled_floor_f32(cv[u], ei + fj), p.ba_ratio32));
+            const bool inside = row_ok && !zj && j < p.n && !(p.tri == 1 && i > j) &&
                                 !(p.tri == 2 && i < j);
-            if (!inside) continue;
-            const unsigned long long cm = p.cmax[j];
-            if (cm == 0) continue;
-            double d = __dmul_rd((double)__int_as_float(acc[jj]), p.c1);
-            if (p.ba_ratio > 0.0) {
-                const double t = __dmul_rd(fabs(p.ch[i + j * p.ldc]), p.ba_ratio);
-                d = __dadd_rd(d, scale2_rd(t, -(ei + scale_exponent(cm))));
-            }
-            const unsigned long long db = (unsigned long long)__double_as_longlong(d);
-            if (d >= 0.0 && db < dm) dm = db;
+            const unsigned int db = __float_as_uint(d);
+            dm = (inside && db < dm) ? db : dm;
         }
     }
-    const unsigned mask = __activemask();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(mask, dm, o);
-        dm = v < dm ? v : dm;
-    }
-    if ((threadIdx.x & 31) == 0 && dm != kInfBits) atomicMin(p.dmin_out, dm);
+    dm = __reduce_min_sync(mask, dm);
+    if (lane == 0 && dm != kInfBits32) atomicMin(p.dmin_out, dm);
 }
 
 // MAG: the certificate's magnitude product (bf16 operands, fp32 sums, the
@@ -453,8 +500,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                         for (int kb = 0; kb < KB; ++kb, ++it, ++sidx) {
                             const int s = it % STAGES;
                             const uint32_t f = it / STAGES;
-                            const bool first = (sidx % CHUNK_KB) == 0;
-                            const bool last = ((sidx + 1) % CHUNK_KB) == 0 || sidx + 1 == steps;
+                            const bool first = (sidx % chunk_kb<MAG>()) == 0;
+                            const bool last =
+                                ((sidx + 1) % chunk_kb<MAG>()) == 0 || sidx + 1 == steps;
                             const uint32_t buf = chunk & 1, use = chunk >> 1;
                             if (first) {
                                 if (!mbar_wait(&acce[buf], (use & 1) ^ 1, abort_flag)) {
@@ -507,7 +555,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
                 const int steps = (p.diag ? 1 : b + 1) * KB;
-                const int nchunks = (steps + CHUNK_KB - 1) / CHUNK_KB;
+                const int nchunks = (steps + chunk_kb<MAG>() - 1) / chunk_kb<MAG>();
                 for (int c = 0; c < nchunks; ++c, ++chunk) {
                     const uint32_t buf = chunk & 1, use = chunk >> 1;
                     if (!mbar_wait(&accf[buf], use & 1, abort_flag)) {
@@ -869,8 +917,8 @@ int sliced_magnitude_offsets(int64_t m, int64_t n, int64_t k, int S, size_t *off
 
 // ------------------------------------------------------------------ certificate (host)
 
-SplitPlan make_plan(SplitHeader *h, unsigned long long *dmin_dev, int form, int64_t k,
-                    int ncand, const int *widths, const int *counts, const double *cst) {
+SplitPlan make_plan(SplitHeader *h, unsigned int *dmin_dev, int form, int64_t k, int ncand,
+                    const int *widths, const int *counts, const double *cst) {
     SplitPlan pl{};
     pl.dmin = dmin_dev;
     pl.ncand = ncand;
@@ -878,13 +926,16 @@ SplitPlan make_plan(SplitHeader *h, unsigned long long *dmin_dev, int form, int6
     h->form = form;
     h->ncand = ncand;
     h->k = k;
-    h->dmin = 0x7FF0000000000000ull;   // +inf until the magnitude product lowers it
+    h->dmin = 0x7F800000u;   // +inf until the magnitude product lowers it
     for (int c = 0; c < ncand; ++c) {
-        // cst 2^(106 - W) / 12, rounded up: the power of two is exact, the
-        // quotient is within 2^-53 of itself, and 1 + 2^-50 covers that
-        double t = std::ldexp(cst[c], 106 - widths[c]) / 12.0 * (1.0 + 0x1p-50);
-        unsigned long long bits;
-        memcpy(&bits, &t, 8);
+        // cst 2^(106 - W) / 12 rounded up to fp32: the power of two is exact,
+        // the binary64 quotient is within 2^-53 of itself, (1 + 2^-50) covers
+        // that, and the conversion to fp32 rounds up (to +inf if too large)
+        const double t = std::ldexp(cst[c], 106 - widths[c]) / 12.0 * (1.0 + 0x1p-50);
+        float f = (float)t;
+        if ((double)f < t) f = std::nextafter(f, std::numeric_limits<float>::infinity());
+        unsigned int bits;
+        memcpy(&bits, &f, 4);
         pl.thr[c] = h->thr[c] = bits;
         pl.count[c] = h->count[c] = counts[c];
         pl.width[c] = h->width[c] = widths[c];
@@ -943,10 +994,20 @@ int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int
     ba.cmax = cmax;
     ba.ch = p.ch;
     ba.ba_ratio = p.beta_zero ? 0.0 : ratio_lower(p.beta, p.alpha);
-    // the fp32 sums of non-negative products are at most (1 + k 2^-21) above
-    // the exact sums of the bf16 products (see the accumulation argument of
-    // the certificate), and |hi| is within 2^-53 of |hi + lo|
-    ba.c1 = 1.0 - (double)(p.k + 1) * 0x1p-20;
+    {   // rounded toward zero to fp32
+        float f = (float)ba.ba_ratio;
+        if ((double)f > ba.ba_ratio) f = std::nextafter(f, 0.0f);
+        ba.ba_ratio32 = f;
+    }
+    // Safety factor of the fp32 sums.  Each bf16 x bf16 product is exact
+    // (16 significant bits) or, flushed, smaller; the k products are
+    // non-negative, so each fp32 addition raises the running sum by at most
+    // 2^-23 of the final sum (round to nearest: 2^-24; truncation lowers it),
+    // and the computed sum is at most (1 + k 2^-23) times the exact one.
+    // With |hi| >= (1 - 2^-53) |hi + lo| as well, multiplying by
+    // 1 - (k+1) 2^-20 (exact in fp32 for k < 2^17) leaves a lower bound of
+    // (|A||B|)_ij 2^-(e_i+f_j) with an eightfold margin on the additions.
+    ba.c1 = (float)(1.0 - (double)(p.k + 1) * 0x1p-20);
     ba.dmin_out = &hdr->dmin;
     return launch_band(tmA, tmB, ba, TN, st);
 }
@@ -1050,39 +1111,33 @@ int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStr
 
 namespace {
 
-template <bool MAG>
-void set_band_attrs() {
-    cudaFuncSetAttribute(band_gemm_kernel<128, MAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BandCfg<128>::SMEM);
-    cudaFuncSetAttribute(band_gemm_kernel<256, MAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)BandCfg<256>::SMEM);
-}
-
-template <bool MAG>
-void launch_band_t(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
-                   int grid, cudaStream_t st) {
-    if (TN == 256)
-        band_gemm_kernel<256, MAG><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(
-            tmA, tmB, ba);
-    else
-        band_gemm_kernel<128, MAG><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
-            tmA, tmB, ba);
-}
-
 }  // namespace
 
 int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
                 cudaStream_t st) {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
-        set_band_attrs<false>();
-        set_band_attrs<true>();
+        cudaFuncSetAttribute(band_gemm_kernel<128, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
+        cudaFuncSetAttribute(band_gemm_kernel<256, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<256>::SMEM);
+        cudaFuncSetAttribute(band_gemm_kernel<128, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
     });
     const int tiles = ba.tiles_m * ba.tiles_n;
     const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords (S: the most bands)
     const int grid = items < sm_count() ? items : sm_count();
-    if (ba.mag) launch_band_t<true>(tmA, tmB, ba, TN, grid, st);
-    else launch_band_t<false>(tmA, tmB, ba, TN, grid, st);
+    // (the magnitude product always runs on 128-wide tiles)
+    if (ba.mag && TN != 128) return fail(MP_DD_ERR_TOO_LARGE, "magnitude product: tile width");
+    if (ba.mag)
+        band_gemm_kernel<128, true><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
+            tmA, tmB, ba);
+    else if (TN == 256)
+        band_gemm_kernel<256, false><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(
+            tmA, tmB, ba);
+    else
+        band_gemm_kernel<128, false><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
+            tmA, tmB, ba);
     return check_launch("band_gemm_kernel");
 }
 
@@ -1103,8 +1158,9 @@ int split_report(const void *ws, mp_dd_split_info *info) {
     *info = mp_dd_split_info{};
     info->status = h.status;
     info->form = h.form;
-    double dmin;
-    memcpy(&dmin, &h.dmin, 8);
+    float dmin32;
+    memcpy(&dmin32, &h.dmin, 4);
+    const double dmin = dmin32;
     info->dmin = dmin;
     if (h.form == 0 || h.ncand < 1 || h.ncand > kMaxCand) {
         info->max_err_est = 0.0;   // no product formed: C := beta C, as the plain path
@@ -1122,8 +1178,9 @@ int split_report(const void *ws, mp_dd_split_info *info) {
         info->max_err_est = 0.5 + fin;
         return 0;
     }
-    double thr;
-    memcpy(&thr, &h.thr[c], 8);
+    float thr32;
+    memcpy(&thr32, &h.thr[c], 4);
+    const double thr = thr32;
     info->width_bits = h.width[c];
     info->count = h.count[c];
     // operand rounding: cst 2^(106 - W) / (16 dmin) = (3/4) thr / dmin

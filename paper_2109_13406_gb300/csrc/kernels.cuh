@@ -35,8 +35,8 @@ struct GemmArgs {
     // Fallback of a split-precision call: when gate != nullptr the kernel
     // computes C only if *gate (the call's certificate margin, as bits) is
     // below gate_below, i.e. when no operand width certified the bound.
-    const unsigned long long *gate = nullptr;
-    unsigned long long gate_below = 0;
+    const unsigned int *gate = nullptr;
+    unsigned int gate_below = 0;
 };
 
 // Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).

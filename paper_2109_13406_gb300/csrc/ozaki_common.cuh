@@ -28,10 +28,11 @@ namespace mpdd {
 // for every entry, L_ij a lower bound of (|A||B|)_ij.  L comes from one
 // tensor-core product of magnitude planes |hi| 2^-e rounded toward zero to
 // bf16, accumulated in fp32 and scaled by (1 - (k+1) 2^-20) (see the
-// magnitude kernel and the band kernel's magnitude mode); the smallest d_ij
-// of the call is kept in the workspace header (its bit pattern: non-negative
-// doubles order like their bits).  Every later kernel of the call derives
-// the same decision from it with plan_choice().
+// magnitude kernel and the band kernel's magnitude mode); d_ij is formed in
+// fp32 with every step rounded toward zero, and the smallest d_ij of the
+// call is kept in the workspace header as its fp32 bit pattern
+// (non-negative floats order like their bits).  Every later kernel of the
+// call derives the same decision from it with plan_choice().
 constexpr int kMaxCand = 3;
 
 // Workspace header (the first bytes of every split-precision workspace).
@@ -40,9 +41,10 @@ struct SplitHeader {
     int form;                          // 1 digit slices, 2 residues; 0: no product formed
     int ncand;                         // candidate widths, ascending
     int reserved;
-    unsigned long long dmin;           // bits of min_ij d_ij (+inf: no entry constrains)
+    unsigned int dmin;                 // fp32 bits of min_ij d_ij (+inf: no entry constrains)
+    unsigned int reserved2;
     long long k;
-    unsigned long long thr[kMaxCand];  // bits of cst_c 2^(106 - W_c) / 12, rounded up
+    unsigned int thr[kMaxCand];        // fp32 bits of cst_c 2^(106 - W_c) / 12, rounded up
     int count[kMaxCand];               // slices or moduli of candidate c
     int width[kMaxCand];               // W_c in bits
 };
@@ -51,8 +53,8 @@ struct SplitHeader {
 // least thr[c] (the first such c, i.e. the narrowest width); -1: none, the
 // plain kernel computes the product.
 struct SplitPlan {
-    const unsigned long long *dmin;    // header word; nullptr: no certificate (count[0])
-    unsigned long long thr[kMaxCand];
+    const unsigned int *dmin;          // header word; nullptr: no certificate (count[0])
+    unsigned int thr[kMaxCand];
     int count[kMaxCand];
     int width[kMaxCand];
     int ncand;
@@ -66,7 +68,7 @@ struct PlanPick {
 // kernel's parameter space instead of being copied to local memory.)
 __device__ __forceinline__ PlanPick plan_choice(const SplitPlan &pl) {
     if (pl.dmin == nullptr) return PlanPick{0, pl.count[0], pl.width[0]};
-    const unsigned long long d = *reinterpret_cast<const volatile unsigned long long *>(pl.dmin);
+    const unsigned int d = *reinterpret_cast<const volatile unsigned int *>(pl.dmin);
     PlanPick r{-1, 0, 0};
 #pragma unroll
     for (int c = kMaxCand - 1; c >= 0; --c)
@@ -100,8 +102,9 @@ struct BandArgs {
     const unsigned long long *rmax, *cmax;
     const double *ch;          // hi plane of C (read when ba_ratio > 0)
     double ba_ratio;           // lower bound of |beta| / |alpha|, 0 when beta = 0
-    double c1;                 // 1 - (k + 1) 2^-20: the fp32 sums' safety factor
-    unsigned long long *dmin_out;
+    float c1;                  // 1 - (k + 1) 2^-20 (exact in fp32): the sums' safety factor
+    float ba_ratio32;          // ba_ratio rounded toward zero to fp32
+    unsigned int *dmin_out;
 };
 
 // Host launchers shared by the two forms (defined in dd_sliced.cu).
@@ -119,7 +122,7 @@ int band_tn(int64_t m, int64_t n);
 // residues; widths[c] / counts[c] / cst[c] the candidates (ascending width)
 // and their per-product error constants.  make_plan also fills the header
 // image that the first magnitude launch writes (init != nullptr).
-SplitPlan make_plan(SplitHeader *hdr_image, unsigned long long *dmin_dev, int form, int64_t k,
+SplitPlan make_plan(SplitHeader *hdr_image, unsigned int *dmin_dev, int form, int64_t k,
                     int ncand, const int *widths, const int *counts, const double *cst);
 int launch_magnitude(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
                      int64_t rows_pad, int64_t k_pad, const unsigned long long *rmax, void *M,
