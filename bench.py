@@ -359,9 +359,13 @@ def fp64_peak_line(r64):
     return 2.0 * r64 / 15.0 / 1e9
 
 
-def plain_section(mp, torch, size, problems, r64):
+def plain_section(mp, torch, size, problems, r64, rmac=None):
     """The plain FP64 path on the step's three problems, one call each timed
-    with CUDA events (after the split-precision runs on the same inputs)."""
+    with CUDA events (after the split-precision runs on the same inputs).
+    Fractions: of 2 R64 / 15 (the survey's accounting, R64 the measured FP64
+    FMA rate), of the FP64 pipe at the kernel's 12.75 instructions per
+    multiply-add, and of the measured rate of the kernel's own multiply-add
+    mix with operands in registers (mp_dd_peak_ddmac)."""
     nn, tn, syrk, dnn, dtn, dsy = problems
     st = torch.cuda.current_stream()
     flops = plain_flops(size)
@@ -387,7 +391,8 @@ def plain_section(mp, torch, size, problems, r64):
         instr = FP64_OPS_PER_MAC * macs / (ms * 1e-3)
         out[nm] = {"ms": ms, "dd_GFlops": gf,
                    "frac_of_2R64_over_15": gf / ceiling if ceiling else None,
-                   "fp64_pipe_frac": instr / r64 if r64 else None}
+                   "fp64_pipe_frac": instr / r64 if r64 else None,
+                   "frac_of_mac_mix_ceiling": gf / (2.0 * rmac / 1e9) if rmac else None}
     return out
 
 
@@ -480,6 +485,7 @@ def run_default(args):
     torch.cuda.synchronize()
     r64 = mp.mp_dd_peak_fp64()
     r8 = mp.mp_dd_peak_imma()
+    rmac = mp.mp_dd_peak_ddmac()
     ranks.barrier()
     torch.cuda.synchronize()
     mp.mp_dd_sliced_timing(True)      # per-call phase events on this stream
@@ -528,7 +534,7 @@ def run_default(args):
                 "traffic_note": "dram__bytes_read.sum + write.sum of one launch (ncu); null "
                                 "when the kernel changed since the capture"}
     e2e = None if args.no_e2e else certified_e2e(args, mp, torch, problems, ws, ranks)
-    plain = plain_section(mp, torch, size, problems, r64)
+    plain = plain_section(mp, torch, size, problems, r64, rmac)
     del problems, calls, ws
     torch.cuda.empty_cache()
     sections = {}
@@ -550,7 +556,9 @@ def run_default(args):
             "config1_8192_plain": {
                 nm: {"ms": _sig(v["ms"]), "dd_GFlops": _sig(v["dd_GFlops"]),
                      "frac_of_2R64_over_15": _sig(v["frac_of_2R64_over_15"]),
-                     "fp64_pipe_frac": _sig(v["fp64_pipe_frac"])} for nm, v in plain.items()},
+                     "fp64_pipe_frac": _sig(v["fp64_pipe_frac"]),
+                     "frac_of_mac_mix": _sig(v["frac_of_mac_mix_ceiling"])}
+                for nm, v in plain.items()},
             "certified_over_plain": _sig(plain["Rgemm_NN"]["ms"] / per["Rgemm_NN"]["ms"]),
         }
         if sections:
@@ -587,7 +595,9 @@ def run_default(args):
                              "L2, no flush", "parallelism": f"replicas x{world}"},
             "per_call": per,
             "measured_peaks": {"fp64_instr_per_s": r64, "imma_int8_ops_per_s": r8,
-                               "plain_ceiling_dd_GFlops_2R64_over_15": gemm_ceiling},
+                               "dd_mac_mix_per_s": rmac,
+                               "plain_ceiling_dd_GFlops_2R64_over_15": gemm_ceiling,
+                               "plain_mac_mix_ceiling_dd_GFlops": 2.0 * rmac / 1e9},
             "plain_fp64_8192": plain,
             "sections": sections,
             "cpu_baseline": cpu,

@@ -629,6 +629,14 @@ int mp_dd_peak_fp64(double *rate);
  * fp16 tcgen05 path is compared.  Synchronous.  Returns 0 or an error. */
 int mp_dd_peak_imma(double *rate);
 
+/* Time the plain kernel's dd multiply-add (the same operation sequence, 4 x 4
+ * accumulators per thread, renormalised every 4 steps) on operands that stay
+ * in registers and change every step by integer operations only, filling
+ * every SM, and report the rate in dd multiply-adds per second in *rate: the
+ * ceiling of the plain kernel's instruction mix on this GPU's FP64 pipe
+ * (twice it in dd-flop/s).  Synchronous.  Returns 0 or an error. */
+int mp_dd_peak_ddmac(double *rate);
+
 #ifdef __cplusplus
 }
 #endif

@@ -783,4 +783,12 @@ int mp_dd_peak_imma(double *rate) {
     return run_peak_imma(tls().stream, rate);
 }
 
+int mp_dd_peak_ddmac(double *rate) {
+    clear_error();
+    if (rate == nullptr) return fail(-1, "peak_ddmac: rate is NULL");
+    int rc = require_device();
+    if (rc) return rc;
+    return run_peak_ddmac(tls().stream, rate);
+}
+
 }  // extern "C"

@@ -75,6 +75,29 @@ constexpr ModWeights make_mod_weights() {
 
 __constant__ ModWeights c_mod_weights = make_mod_weights();
 
+// The same weights, each duplicated into both halves of a float2, with the
+// packed constants of the quotient step: the residue kernel works on two
+// entries at once with the packed fp32 instructions (f32x2), whose lanes are
+// the same IEEE operations as the scalar ones.
+struct ModWeights2 {
+    float2 w[kMaxMod][kMaxDigits];
+    float2 inv[kMaxMod];
+    float2 negp[kMaxMod];
+};
+
+constexpr ModWeights2 make_mod_weights2() {
+    ModWeights2 m{};
+    const ModWeights s = make_mod_weights();
+    for (int i = 0; i < kMaxMod; ++i) {
+        for (int t = 0; t < kMaxDigits; ++t) m.w[i][t] = float2{s.w[i][t], s.w[i][t]};
+        m.inv[i] = float2{s.inv[i], s.inv[i]};
+        m.negp[i] = float2{-(float)modulus(i), -(float)modulus(i)};
+    }
+    return m;
+}
+
+__constant__ ModWeights2 c_mod_weights2 = make_mod_weights2();
+
 // 4 threads per (row, 16 consecutive k), 4 entries each, one 8-byte store
 // per residue plane and thread (a quad of lanes writes one 32-byte sector).
 // Residues from the balanced digits d_t of X on the FP32 pipe:
@@ -95,52 +118,59 @@ __device__ __forceinline__ void residue_body(
     const int64_t l0 = (int64_t)blockIdx.y * 16 + 4 * (threadIdx.x & 3);
     const int e = r < rows ? scale_exponent(rmax[r]) : 0;
     const int shift = 8 * DG - e;
-    float df[4][DG];
+    // digits of the entry pairs (l0, l0 + 1) and (l0 + 2, l0 + 3), packed
+    float2 d2[2][DG];
+    int lowest[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t l = l0 + q;
-        double hi = 0.0, lo = 0.0;
-        if (r < rows && l < k) {
-            const int64_t off = row_contig ? (r + l * ld) : (l + r * ld);
-            hi = Xh[off];
-            lo = Xl[off];
+    for (int h = 0; h < 2; ++h) {
+        int dg[2][DG];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t l = l0 + 2 * h + u;
+            double hi = 0.0, lo = 0.0;
+            if (r < rows && l < k) {
+                const int64_t off = row_contig ? (r + l * ld) : (l + r * ld);
+                hi = Xh[off];
+                lo = Xl[off];
+            }
+            dd_digits<DG>(hi, lo, shift, dg[u]);
+            lowest[2 * h + u] = dg[u][DG - 1];
         }
-        int dg[DG];
-        dd_digits<DG>(hi, lo, shift, dg);
-        // d as a float without a conversion instruction: the bits of 2^23 + 128 + d
-        // (exact, d in [-128, 128]) minus 2^23 + 128
+        // d as a float without a conversion instruction: the bits of
+        // 2^23 + 128 + d (exact, d in [-128, 128]) minus 2^23 + 128
 #pragma unroll
         for (int t = 0; t < DG; ++t)
-            df[q][t] = __fsub_rn(__int_as_float(0x4B000000 + 128 + dg[t]), 8388736.0f);
+            d2[h][t] = __fadd2_rn(float2{__int_as_float(0x4B000000 + 128 + dg[0][t]),
+                                         __int_as_float(0x4B000000 + 128 + dg[1][t])},
+                                  float2{-8388736.0f, -8388736.0f});
     }
-    // plane 0 (p = 256): the lowest digits; two fp16 per conversion
+    // plane 0 (p = 256): the lowest digits, exact in fp16
     {
-        const __half2 h01 = __floats2half2_rn(df[0][DG - 1], df[1][DG - 1]);
-        const __half2 h23 = __floats2half2_rn(df[2][DG - 1], df[3][DG - 1]);
+        const __half2 h01 = __floats2half2_rn((float)lowest[0], (float)lowest[1]);
+        const __half2 h23 = __floats2half2_rn((float)lowest[2], (float)lowest[3]);
         *reinterpret_cast<uint2 *>(R + r * k_pad + l0) =
             make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
                        *reinterpret_cast<const uint32_t *>(&h23));
     }
+    const float2 magic{12582912.0f, 12582912.0f}, nmagic{-12582912.0f, -12582912.0f};
 #pragma unroll
     for (int i = 1; i < 2 * NP; ++i) {
         if (i >= N) break;
-        const float p = (float)modulus(i), inv = c_mod_weights.inv[i];
-        float res[4];
+        uint32_t packed[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float s = 0.0f;
+        for (int h = 0; h < 2; ++h) {
+            float2 s2{0.0f, 0.0f};
 #pragma unroll
             for (int t = 0; t < DG; ++t)
-                s = __fmaf_rn(df[q][t], c_mod_weights.w[i][kMaxDigits - DG + t], s);
+                s2 = __ffma2_rn(d2[h][t], c_mod_weights2.w[i][kMaxDigits - DG + t], s2);
             // rint(s / p) by the 1.5 2^23 shift (|s / p| < 2^22), then the residue
-            const float qn = __fsub_rn(__fmaf_rn(s, inv, 12582912.0f), 12582912.0f);
-            res[q] = __fmaf_rn(-p, qn, s);
+            const float2 qn = __fadd2_rn(__ffma2_rn(s2, c_mod_weights2.inv[i], magic), nmagic);
+            const float2 res = __ffma2_rn(c_mod_weights2.negp[i], qn, s2);
+            const __half2 hv = __float22half2_rn(res);
+            packed[h] = *reinterpret_cast<const uint32_t *>(&hv);
         }
-        const __half2 h01 = __floats2half2_rn(res[0], res[1]);
-        const __half2 h23 = __floats2half2_rn(res[2], res[3]);
         *reinterpret_cast<uint2 *>(R + ((int64_t)i * rows_pad + r) * k_pad + l0) =
-            make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
-                       *reinterpret_cast<const uint32_t *>(&h23));
+            make_uint2(packed[0], packed[1]);
     }
 }
 

@@ -46,6 +46,8 @@ int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream);
 int run_peak_fp64(cudaStream_t stream, double *rate);
 // INT8 warp-level tensor rate (mma.sync m16n8k32 s8); *rate in integer ops/s.
 int run_peak_imma(cudaStream_t stream, double *rate);
+// dd multiply-add rate of the plain kernel's instruction mix (registers only).
+int run_peak_ddmac(cudaStream_t stream, double *rate);
 
 // Split-precision (sliced) Rgemm on the fp16 tensor cores.
 constexpr int kDefaultSlices = 14;  // base-256 digits per operand entry

@@ -183,3 +183,10 @@ def test_imma_peak_is_positive(cuda_lib):
     """The warp-level INT8 tensor rate (mma.sync m16n8k32) is measurable."""
     r = cuda_lib.mp_dd_peak_imma()
     assert r > 1e12
+
+
+def test_ddmac_peak_is_positive(cuda_lib):
+    """The plain kernel's multiply-add mix rate is measurable and below the
+    FP64 issue rate divided by the 12 FP64 instructions it needs at least."""
+    r = cuda_lib.mp_dd_peak_ddmac()
+    assert 1e9 < r < cuda_lib.mp_dd_peak_fp64() / 10
