@@ -132,6 +132,19 @@ int mp_dd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, in
                 mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb, mp_dd beta,
                 mp_dd_mat C, int64_t ldc);
 
+/* Operand staging of the plain Rgemm / Rsyrk kernel (no counterpart in the
+ * manual; process-wide, for tuning and testing).  mode 0 (the default):
+ * Rgemm products large enough for 64 x 64 output tiles whose A and B planes
+ * start on 16-byte boundaries with even leading dimensions are computed by
+ * a kernel whose op(A) / op(B) panels arrive by TMA tile copies into a ring
+ * of shared-memory stages (mbarrier-synchronised, one producer warp, eight
+ * computing warps); the others (thin products, the Rsyrk triangle) by the
+ * register-staged kernels on the tile size that fills the SMs best.  mode 1: register staging only.  mode 2: TMA
+ * staging wherever its alignment rules allow, whatever the size.  Every
+ * mode gives bitwise the same results (the per-entry operation sequence is
+ * the same).  Returns 0, or -1 for another mode. */
+int mp_dd_set_plain_staging(int mode);
+
 /* Rsyrk (Sec. 6 table; CUDA dd Rsyrk in Sec. 7.3):
  *
  *     C := alpha * A * A^T + beta * C   (trans N, A is n x k), or

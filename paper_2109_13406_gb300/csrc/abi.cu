@@ -767,6 +767,13 @@ int mp_dd_elementwise(const char *op, int64_t n, mp_dd_cmat x, mp_dd_cmat y, mp_
     return run_dd_elementwise(code, n, x.hi, x.lo, y.hi, y.lo, z.hi, z.lo, tls().stream);
 }
 
+int mp_dd_set_plain_staging(int mode) {
+    clear_error();
+    if (mode < 0 || mode > 2) return fail(-1, "set_plain_staging: mode must be 0, 1 or 2");
+    set_plain_staging(mode);
+    return 0;
+}
+
 int mp_dd_peak_fp64(double *rate) {
     clear_error();
     if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");

@@ -12,7 +12,8 @@
 //
 // On GB300 the FP64 pipe is the bottleneck by a wide margin (12.75 FP64
 // instructions per dd multiply-add), so the kernel is organised to keep that
-// pipe busy and nothing else: each CTA owns a 16R x 16R tile of C (R = 4, 2
+// pipe busy and nothing else (large plain products go to the TMA-staged form
+// of this kernel, dd_gemm_tma.cu, whose per-entry arithmetic is identical): each CTA owns a 16R x 16R tile of C (R = 4, 2
 // or 1), each thread an R x R block of dd accumulators, and the hi/lo planes
 // of the op(A) and op(B) panels are staged through shared memory 16 columns
 // of k at a time with a register prefetch of the next panel.  One SM's FP64
@@ -254,12 +255,16 @@ int launch_r(const GemmArgs &p, cudaStream_t stream) {
 // (work per tile), i.e. ceil(tiles_R / SMs) R^2 in units of a 16 x 16 tile;
 // the largest R with the least such time wins (the per-entry operation
 // sequence, and hence the result, does not depend on R).
-int plain_tile_r(const GemmArgs &p) {
+int64_t plain_tile_cost(const GemmArgs &p, int r) {
     const int64_t sms = sm_count() > 0 ? sm_count() : 152;
+    return ceil_div(tile_count(p, 16 * r), sms) * r * r;
+}
+
+int plain_tile_r(const GemmArgs &p) {
     int best = 4;
     int64_t best_t = -1;
     for (int r = 4; r >= 1; r /= 2) {
-        const int64_t t = ceil_div(tile_count(p, 16 * r), sms) * r * r;
+        const int64_t t = plain_tile_cost(p, r);
         if (best_t < 0 || t < best_t) { best_t = t; best = r; }
     }
     return best;
@@ -273,14 +278,19 @@ int launch_plain_fallback(const GemmArgs &p, const SplitPlan &plan, cudaStream_t
     q.gate = plan.dmin;
     q.gate_below = plan.thr[plan.ncand - 1];
     // with the gate closed every CTA returns at once, so the launch costs
-    // about its CTA count: take the 64 x 64 tiles whenever they fill the
-    // SMs twice (the result does not depend on the tile size)
+    // about its CTA count: the persistent TMA-staged kernel where it applies,
+    // else the 64 x 64 tiles whenever they fill the SMs twice (the result
+    // does not depend on the staging or the tile size)
+    int rc = 0;
+    if (try_launch_gemm_tma(q, stream, &rc)) return rc;
     const int64_t sms = sm_count() > 0 ? sm_count() : 152;
     if (tile_count(q, 64) >= 2 * sms) return launch_r<4>(q, stream);
     return launch_gemm_plain(q, stream);
 }
 
 int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream) {
+    int rc = 0;
+    if (try_launch_gemm_tma(p, stream, &rc)) return rc;
     switch (plain_tile_r(p)) {
         case 1: return launch_r<1>(p, stream);
         case 2: return launch_r<2>(p, stream);

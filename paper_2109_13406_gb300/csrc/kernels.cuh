@@ -41,6 +41,16 @@ struct GemmArgs {
 
 // Plain FP64 dd kernel (64 x 64 output tiles, 4 x 4 dd accumulators per thread).
 int launch_gemm_plain(const GemmArgs &p, cudaStream_t stream);
+// The TMA-staged form of the plain kernel (dd_gemm_tma.cu): 1 when it took the
+// problem (*rc its launch status), 0 when the register-staged kernels must.
+int try_launch_gemm_tma(const GemmArgs &p, cudaStream_t stream, int *rc);
+// Busiest-SM time of the plain kernel on 16r x 16r tiles, in units of a 16 x
+// 16 tile (ceil(tiles / SMs) r^2), and the r the register path takes.
+int64_t plain_tile_cost(const GemmArgs &p, int r);
+int plain_tile_r(const GemmArgs &p);
+// Operand staging of the plain kernel: 0 automatic, 1 registers, 2 TMA.
+void set_plain_staging(int mode);
+int plain_staging();
 
 // FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.
 int run_peak_fp64(cudaStream_t stream, double *rate);
