@@ -613,7 +613,11 @@ int crt_tables(int N, CrtTables &T, int *nwords) {
         for (int t = 0; t < kWords; ++t) T.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
         T.frac[i] = (float)((double)inv / (double)modulus(i));
     }
-    *nwords = (int)P.size() + 1;
+    // words of the sums: S = sum_b c_b w_b < N 255 P, and Z = S - q P takes
+    // a sign bit: bits(P) + ceil(log2(255 N)) + 1
+    int need = big_bits(P) + 1;
+    for (int64_t x = 255LL * N - 1; x > 0; x >>= 1) ++need;
+    *nwords = (need + 31) / 32;
     return 0;
 }
 
@@ -748,12 +752,14 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     const int64_t total = p.m * p.n;
     int64_t blocks = ceil_div(total, 256);
     if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
-    // the word counts that occur for k < 2^17: 9 at 112 bits, 9 or 10 at
-    // 120 bits, 10 at 128 bits (fewer words than allocated are zero-padded)
+    // the word counts that occur for k < 2^17: 8 at 112 bits (9 for the
+    // largest k), 9 at 120 bits, 9 or 10 at 128 bits; a kernel with more
+    // words than needed gives the same result (the weights are zero-padded)
     if (nw[0] > 9 || nw[1] > 10 || nw[2] > 10)
         return fail(MP_DD_ERR_TOO_LARGE, "CRT word counts %d/%d/%d beyond the kernel's", nw[0],
                     nw[1], nw[2]);
-    if (nw[1] <= 9) crt_kernel<9, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    if (nw[0] <= 8 && nw[1] <= 9) crt_kernel<8, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    else if (nw[1] <= 9) crt_kernel<9, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
     else crt_kernel<9, 10, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
     if ((rc = check_launch("crt_kernel"))) return rc;
     rc = launch_plain_fallback(p, plan, st);
