@@ -20,8 +20,9 @@
  * Ownership and execution: unless a call says otherwise, every matrix
  * pointer is DEVICE memory owned by the caller, and every call is
  * asynchronous on the calling thread's current stream (mp_dd_set_stream).
- * The library allocates nothing that outlives a call except what a call
- * documents.
+ * The library keeps nothing allocated beyond a call except what a call
+ * documents (the host forms' memory pool, the no-allocation form's fixed
+ * array).
  *
  * Return codes (all int-returning calls):
  *    0            success
@@ -196,10 +197,14 @@ int mp_dd_Rsymm(const char *side, const char *uplo, int64_t m, int64_t n, mp_dd 
  * used (Sec. 7.3: the caller passes host arrays; the library moves them to
  * the GPU and back -- the "with host-GPU transfer" figures of Sec. 10).
  * All matrix pointers are HOST memory (pinned memory gives the fastest
- * copies).  The call allocates device buffers for the operands with
- * cudaMallocAsync on the current stream, copies in, computes, copies C
- * back, frees the buffers and synchronises the stream before returning.
- * Same arguments, accuracy and error codes as the device forms. */
+ * copies).  The call takes device buffers for the operands from a
+ * stream-ordered memory pool the library owns (one per device, created at
+ * the first such call), copies in, computes, copies C back, returns the
+ * buffers to the pool and synchronises the stream before returning.  The
+ * pool keeps freed memory mapped for later calls (its release threshold is
+ * unlimited): device memory once used by a host-form call stays reserved
+ * by the library until the process exits.  Same arguments, accuracy and
+ * error codes as the device forms. */
 int mp_dd_Rgemm_host(const char *transa, const char *transb, int64_t m, int64_t n, int64_t k,
                      mp_dd alpha, mp_dd_cmat A, int64_t lda, mp_dd_cmat B, int64_t ldb,
                      mp_dd beta, mp_dd_mat C, int64_t ldc);
