@@ -146,6 +146,17 @@ int mp_dd_Rgemm(const char *transa, const char *transb, int64_t m, int64_t n, in
  * the same).  Returns 0, or -1 for another mode. */
 int mp_dd_set_plain_staging(int mode);
 
+/* Scheduling of the split-precision band / residue products on 128 x 256
+ * tiles (no counterpart in the manual; process-wide, for tuning and
+ * testing).  A CTA pair is a cluster of two CTAs on vertically adjacent
+ * tiles that share the op(B) panel, each loading one half and multicasting
+ * it to both (a third fewer L2 reads per product); it needs an even number
+ * of 128-row tiles.  mode 0 (the default): pairs for the Rsyrk triangle,
+ * single CTAs for full products; mode 1: single CTAs only; mode 2: pairs
+ * wherever they apply.  The products are exact integers, so every mode
+ * gives bitwise the same results.  Returns 0, or -1 for another mode. */
+int mp_dd_set_band_pairs(int mode);
+
 /* Rsyrk (Sec. 6 table; CUDA dd Rsyrk in Sec. 7.3):
  *
  *     C := alpha * A * A^T + beta * C   (trans N, A is n x k), or
@@ -449,7 +460,7 @@ size_t mp_dd_Rgemm_sliced_workspace(int64_t m, int64_t n, int64_t k, int slices)
  *    to a multiple of 2^-8S of that scale (error at most one unit) and cut
  *    into S signed base-256 digits in [-128, 128];
  *  - the digit products are exact integer GEMMs (fp16 inputs, fp32
- *    accumulation kept exact by draining every 512 products, int32 sums),
+ *    accumulation kept exact by draining every 1024 products, int32 sums),
  *    grouped by digit significance t + u = b for b < S;
  *  - the band sums are combined exactly in integer arithmetic, rounded once
  *    to dd, scaled back, and alpha/beta are applied in dd arithmetic.

@@ -24,7 +24,7 @@ from ._abi import MpDD, MpDDCMat, MpDDMat
 
 __all__ = [
     "MpddError", "mp_dd_Rgemm", "mp_dd_Rsyrk", "mp_dd_Rgemm_host", "mp_dd_Rsyrk_host",
-    "mp_dd_peak_fp64", "mp_dd_peak_imma", "mp_dd_peak_ddmac", "mp_dd_set_plain_staging", "mp_dd_elementwise", "mp_dd_set_stream", "mp_dd_last_error",
+    "mp_dd_peak_fp64", "mp_dd_peak_imma", "mp_dd_peak_ddmac", "mp_dd_set_plain_staging", "mp_dd_set_band_pairs", "mp_dd_elementwise", "mp_dd_set_stream", "mp_dd_last_error",
     "mp_dd_Rgemm_sliced",
     "mp_dd_Rgemm_sliced_workspace", "mp_dd_Rgemm_sliced_noalloc", "mp_dd_sliced_layout",
     "mp_dd_Rgemm_crt", "mp_dd_Rgemm_crt_workspace", "mp_dd_Rsyrk_crt",
@@ -400,6 +400,12 @@ def mp_dd_peak_fp64() -> float:
 def mp_dd_set_plain_staging(mode: int) -> None:
     """0 automatic, 1 register staging only, 2 TMA staging where it applies."""
     _check(_LIB.mp_dd_set_plain_staging(int(mode)), "mp_dd_set_plain_staging")
+
+
+def mp_dd_set_band_pairs(mode: int) -> None:
+    """CTA pairs for 256-wide band products: 0 triangle (Rsyrk) products
+    only, 1 never, 2 wherever they apply."""
+    _check(_LIB.mp_dd_set_band_pairs(int(mode)), "mp_dd_set_band_pairs")
 
 
 def mp_dd_peak_ddmac() -> float:

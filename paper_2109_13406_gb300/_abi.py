@@ -99,6 +99,7 @@ SIGNATURES = {
     "mp_dd_Rsyrk_host": (_int, [_c, _c, _i64, _i64, MpDD, MpDDCMat, _i64, MpDD, MpDDMat, _i64]),
     "mp_dd_peak_fp64": (_int, [_dp]),
     "mp_dd_set_plain_staging": (_int, [_int]),
+    "mp_dd_set_band_pairs": (_int, [_int]),
     "mp_dd_peak_imma": (_int, [_dp]),
     "mp_dd_peak_ddmac": (_int, [_dp]),
     "mp_dd_elementwise": (_int, [_c, _i64, MpDDCMat, MpDDCMat, MpDDMat]),

@@ -774,6 +774,13 @@ int mp_dd_set_plain_staging(int mode) {
     return 0;
 }
 
+int mp_dd_set_band_pairs(int mode) {
+    clear_error();
+    if (mode < 0 || mode > 2) return fail(-1, "set_band_pairs: mode must be 0, 1 or 2");
+    set_band_pairs(mode);
+    return 0;
+}
+
 int mp_dd_peak_fp64(double *rate) {
     clear_error();
     if (rate == nullptr) return fail(-1, "peak_fp64: rate is NULL");

@@ -712,6 +712,8 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     CUtensorMap tmA, tmB;
     if ((rc = make_tmap(&tmA, RA, (int64_t)L.N * L.m_pad, L.k_pad, kBandTM))) return rc;
     if ((rc = make_tmap(&tmB, RB, (int64_t)L.N * L.n_pad, L.k_pad, TN))) return rc;
+    CUtensorMap tmB_half;   // half-height boxes for CTA pairs on 256-wide tiles
+    if ((rc = make_tmap(&tmB_half, RB, (int64_t)L.N * L.n_pad, L.k_pad, TN / 2))) return rc;
     BandArgs ba{};
     ba.S = L.N;
     ba.kb_count = (int)(L.k_pad / kBandTK);
@@ -726,7 +728,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ba.tri = p.tri;
     ba.plan = plan;
     for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
-    if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
+    if ((rc = launch_band(tmA, tmB, ba, TN, st, &tmB_half))) return rc;
     sliced_timing_mark(2, st);
 
     // CRT constants of every candidate

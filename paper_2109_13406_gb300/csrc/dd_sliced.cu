@@ -12,9 +12,10 @@
 //     K-major [row][k] layout padded to the tile sizes with zeros.
 //  3. Band products.  For b = 0 .. S-1 the exact integer matrix
 //     P_b = sum_{t+u=b} D_A[t] D_B[u]^T is computed on the tensor cores with
-//     fp32 accumulation in tensor memory, drained every 512 products: a run
-//     of 512 products of |d| <= 128 stays within 2^23, so every partial sum
-//     is an integer the fp32 accumulator holds exactly.  The drained values
+//     fp32 accumulation in tensor memory, drained every 1024 products: a
+//     run of 1024 products of |d| <= 128 stays within 2^24 in magnitude, so
+//     every partial sum is an integer the fp32 accumulator holds exactly
+//     (an fp32 addition whose exact sum is representable does not round).  The drained values
 //     are summed in int32 registers (|P_b| < 2^31 for k (b+1) 2^14 < 2^31).
 //     Pairs with t + u >= S are dropped (triangular truncation).
 //  4. Recombination.  V = sum_b P_b 256^(S-1-b) is formed exactly in 192-bit
@@ -38,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -56,7 +58,7 @@ namespace {
 using namespace sm100;
 
 constexpr int TM = 128, TK = 64;            // tile rows and k-block
-constexpr int CHUNK_KB = 8;                 // k-blocks per exact fp32 run (512 products)
+constexpr int CHUNK_KB = 16;                // k-blocks per exact fp32 run (1024 products)
 // The magnitude product needs no exact runs (its fp32 sums only have to stay
 // within the certificate's safety factor): one run over the whole k.
 template <bool MAG>
@@ -295,9 +297,9 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
 // share one modulus's operand panels in L2.
 // Tiles entirely outside the requested triangle (Rsyrk form) get an empty
 // band range, so every role skips them alike.
-template <int TN>
+template <int TN, bool PAIR>
 __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, int num_tiles,
-                                            int &tm, int &tn, int &b0, int &b1) {
+                                            int rank, int &tm, int &tn, int &b0, int &b1) {
     int tile = item;
     b0 = 0;
     b1 = S;
@@ -306,9 +308,22 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, 
         b1 = b0 + 1;
         tile = item % num_tiles;
     }
-    tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
-    const int64_t r0 = (int64_t)tm * TM, c0 = (int64_t)tn * TN;
-    if ((p.tri == 1 && r0 > c0 + TN - 1) || (p.tri == 2 && r0 + TM - 1 < c0)) b1 = b0;
+    // a CTA pair takes two vertically adjacent tiles (one per CTA) and skips
+    // a triangle item only when both tiles lie outside
+    int64_t r0, rows;
+    if (PAIR) {
+        int tp;
+        tile_coords(tile, p.tiles_m / 2, p.tiles_n, tp, tn);
+        tm = 2 * tp + rank;
+        r0 = (int64_t)tp * 2 * TM;
+        rows = 2 * TM;
+    } else {
+        tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+        r0 = (int64_t)tm * TM;
+        rows = TM;
+    }
+    const int64_t c0 = (int64_t)tn * TN;
+    if ((p.tri == 1 && r0 > c0 + TN - 1) || (p.tri == 2 && r0 + rows - 1 < c0)) b1 = b0;
 }
 
 constexpr unsigned int kInfBits32 = 0x7F800000u;   // +inf as fp32 bits
@@ -389,7 +404,13 @@ __device__ __forceinline__ void certificate_margin(const BandArgs &p,
 // MAG: the certificate's magnitude product (bf16 operands, fp32 sums, the
 // margin d_ij of every entry reduced to its minimum); otherwise the integer
 // band products with the band count taken from the call's plan.
-template <int TN, bool MAG>
+// PAIR: a cluster of two CTAs on vertically adjacent tiles with the same
+// columns.  Each CTA loads its own op(A) panel and one half of the shared
+// op(B) panel, delivered to both CTAs by a multicast copy (tmB's box is
+// TN / 2 rows), so a stage costs 32 KB of L2 reads per CTA instead of 48.
+// A stage is refilled only after both CTAs' MMAs have consumed it: every
+// MMA commit arrives on the "empty" barriers of both CTAs.
+template <int TN, bool MAG, bool PAIR = false>
 __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const BandArgs p) {
@@ -418,11 +439,15 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(fin + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
+    static_assert(!PAIR || (TN == 256 && !MAG), "CTA pairs: residue / digit products, 256 wide");
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int rank = PAIR ? (int)cluster_ctarank() : 0;
+    const int item0 = PAIR ? (int)cluster_id_x() : (int)blockIdx.x;
+    const int item_step = PAIR ? (int)cluster_count_x() : (int)gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], PAIR ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
@@ -439,9 +464,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (PAIR) cluster_sync();   // the peer's barriers exist before anything lands there
     const uint32_t tmem = *tmem_holder;
 
-    const int num_tiles = p.tiles_m * p.tiles_n;
+    const int num_tiles = (PAIR ? p.tiles_m / 2 : p.tiles_m) * p.tiles_n;
     const int KB = p.kb_count;
     const int num_items = p.diag ? num_tiles * S : num_tiles;
 
@@ -452,9 +478,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             prefetch_tmap(&tmB);
             uint32_t it = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+            for (int item = item0; item < num_items && ok; item += item_step) {
                 int tm, tn, b0, b1;
-                item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b)
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
@@ -468,9 +494,21 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                             }
                             mbar_arrive_expect_tx(&full[s], kStageBytes);
                             tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, &full[s], kb * TK, ya);
-                            tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, &full[s], kb * TK, yb);
+                            if (PAIR)
+                                tma_load_2d_multicast(
+                                    sB + s * Cfg::B_BYTES + rank * (Cfg::B_BYTES / 2), &tmB,
+                                    &full[s], kb * TK, yb + rank * (TN / 2), (uint16_t)3);
+                            else
+                                tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, &full[s], kb * TK, yb);
                         }
                     }
+            }
+            if (PAIR && ok) {
+                // both MMAs' last arrivals on this CTA's barriers have landed
+                // before it may exit
+                const uint32_t first = it > STAGES ? it - STAGES : 0;
+                for (uint32_t j = first; j < it && ok; ++j)
+                    ok = mbar_wait(&empty[j % STAGES], (j / STAGES) & 1, abort_flag);
             }
             if (!ok) {
                 // let the copies already issued land before the CTA exits
@@ -490,9 +528,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
             const uint32_t idesc = MAG ? idesc_bf16_f32(TM, TN) : idesc_f16_f32(TM, TN);
             uint32_t it = 0, chunk = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+            for (int item = item0; item < num_items && ok; item += item_step) {
                 int tm, tn, b0, b1;
-                item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
+                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b) {
                     const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
@@ -524,7 +562,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                                 mma_f16(d, desc_sw128_kmajor(a0 + kk * 32),
                                         desc_sw128_kmajor(b0 + kk * 32), idesc,
                                         (first && kk == 0) ? 0u : 1u);
-                            mma_commit(&empty[s]);
+                            if (PAIR)
+                                mma_commit_multicast(&empty[s], (uint16_t)3);
+                            else
+                                mma_commit(&empty[s]);
                             if (last) {
                                 mma_commit(&accf[buf]);
                                 ++chunk;
@@ -547,9 +588,9 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t chunk = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < num_items && ok; item += gridDim.x) {
+        for (int item = item0; item < num_items && ok; item += item_step) {
             int tm, tn, b0, b1;
-            item_coords<TN>(p, S, item, num_tiles, tm, tn, b0, b1);
+            item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
             for (int b = b0; b < b1 && ok; ++b) {
                 int32_t acc[kEpiCols];
 #pragma unroll
@@ -611,6 +652,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, kTmemCols);
     if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, MP_DD_ERR_TIMEOUT);
+    if (PAIR) cluster_sync();   // no CTA leaves while its peer may still signal it
 }
 
 // ------------------------------------------------------------------ step 4
@@ -1077,6 +1119,8 @@ int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStr
     CUtensorMap tmA, tmB;
     if ((rc = make_tmap(&tmA, DA, (int64_t)S * L.m_pad, L.k_pad, TM))) return rc;
     if ((rc = make_tmap(&tmB, DB, (int64_t)S * L.n_pad, L.k_pad, TN))) return rc;
+    CUtensorMap tmB_half;   // half-height boxes for CTA pairs on 256-wide tiles
+    if ((rc = make_tmap(&tmB_half, DB, (int64_t)S * L.n_pad, L.k_pad, TN / 2))) return rc;
     BandArgs ba{};
     ba.S = S;
     ba.kb_count = (int)(L.k_pad / TK);
@@ -1089,7 +1133,7 @@ int run_sliced(const GemmArgs &p, int slices, void *ws, size_t ws_bytes, cudaStr
     ba.diag = 0;
     ba.status = &hdr->status;
     ba.plan = plan;
-    if ((rc = launch_band(tmA, tmB, ba, TN, st))) return rc;
+    if ((rc = launch_band(tmA, tmB, ba, TN, st, &tmB_half))) return rc;
     timer().mark(2, st);
 
     RecArgs ra{};
@@ -1113,8 +1157,49 @@ namespace {
 
 }  // namespace
 
+namespace {
+
+// 0: CTA pairs for triangle (Rsyrk) products, 1: never, 2: wherever they
+// apply.  On full products pairs measured 4 % slower (the per-SM operand
+// bytes, which limit this kernel, stay the same, and the pair's MMAs wait on
+// each other); on triangles they balance the skipped tiles better (11 %
+// faster at 8192).
+std::atomic<int> g_band_pairs{0};
+
+// Clusters of two band CTAs that fit on the GPU at once (0: none).
+int pair_clusters() {
+    static int count = -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        using Cfg = BandCfg<256>;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * sm_count());
+        cfg.blockDim = dim3(Cfg::THREADS);
+        cfg.dynamicSmemBytes = Cfg::SMEM;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, band_gemm_kernel<256, false, true>, &cfg) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        count = n;
+    });
+    return count;
+}
+
+}  // namespace
+
+void set_band_pairs(int mode) { g_band_pairs.store(mode); }
+
 int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
-                cudaStream_t st) {
+                cudaStream_t st, const CUtensorMap *tmB_half) {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
         cudaFuncSetAttribute(band_gemm_kernel<128, false>,
@@ -1123,12 +1208,36 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<256>::SMEM);
         cudaFuncSetAttribute(band_gemm_kernel<128, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
+        cudaFuncSetAttribute(band_gemm_kernel<256, false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<256>::SMEM);
     });
     const int tiles = ba.tiles_m * ba.tiles_n;
     const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords (S: the most bands)
     const int grid = items < sm_count() ? items : sm_count();
     // (the magnitude product always runs on 128-wide tiles)
     if (ba.mag && TN != 128) return fail(MP_DD_ERR_TOO_LARGE, "magnitude product: tile width");
+    if (!ba.mag && TN == 256 && tmB_half != nullptr && ba.tiles_m % 2 == 0 &&
+        (g_band_pairs.load() == 2 || (g_band_pairs.load() == 0 && ba.tri != 0)) &&
+        pair_clusters() > 0) {
+        const int pair_items = items / 2;
+        const int clusters = pair_items < pair_clusters() ? pair_items : pair_clusters();
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * clusters);
+        cfg.blockDim = dim3(BandCfg<256>::THREADS);
+        cfg.dynamicSmemBytes = BandCfg<256>::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e =
+            cudaLaunchKernelEx(&cfg, band_gemm_kernel<256, false, true>, tmA, *tmB_half, ba);
+        if (e != cudaSuccess) return cuda_fail(e, "band_gemm_kernel (CTA pairs)");
+        return check_launch("band_gemm_kernel");
+    }
     if (ba.mag)
         band_gemm_kernel<128, true><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
             tmA, tmB, ba);

@@ -51,6 +51,9 @@ int plain_tile_r(const GemmArgs &p);
 // Operand staging of the plain kernel: 0 automatic, 1 registers, 2 TMA.
 void set_plain_staging(int mode);
 int plain_staging();
+// CTA pairs for the 256-wide split-precision band products (dd_sliced.cu):
+// 0 triangle products only, 1 never, 2 wherever they apply.
+void set_band_pairs(int mode);
 
 // FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.
 int run_peak_fp64(cudaStream_t stream, double *rate);

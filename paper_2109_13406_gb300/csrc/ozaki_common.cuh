@@ -113,8 +113,10 @@ int make_tmap(CUtensorMap *m, void *base, int64_t rows, int64_t k_pad, int box_r
               int elem = 0);
 int launch_absmax(const double *X, int64_t ld, int row_contig, int64_t rows, int64_t k,
                   unsigned long long *out, cudaStream_t st);
+// tmB_half: the op(B) map with TN / 2-row boxes; given for a product that may
+// run on CTA pairs (NULL: single CTAs).
 int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &ba, int TN,
-                cudaStream_t st);
+                cudaStream_t st, const CUtensorMap *tmB_half = nullptr);
 constexpr int kBandTM = 128, kBandTK = 64;
 int band_tn(int64_t m, int64_t n);
 

@@ -175,3 +175,34 @@ def test_rsyrk_crt_errors(cuda_lib):
                               check=False) == -12
     assert mp.mp_dd_Rsyrk_crt("U", "N", 8, 4, (1.0, 0.0), A, 8, (0.0, 0.0), C, 8, ws, 16,
                               check=False) == 2003
+
+
+def test_crt_exact_runs_at_their_bound(cuda_lib):
+    """Entries +-(1/2 + 2^-104) scale to X = +-(2^110 + 2^7), whose residue
+    mod 256 is -128 whatever the sign: every product of the 256 plane is
+    2^14, so each run of 1024 products sums to exactly 2^24, the largest
+    partial sum an exact fp32 run may reach.  Product planes bit-exact
+    against the oracle; the result within the bound."""
+    mp = cuda_lib
+    m, n, k = 16, 24, 2048
+    g = datagen.rng(740)
+    sa = np.where(g.random((m, k)) < 0.5, -1.0, 1.0)
+    sb = np.where(g.random((k, n)) < 0.5, -1.0, 1.0)
+    A = (np.asfortranarray(0.5 * sa), np.asfortranarray(2.0 ** -104 * sa))
+    B = (np.asfortranarray(0.5 * sb), np.asfortranarray(2.0 ** -104 * sb))
+    C = datagen.dd_matrix(g, m, n, m)
+    c = datagen.GemmCase("N", "N", m, n, k, (1.0, 0.0), A, B, (1.0, 0.0), C)
+    got, ws = run_crt(mp, c)
+    rep = mp.mp_dd_split_report(ws)
+    assert rep["width_bits"] == 112
+    L = mp.mp_dd_crt_layout(m, n, k)
+    mods = L["moduli"][:rep["count"]]
+    assert mods[0] == 256
+    RA, _ = oz.residue_planes(*oz.op_rows(c.A, False, m, k), mods, 14)
+    RB, _ = oz.residue_planes(*oz.op_cols(c.B, False, k, n), mods, 14)
+    assert (RA[0] == -128).all() and (RB[0] == -128).all()
+    N, mp_, np_ = len(mods), L["m_pad"], L["n_pad"]
+    prods = view(ws, L["products"], N * np_ * mp_, np.uint8).reshape(N, np_, mp_)
+    want = oz.crt_products(RA, RB, mods)
+    assert np.array_equal(prods[:, :n, :m].transpose(0, 2, 1).astype(np.int64), want)
+    assert check_against_exact(c, got) <= 1.0
