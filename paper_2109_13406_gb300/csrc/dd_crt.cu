@@ -28,8 +28,10 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
+#include "bigfloat.cuh"
 #include "common.cuh"
 #include "dd_arith.cuh"
 #include "kernels.cuh"
@@ -72,8 +74,6 @@ constexpr ModWeights make_mod_weights() {
     }
     return mw;
 }
-
-__constant__ ModWeights c_mod_weights = make_mod_weights();
 
 // The same weights, each duplicated into both halves of a float2, with the
 // packed constants of the quotient step: the residue kernel works on two
@@ -200,8 +200,13 @@ __global__ void __launch_bounds__(128) residue_kernel(
 // Reconstruction constants of one moduli count N.
 struct CrtTables {
     uint32_t P[kWords];                   // product of the moduli
-    uint32_t w[kMaxMod][kWords];          // CRT weights (P / p_b) ((P / p_b)^-1 mod p_b)
-    float frac[kMaxMod];                  // ((P / p_b)^-1 mod p_b) / p_b = w_b / P
+    // Byte t of the CRT weights w_b = (P / p_b) ((P / p_b)^-1 mod p_b) of the
+    // four moduli b = 4g .. 4g+3, packed in one word (zero past N): the dp4a
+    // operand of digit t of the sums.
+    uint32_t wp[kMaxMod / 4][4 * kWords];
+    // The same for qfix_b = RN(2^24 ((P / p_b)^-1 mod p_b) / p_b), w_b / P in
+    // fixed point (three bytes).
+    uint32_t qp[kMaxMod / 4][3];
 };
 
 struct CrtArgs {
@@ -219,41 +224,6 @@ struct CrtArgs {
     int tri;                              // 0: all of C; 1 / 2: upper / lower triangle
     const int64_t *info;                  // optional: non-zero -> leave C as is
 };
-
-// Word idx of a little-endian multiword value, without dynamic indexing
-// (which would move the array to local memory).
-template <int NW>
-__device__ __forceinline__ uint32_t word_at(const uint32_t (&v)[NW], int idx) {
-    uint32_t r = 0;
-#pragma unroll
-    for (int t = 0; t < NW; ++t) r = (t == idx) ? v[t] : r;
-    return r;
-}
-
-// x 2^e for a binary64 x that is zero or normal, by exponent arithmetic when
-// the result stays normal (one DMUL otherwise).
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-    if (x == 0.0) return 0.0;
-    const long long bits = __double_as_longlong(x);
-    const int E = (int)((bits >> 52) & 0x7FF);
-    if (E + e >= 1 && E + e <= 2046) return __longlong_as_double(bits + ((long long)e << 52));
-    double r = x;
-    while (e > 1000) { r = __dmul_rn(r, 0x1p1000); e -= 1000; }
-    while (e < -1000) { r = __dmul_rn(r, 0x1p-1000); e += 1000; }
-    return __dmul_rn(r, __longlong_as_double((long long)(e + 1023) << 52));
-}
-
-// m 2^e for an integer 0 <= m <= 2^53, assembled from the binary64 fields
-// when the result is normal (integer instructions only), else by scale_pow2.
-__device__ __forceinline__ double mant_pow2(uint64_t m, int e) {
-    if (m == 0) return 0.0;
-    const int top = 63 - __clzll((long long)m);          // m in [2^top, 2^(top+1))
-    const uint64_t norm = top > 52 ? m >> (top - 52) : m << (52 - top);   // exact
-    const int E = top + e + 1023;
-    if (E >= 1 && E <= 2046)
-        return __longlong_as_double((long long)(((uint64_t)E << 52) | (norm & ((1ull << 52) - 1))));
-    return scale_pow2(__ull2double_rn(m), e);
-}
 
 // alpha v + beta c in dd with one rounding chain: the two leading products
 // split exactly (product and FMA error), their sum by TwoSum, every
@@ -274,107 +244,106 @@ __device__ __forceinline__ dd axpby_dd(dd alpha, dd v, dd beta, dd c) {
     return r;
 }
 
-// Round the magnitude v (little-endian 32-bit words) to the nearest binary64
-// (ties to even) times 2^scale.  rem receives the exact remainder v - RN(v)
-// as a magnitude, rem_neg its sign.
-template <int NW>
-__device__ __forceinline__ double round_words(const uint32_t (&v)[NW], int scale,
-                                              uint32_t (&rem)[NW], bool &rem_neg) {
-    int top = -1;
-#pragma unroll
-    for (int t = NW - 1; t >= 0; --t)
-        if (top < 0 && v[t] != 0) top = t;
-    rem_neg = false;
-#pragma unroll
-    for (int t = 0; t < NW; ++t) rem[t] = 0;
-    if (top < 0) return 0.0;
-    const int msb = 32 * top + (31 - __clz(word_at(v, top)));
-    if (msb <= 52) {
-        const uint64_t x = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
-        return mant_pow2(x, scale);   // exact
-    }
-    const int q = msb - 52, w = q / 32, b = q % 32;
-    const uint64_t v0 = word_at(v, w), v1 = word_at(v, w + 1), v2 = word_at(v, w + 2);
-    uint64_t mant = b ? ((v0 >> b) | (v1 << (32 - b)) | (v2 << (64 - b))) : (v0 | (v1 << 32));
-    mant &= (1ull << 53) - 1;
-    // remainder below bit q, compared with 2^(q-1)
-    const int hw = (q - 1) / 32, hb = (q - 1) % 32;
-    bool gt = false, eq = true;
-#pragma unroll
-    for (int t = NW - 1; t >= 0; --t) {
-        uint32_t word = v[t];
-        word = (t > w) ? 0u : (t == w ? (b ? (word & ((1u << b) - 1)) : 0u) : word);
-        rem[t] = word;
-        const uint32_t hwd = (t == hw) ? (1u << hb) : 0u;
-        if (eq && word != hwd) {
-            gt = word > hwd;
-            eq = false;
-        }
-    }
-    if (gt || (eq && (mant & 1))) {
-        ++mant;                       // rounded up: remainder becomes 2^q - rem, negative
-        rem_neg = true;
-        uint64_t borrow = 0;
-#pragma unroll
-        for (int t = 0; t < NW; ++t) {
-            const uint64_t bit = (t == w) ? (1ull << b) : 0ull;
-            const uint64_t d = bit - (uint64_t)rem[t] - borrow;
-            rem[t] = (uint32_t)d;
-            borrow = (d >> 63) & 1;
-        }
-    }
-    return mant_pow2(mant, q + scale);   // mant <= 2^53: exact
-}
+// The CRT sums of two adjacent entries (i, j), (i + 1, j) from the N
+// products reduced mod p_b: S = sum_b c_b w_b over NW 32-bit words and the
+// fixed-point quotient column Q = sum_b c_b qfix_b.  The residues of both
+// entries come in one 2-byte load per modulus and are packed four moduli to
+// a register, so each byte digit t of the sums is one dp4a per four moduli
+// (the digit sums stay below 40 255^2 < 2^22, exact in 32 bits) before the
+// digits are carried into words.  T is a reference into the kernel's
+// parameter block: the packed weights are constant-bank operands.
+constexpr int kCrtGroups = kMaxMod / 4;
 
-// One output entry (i, j) from the N products reduced mod p_b: the CRT sum,
-// its symmetric representative, the rounding to dd and the alpha/beta
-// epilogue.  T is a reference into the kernel's parameter block and every
-// modulus index below is a constant after unrolling, so the weights are
-// read straight from the constant bank (no per-term load).
-// NW: 32-bit words of the sums (P < 2^(32 (NW - 1)), and the sum of N
-// residues < 256 times the weights < P stays below 2^(32 NW)).
-template <int NW>
-__device__ __forceinline__ void crt_entry(const CrtArgs &p, const CrtTables &T, int N, int W,
-                                          int64_t i, int64_t j) {
-    // S = sum_b c_b w_b with 64-bit column sums, then carries; the products
-    // are read 8 moduli at a time, the 8 loads in flight together
+// The residues of entries (i, i + 1), i even (2-byte aligned): word h holds
+// moduli 2h and 2h + 1 as bytes e0b e1b e0b' e1b' (zero past N).
+__device__ __forceinline__ void crt_load_pair(const CrtArgs &p, int N, int64_t i, int64_t j,
+                                              uint32_t (&v)[kMaxMod / 2]) {
     const uint8_t *res = p.res + j * p.m_pad + i;
     const int64_t plane = p.n_pad * p.m_pad;
-    // (and, for the quotient below, qf = sum_b c_b (inv_b / p_b) in fp32)
-    uint64_t acc[NW];
 #pragma unroll
-    for (int t = 0; t < NW; ++t) acc[t] = 0;
-    float qf = 0.0f;
+    for (int h = 0; h < kMaxMod / 2; ++h) {
+        const uint32_t lo = 2 * h < N
+            ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(res + 2 * h * plane)) : 0u;
+        const uint32_t hi = 2 * h + 1 < N
+            ? (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(res + (2 * h + 1) * plane))
+            : 0u;
+        v[h] = lo | (hi << 16);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void crt_sums(const CrtTables &T, int N,
+                                         const uint32_t (&v)[kMaxMod / 2],
+                                         uint32_t (&S0)[NW], uint32_t (&S1)[NW], uint64_t &Q0,
+                                         uint64_t &Q1) {
+    constexpr int G = kCrtGroups;
+    uint32_t R0[G], R1[G];
 #pragma unroll
-    for (int b0 = 0; b0 < kMaxMod; b0 += 8) {
-        if (b0 >= N) break;
-        uint32_t cv[8];
+    for (int g = 0; g < G; ++g) {
+        // v[2g] = e0b0 e1b0 e0b1 e1b1, v[2g + 1] = e0b2 e1b2 e0b3 e1b3
+        R0[g] = __byte_perm(v[2 * g], v[2 * g + 1], 0x6420);   // entry i: moduli 4g .. 4g+3
+        R1[g] = __byte_perm(v[2 * g], v[2 * g + 1], 0x7531);   // entry i + 1
+    }
+    const int groups = (N + 3) / 4;
+    uint64_t c0 = 0, c1 = 0;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cv[u] = b0 + u < N ? res[(b0 + u) * plane] : 0u;
+    for (int k = 0; k < NW; ++k) {
+        uint32_t d0[4] = {0u, 0u, 0u, 0u}, d1[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int b = b0 + u;                     // cv[u] = 0 past N
+        for (int g = 0; g < G; ++g) {
+            if (g >= groups) break;
 #pragma unroll
-            for (int t = 0; t < NW; ++t) acc[t] += (uint64_t)cv[u] * T.w[b][t];
-            qf = __fmaf_rn((float)cv[u], T.frac[b], qf);
+            for (int u = 0; u < 4; ++u) {
+                d0[u] = __dp4a(R0[g], T.wp[g][4 * k + u], d0[u]);
+                d1[u] = __dp4a(R1[g], T.wp[g][4 * k + u], d1[u]);
+            }
+        }
+        // word k: d[0] + d[1] 2^8 + d[2] 2^16 + d[3] 2^24 + the carry
+        const uint64_t v0 = c0 + (d0[0] + (d0[1] << 8)) + ((uint64_t)(d0[2] + (d0[3] << 8)) << 16);
+        const uint64_t v1 = c1 + (d1[0] + (d1[1] << 8)) + ((uint64_t)(d1[2] + (d1[3] << 8)) << 16);
+        S0[k] = (uint32_t)v0;
+        S1[k] = (uint32_t)v1;
+        c0 = v0 >> 32;
+        c1 = v1 >> 32;
+    }
+    uint32_t q0[3] = {0u, 0u, 0u}, q1[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (g >= groups) break;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            q0[u] = __dp4a(R0[g], T.qp[g][u], q0[u]);
+            q1[u] = __dp4a(R1[g], T.qp[g][u], q1[u]);
         }
     }
+    Q0 = q0[0] + ((uint64_t)q0[1] << 8) + ((uint64_t)q0[2] << 16);
+    Q1 = q1[0] + ((uint64_t)q1[1] << 8) + ((uint64_t)q1[2] << 16);
+}
+
+// One output entry from its sums: the symmetric representative of S mod P,
+// then the alpha/beta epilogue rounded once to dd.
+// NW: 32-bit words of the sums (P < 2^(32 (NW - 1)), and the sum of N
+// residues < 256 times the weights < P stays below 2^(32 NW)).
+// ch, cl: C(i, j) when the epilogue reads it; rbits, cbits: the row and
+// column maxima of op(A) and op(B) (loaded ahead by the caller).
+template <int NW>
+__device__ __forceinline__ void crt_entry(const CrtArgs &p, const CrtTables &T, int W,
+                                          uint32_t (&S)[NW], uint64_t Q, int64_t i, int64_t j,
+                                          double ch, double cl, unsigned long long rbits,
+                                          unsigned long long cbits) {
     // The symmetric representative is Z = S - q P with q the integer
     // nearest to S / P = sum_b c_b (inv_b / p_b): |Z| < k 2^(2W-2) <= P / 4,
-    // and the fp32 sum of the N <= 40 fractions (each term below 256, the
-    // sum below 10240) is off by less than 0.03, so rounding it gives q.
-    const uint64_t q = (uint64_t)(int64_t)rintf(qf);
+    // and Q 2^-24 is within N 255 2^-25 < 0.0004 of S / P (each qfix_b
+    // within 2^-25 of inv_b / p_b), so rounding it gives q.
+    const uint64_t q = (Q + (1ull << 23)) >> 24;
     // Z = S - q P in two's complement over NW words (exact: |Z| < 2^(32 NW - 1))
-    uint32_t S[NW];
     {
-        uint64_t carry = 0, mc = 0, borrow = 0;
+        uint64_t mc = 0, borrow = 0;
 #pragma unroll
         for (int t = 0; t < NW; ++t) {
-            const uint64_t v = acc[t] + carry;
-            carry = v >> 32;
             const uint64_t prod = q * T.P[t] + mc;
             mc = prod >> 32;
-            const uint64_t d = (uint64_t)(uint32_t)v - (uint32_t)prod - borrow;
+            const uint64_t d = (uint64_t)S[t] - (uint32_t)prod - borrow;
             S[t] = (uint32_t)d;
             borrow = (d >> 63) & 1;
         }
@@ -390,47 +359,74 @@ __device__ __forceinline__ void crt_entry(const CrtArgs &p, const CrtTables &T, 
             c2 = v >> 32;
         }
     }
-    const int sc = scale_exponent(p.rmax[i]) + scale_exponent(p.cmax[j]) - 2 * W;
-    uint32_t rem[NW], rem2[NW];
-    bool rem_neg, unused;
-    double vh = round_words(S, sc, rem, rem_neg);
-    double vl = round_words(rem, sc, rem2, unused);
-    if (rem_neg) vl = -vl;
-    if (negative) {
-        vh = -vh;
-        vl = -vl;
-    }
-    dd v{vh, vl};
+    const int sc = scale_exponent(rbits) + scale_exponent(cbits) - 2 * W;
+    // v = Z 2^sc rounded once to dd by integer operations (no FP64), then
+    // the alpha / beta epilogue in dd arithmetic
+    dd v;
+    bigf::to_dd(bigf::from_words<NW>(S, negative ? 1u : 0u, sc), v.hi, v.lo);
     const int64_t off = i + j * p.ldc;
+    dd r;
     switch (p.ab_mode) {
         case 1:   // alpha = +-1, beta = 0: the product itself
-            if (p.alpha_neg) v = dd{-v.hi, -v.lo};
+            r = p.alpha_neg ? dd{-v.hi, -v.lo} : v;
             break;
-        case 2: {   // alpha = +-1, beta = 1 (every Cholesky update): one dd addition
-            const dd av = p.alpha_neg ? dd{-v.hi, -v.lo} : v;
-            v = add_sloppy(dd{p.ch[off], p.cl[off]}, av);
+        case 2:   // alpha = +-1, beta = 1 (every Cholesky update): one dd addition
+            r = add_sloppy(dd{ch, cl}, p.alpha_neg ? dd{-v.hi, -v.lo} : v);
             break;
-        }
         default:
             if (!p.beta_zero)
-                v = axpby_dd(dd{p.alpha.hi, p.alpha.lo}, v, dd{p.beta.hi, p.beta.lo},
-                             dd{p.ch[off], p.cl[off]});
-            else if (!p.alpha_one)
-                v = mul(dd{p.alpha.hi, p.alpha.lo}, v);
+                r = axpby_dd(dd{p.alpha.hi, p.alpha.lo}, v, dd{p.beta.hi, p.beta.lo}, dd{ch, cl});
+            else
+                r = p.alpha_one ? v : mul(dd{p.alpha.hi, p.alpha.lo}, v);
     }
-    p.ch[off] = v.hi;
-    p.cl[off] = v.lo;
+    p.ch[off] = r.hi;
+    p.cl[off] = r.lo;
+}
+
+// Entry pairs (i, i + 1) of column j, i even (m_pad is even, so the pair's
+// residues exist even when i + 1 = m).  (Requesting the next pair's loads
+// ahead measured slower: the extra registers cost more occupancy than the
+// overlap gains.)
+template <int NW>
+__device__ __forceinline__ void crt_pair(const CrtArgs &p, const CrtTables &T, int N, int W,
+                                         int64_t i, int64_t j) {
+    const bool in0 = !((p.tri == 1 && i > j) || (p.tri == 2 && i < j));
+    const bool in1 = i + 1 < p.m && !((p.tri == 1 && i + 1 > j) || (p.tri == 2 && i + 1 < j));
+    if (!in0 && !in1) return;
+    uint32_t v[kMaxMod / 2];
+    crt_load_pair(p, N, i, j, v);
+    uint32_t S0[NW], S1[NW];
+    uint64_t Q0, Q1;
+    crt_sums<NW>(T, N, v, S0, S1, Q0, Q1);
+    const bool use_c = p.ab_mode == 2 || (p.ab_mode == 0 && !p.beta_zero);
+    const unsigned long long cb = __ldg(p.cmax + j);
+    if (in0) {
+        const int64_t off = i + j * p.ldc;
+        crt_entry<NW>(p, T, W, S0, Q0, i, j, use_c ? p.ch[off] : 0.0, use_c ? p.cl[off] : 0.0,
+                      __ldg(p.rmax + i), cb);
+    }
+    if (in1) {
+        const int64_t off = i + 1 + j * p.ldc;
+        crt_entry<NW>(p, T, W, S1, Q1, i + 1, j, use_c ? p.ch[off] : 0.0,
+                      use_c ? p.cl[off] : 0.0, __ldg(p.rmax + i + 1), cb);
+    }
 }
 
 template <int NW>
 __device__ __forceinline__ void crt_loop(const CrtArgs &p, const CrtTables &T, int N, int W) {
-    const int64_t total = p.m * p.n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx % p.m, j = idx / p.m;
-        if ((p.tri == 1 && i > j) || (p.tri == 2 && i < j)) continue;
-        crt_entry<NW>(p, T, N, W, i, j);
+    const int64_t mh = (p.m + 1) / 2;
+    const int64_t total = mh * p.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (total <= 0xFFFFFFFFll) {   // 32-bit index arithmetic
+        const uint32_t m32 = (uint32_t)mh;
+        for (; idx < total; idx += stride) {
+            const uint32_t u = (uint32_t)idx, jj = u / m32, ih = u - jj * m32;
+            crt_pair<NW>(p, T, N, W, 2 * (int64_t)ih, jj);
+        }
+        return;
     }
+    for (; idx < total; idx += stride) crt_pair<NW>(p, T, N, W, 2 * (idx % mh), idx / mh);
 }
 
 // NW0..NW2: words of the sums for the three candidate widths.
@@ -600,6 +596,7 @@ int launch_residues(int Nmax, const double *Xh, const double *Xl, int64_t ld, in
 
 // Reconstruction constants for the first N moduli.
 int crt_tables(int N, CrtTables &T, int *nwords) {
+    memset(&T, 0, sizeof T);
     Big P{1};
     for (int i = 0; i < N; ++i) P = big_mul_small(P, modulus(i));
     if ((int)P.size() > kWords - 1) return fail(MP_DD_ERR_TOO_LARGE, "moduli product too wide");
@@ -610,8 +607,13 @@ int crt_tables(int N, CrtTables &T, int *nwords) {
         big_div_small(Mi, modulus(i), &mi_mod);
         const uint32_t inv = inv_mod(mi_mod, modulus(i));
         Big wi = big_mul_small(Mi, inv);
-        for (int t = 0; t < kWords; ++t) T.w[i][t] = t < (int)wi.size() ? wi[t] : 0;
-        T.frac[i] = (float)((double)inv / (double)modulus(i));
+        const int g = i / 4, sh = 8 * (i % 4);
+        for (int t = 0; t < 4 * kWords; ++t) {
+            const uint32_t word = t / 4 < (int)wi.size() ? wi[t / 4] : 0u;
+            T.wp[g][t] |= ((word >> (8 * (t % 4))) & 0xFFu) << sh;
+        }
+        const uint32_t qfix = (uint32_t)((((uint64_t)inv << 24) + modulus(i) / 2) / modulus(i));
+        for (int t = 0; t < 3; ++t) T.qp[g][t] |= ((qfix >> (8 * t)) & 0xFFu) << sh;
     }
     // words of the sums: S = sum_b c_b w_b < N 255 P, and Z = S - q P takes
     // a sign bit: bits(P) + ceil(log2(255 N)) + 1
@@ -751,18 +753,21 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     for (int c = 0; c < ncand; ++c)
         if ((rc = crt_tables(counts[c], ca.tab[c], &nw[c]))) return rc;
     for (int c = ncand; c < kMaxCand; ++c) nw[c] = nw[ncand - 1];   // (never chosen)
-    const int64_t total = p.m * p.n;
-    int64_t blocks = ceil_div(total, 256);
-    if (blocks > (int64_t)sm_count() * 32) blocks = (int64_t)sm_count() * 32;
+    // one thread per entry pair; blocks resident at once, looping
+    const int64_t pairs = ceil_div(p.m, 2) * p.n;
+    int64_t blocks = ceil_div(pairs, 256);
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    if (blocks < 1) blocks = 1;
     // the word counts that occur for k < 2^17: 8 at 112 bits (9 for the
     // largest k), 9 at 120 bits, 9 or 10 at 128 bits; a kernel with more
     // words than needed gives the same result (the weights are zero-padded)
     if (nw[0] > 9 || nw[1] > 10 || nw[2] > 10)
         return fail(MP_DD_ERR_TOO_LARGE, "CRT word counts %d/%d/%d beyond the kernel's", nw[0],
                     nw[1], nw[2]);
-    if (nw[0] <= 8 && nw[1] <= 9) crt_kernel<8, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    else if (nw[1] <= 9) crt_kernel<9, 9, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
-    else crt_kernel<9, 10, 10><<<(unsigned)blocks, 256, 0, st>>>(ca);
+    const unsigned nb = (unsigned)blocks;
+    if (nw[0] <= 8 && nw[1] <= 9) crt_kernel<8, 9, 10><<<nb, 256, 0, st>>>(ca);
+    else if (nw[1] <= 9) crt_kernel<9, 9, 10><<<nb, 256, 0, st>>>(ca);
+    else crt_kernel<9, 10, 10><<<nb, 256, 0, st>>>(ca);
     if ((rc = check_launch("crt_kernel"))) return rc;
     rc = launch_plain_fallback(p, plan, st);
     sliced_timing_mark(3, st);

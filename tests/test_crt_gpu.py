@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import datagen
+import oracle
 from oracle import ozaki_ref as oz
 from gpucase import check_against_exact, dev, host, sample_blocks
 
@@ -206,3 +207,64 @@ def test_crt_exact_runs_at_their_bound(cuda_lib):
     want = oz.crt_products(RA, RB, mods)
     assert np.array_equal(prods[:, :n, :m].transpose(0, 2, 1).astype(np.int64), want)
     assert check_against_exact(c, got) <= 1.0
+
+
+@pytest.mark.parametrize("alpha,beta", [((1.0, 0.0), (0.0, 0.0)), ((-1.0, 0.0), (0.0, 0.0)),
+                                        ((1.0, 0.0), (1.0, 0.0)), ((-1.0, 0.0), (1.0, 0.0)),
+                                        ((1.0, 0.0), None), (None, (0.0, 0.0))])
+def test_crt_alpha_beta_forms(cuda_lib, alpha, beta):
+    """alpha = +-1 with beta in {0, 1} (the specialised epilogues), alpha = 1
+    with a general beta and a general alpha with beta = 0."""
+    c = datagen.gemm_case(745, "N", "T", 150, 90, 200, pad=1)
+    if alpha is not None:
+        c.alpha = alpha
+    if beta is not None:
+        c.beta = beta
+    got, _ = run_crt(cuda_lib, c)
+    assert check_against_exact(c, got) <= 1.0
+
+
+@pytest.mark.parametrize("c_exp", [60, -60, 600])
+def test_crt_c_far_from_the_product(cuda_lib, c_exp):
+    """|C| about 2^c_exp times |alpha A B|: the aligned sum of the epilogue
+    over its whole exponent range."""
+    c = datagen.gemm_case(746 + c_exp, "N", "N", 96, 80, 120)
+    c.C = (c.C[0] * 2.0 ** c_exp, c.C[1] * 2.0 ** c_exp)
+    got, _ = run_crt(cuda_lib, c)
+    assert check_against_exact(c, got) <= 1.0
+
+
+def test_crt_cancellation(cuda_lib):
+    """C = -(alpha A B rounded to dd), beta = 1: the result is the tiny
+    rounding residual, within the bound of the exact value."""
+    m, n, k = 64, 48, 100
+    c = datagen.gemm_case(747, "N", "N", m, n, k)
+    c.beta = (1.0, 0.0)
+    rows, cols = np.repeat(np.arange(m), n), np.tile(np.arange(n), m)
+    oh, ol = oracle.exact_gemm_entries(c.transa, c.transb, c.k, c.alpha, c.A, c.B, (0.0, 0.0),
+                                       None, rows, cols)
+    c.C = (np.asfortranarray(-oh.reshape(m, n)), np.asfortranarray(-ol.reshape(m, n)))
+    got, _ = run_crt(cuda_lib, c)
+    assert check_against_exact(c, got) <= 1.0
+    assert np.abs(got[0]).max() < 1e-25
+
+
+def test_crt_non_finite_c_entries(cuda_lib):
+    """Inf and NaN in C with beta != 0 give non-finite results at those
+    entries (dd arithmetic turns an infinite C into NaN: the error term of
+    beta c is inf - inf); the other entries meet the bound."""
+    m, n, k = 40, 30, 64
+    c = datagen.gemm_case(748, "N", "N", m, n, k)
+    C0 = (c.C[0].copy(order="F"), c.C[1].copy(order="F"))
+    C0[0][3, 4] = np.inf
+    C0[0][5, 6] = -np.inf
+    C0[0][7, 8] = np.nan
+    c.C = C0
+    got, _ = run_crt(cuda_lib, c)
+    assert not np.isfinite(got[0][3, 4]) and not np.isfinite(got[0][5, 6])
+    assert np.isnan(got[0][7, 8])
+    keep = np.ones((m, n), bool)
+    keep[3, 4] = keep[5, 6] = keep[7, 8] = False
+    rows, cols = np.nonzero(keep)
+    clean = datagen.gemm_case(748, "N", "N", m, n, k)
+    assert check_against_exact(clean, got, rows, cols) <= 1.0
