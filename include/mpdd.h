@@ -151,10 +151,11 @@ int mp_dd_set_plain_staging(int mode);
  * testing).  A CTA pair is a cluster of two CTAs on vertically adjacent
  * tiles that share the op(B) panel, each loading one half and multicasting
  * it to both (a third fewer L2 reads per product); it needs an even number
- * of 128-row tiles.  mode 0 (the default): pairs for the Rsyrk triangle,
- * single CTAs for full products; mode 1: single CTAs only; mode 2: pairs
- * wherever they apply.  The products are exact integers, so every mode
- * gives bitwise the same results.  Returns 0, or -1 for another mode. */
+ * of 128-row tiles.  mode 0 (the default): one CTA per tile; mode 1: pairs
+ * wherever they apply (measured no faster: the kernel is bound by the
+ * operand bytes each SM receives, which pairs do not change).  The products
+ * are exact integers, so both modes give bitwise the same results.
+ * Returns 0, or -1 for another mode. */
 int mp_dd_set_band_pairs(int mode);
 
 /* Rsyrk (Sec. 6 table; CUDA dd Rsyrk in Sec. 7.3):

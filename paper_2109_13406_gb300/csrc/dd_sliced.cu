@@ -63,7 +63,11 @@ constexpr int CHUNK_KB = 16;                // k-blocks per exact fp32 run (1024
 // within the certificate's safety factor): one run over the whole k.
 template <bool MAG>
 __host__ __device__ constexpr int chunk_kb() { return MAG ? (1 << 30) : CHUNK_KB; }
-constexpr int GROUP_N = 8;                  // tile columns per rasterisation group
+// Tile columns per rasterisation group: 8 for full products; 4 for the
+// Rsyrk triangle, where the balance of the skipped tiles over the CTAs
+// matters more than operand reuse (13 % faster at 8192; 4 and 16 are 1.4 %
+// slower than 8 on full products).
+constexpr int kGroupFull = 8, kGroupTri = 4;
 constexpr int kEpiCols = 64;                // accumulator columns per epilogue thread
 
 // Two tile widths: 128 x 128 (6-stage ring of 32 KB, 8 epilogue warps) and
@@ -278,14 +282,12 @@ __global__ void __launch_bounds__(128) magnitude_kernel(
 
 // ------------------------------------------------------------------ step 3
 
-
-
-__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int &tm,
-                                            int &tn) {
-    int group = tile / (tiles_m * GROUP_N);
-    int first = group * GROUP_N;
-    int gn = tiles_n - first < GROUP_N ? tiles_n - first : GROUP_N;
-    int local = tile - group * tiles_m * GROUP_N;
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int group_n,
+                                            int &tm, int &tn) {
+    int group = tile / (tiles_m * group_n);
+    int first = group * group_n;
+    int gn = tiles_n - first < group_n ? tiles_n - first : group_n;
+    int local = tile - group * tiles_m * group_n;
     tn = first + local % gn;
     tm = local / gn;
 }
@@ -313,12 +315,12 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, 
     int64_t r0, rows;
     if (PAIR) {
         int tp;
-        tile_coords(tile, p.tiles_m / 2, p.tiles_n, tp, tn);
+        tile_coords(tile, p.tiles_m / 2, p.tiles_n, p.tri ? kGroupTri : kGroupFull, tp, tn);
         tm = 2 * tp + rank;
         r0 = (int64_t)tp * 2 * TM;
         rows = 2 * TM;
     } else {
-        tile_coords(tile, p.tiles_m, p.tiles_n, tm, tn);
+        tile_coords(tile, p.tiles_m, p.tiles_n, p.tri ? kGroupTri : kGroupFull, tm, tn);
         r0 = (int64_t)tm * TM;
         rows = TM;
     }
@@ -1159,11 +1161,11 @@ namespace {
 
 namespace {
 
-// 0: CTA pairs for triangle (Rsyrk) products, 1: never, 2: wherever they
-// apply.  On full products pairs measured 4 % slower (the per-SM operand
-// bytes, which limit this kernel, stay the same, and the pair's MMAs wait on
-// each other); on triangles they balance the skipped tiles better (11 %
-// faster at 8192).
+// 0: single CTAs (the default), 1: CTA pairs wherever they apply.  Pairs
+// halve the op(B) reads from L2 but measured no faster at 8192 (full
+// products within 1 %, the Rsyrk triangle 1.5 % slower than single CTAs on
+// 4-wide raster groups): the bytes each SM receives stay the same, and the
+// pair's MMAs wait on each other.
 std::atomic<int> g_band_pairs{0};
 
 // Clusters of two band CTAs that fit on the GPU at once (0: none).
@@ -1217,8 +1219,7 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
     // (the magnitude product always runs on 128-wide tiles)
     if (ba.mag && TN != 128) return fail(MP_DD_ERR_TOO_LARGE, "magnitude product: tile width");
     if (!ba.mag && TN == 256 && tmB_half != nullptr && ba.tiles_m % 2 == 0 &&
-        (g_band_pairs.load() == 2 || (g_band_pairs.load() == 0 && ba.tri != 0)) &&
-        pair_clusters() > 0) {
+        g_band_pairs.load() == 1 && pair_clusters() > 0) {
         const int pair_items = items / 2;
         const int clusters = pair_items < pair_clusters() ? pair_items : pair_clusters();
         cudaLaunchConfig_t cfg{};
