@@ -75,6 +75,8 @@ constexpr ModWeights make_mod_weights() {
     return mw;
 }
 
+__constant__ ModWeights c_mod_weights = make_mod_weights();
+
 // The same weights, each duplicated into both halves of a float2, with the
 // packed constants of the quotient step: the residue kernel works on two
 // entries at once with the packed fp32 instructions (f32x2), whose lanes are
@@ -98,7 +100,8 @@ constexpr ModWeights2 make_mod_weights2() {
 
 __constant__ ModWeights2 c_mod_weights2 = make_mod_weights2();
 
-// 4 threads per (row, 16 consecutive k), 4 entries each, one 8-byte store
+// Residues of an op(X) whose rows are contiguous in memory, on the FP32
+// pipe: 4 threads per (row, 16 consecutive k), 4 entries each, one 8-byte store
 // per residue plane and thread (a quad of lanes writes one 32-byte sector).
 // Residues from the balanced digits d_t of X on the FP32 pipe:
 // s = sum_t d_t (256^(D-1-t) mod p) is an integer below 16 * 128 * 255 < 2^24,
@@ -109,7 +112,7 @@ __constant__ ModWeights2 c_mod_weights2 = make_mod_weights2();
 // lowest digit, in [-128, 127], is the residue.  The first N planes are
 // written (N and D from the call's certificate).
 template <int NP, int DG>
-__device__ __forceinline__ void residue_body(
+__device__ __forceinline__ void residue_rows_body(
     const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
     const unsigned long long *__restrict__ rmax, __half *__restrict__ R, int N) {
@@ -175,7 +178,7 @@ __device__ __forceinline__ void residue_body(
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128) residue_kernel(
+__global__ void __launch_bounds__(128) residue_rows_kernel(
     const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
     const unsigned long long *__restrict__ rmax, __half *__restrict__ R, const SplitPlan plan) {
@@ -184,13 +187,214 @@ __global__ void __launch_bounds__(128) residue_kernel(
     const int N = pk.count;
     switch (pk.width) {
         case 8 * 14:
-            residue_body<NP, 14>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            residue_rows_body<NP, 14>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
             break;
         case 8 * 15:
-            residue_body<NP, 15>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            residue_rows_body<NP, 15>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
             break;
         default:
-            residue_body<NP, 16>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            residue_rows_body<NP, 16>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N);
+            break;
+    }
+}
+
+// Residues on the tensor cores.  For an entry X (the scaled integer of
+// RNE(hi 2^s) + RNE(lo 2^s), |X| < 2^(8D-1) for D digit bytes) the biased
+// X' = X + 2^(8D-1) has D unsigned bytes x_t, and
+//     s_b = sum_t x_t (256^t mod p_b) - (2^(8D-1) mod p_b)
+// is congruent to X mod p_b with -255 <= s_b < 16 255^2 < 2^22.  Over 16
+// entries the sums are the product [16 entries x 16 bytes] x [16 bytes x 8
+// moduli], done by mma.sync m16n8k16: a byte is the fp16 1024 + x_t (exact)
+// and the fp32 accumulator of modulus b starts at -1024 sum_t (256^t mod
+// p_b) - (2^(8D-1) mod p_b), so it ends at exactly s_b (every partial sum an
+// integer below 2^23 in magnitude).  r = s - p rint(s / p) is then the
+// residue in [-(p-1)/2, (p-1)/2] for odd p: the fp32 quotient is within
+// |s / p| 2^-23 of s / p, below 1 / (2 p), while s / p, an integer over an
+// odd p, is never within 1 / (2 p) of a half-integer.  For p = 256 the
+// lowest byte of X, taken in [-128, 127], is the residue.  Moduli 1 .. N-1
+// sit in n-tiles of 8; the first N planes are written (N and D from the
+// call's certificate).
+//
+// A warp computes 32 entries: each lane forms X' of one entry, and the quad
+// exchanges words so that lane (g, q) holds bytes 2q, 2q+1, 2q+8, 2q+9 of
+// its four entries (the A fragments of two m16 tiles); its accumulators
+// then hold two moduli of four consecutive k, stored as one 8-byte write
+// per modulus.  Entries: rows r, columns l of op(X); with l contiguous in
+// memory (row_contig = 0) a warp takes 32 consecutive l of one row, else 4
+// consecutive l of 8 consecutive rows.
+constexpr int kResNT = (kMaxMod - 1 + 7) / 8;   // n-tiles of moduli 1 .. 39
+
+// D = A B + C for one m16n8k16 tile: fp16 A (row) and B (col), fp32 C / D.
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint2 b,
+                                          const float (&c)[4]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%10,%11,%12,%13};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y), "f"(c[0]), "f"(c[1]),
+          "f"(c[2]), "f"(c[3]));
+}
+
+struct ResLane {     // per n-tile and lane: B fragment, accumulator starts,
+    uint32_t b0, b1; // and the reduction constants of the lane's 2 moduli
+    float init0, init1;
+    float4 inv, negp;   // {1/p0, 1/p0, 1/p1, 1/p1}, {-p0, -p0, -p1, -p1}
+};
+
+__device__ __forceinline__ uint32_t res_weight(int b, int t, int N, int DG) {
+    // 256^t mod p_b (0 past N or past the digit count); plane 0 is not here
+    return (b < N && t < DG) ? (uint32_t)c_mod_weights.w[b][kMaxDigits - 1 - t] : 0u;
+}
+
+__device__ void res_setup(int N, int DG, ResLane *tab) {
+    for (int x = threadIdx.x; x < kResNT * 32; x += blockDim.x) {
+        const int lane = x % 32, nt = x / 32, g = lane >> 2, q = lane & 3;
+        const int bm = 1 + 8 * nt + g;   // B column g
+        auto h = [&](int t) {
+            return (uint32_t)__half_as_ushort(__uint2half_rn(res_weight(bm, t, N, DG)));
+        };
+        ResLane L;
+        L.b0 = h(2 * q) | (h(2 * q + 1) << 16);
+        L.b1 = h(2 * q + 8) | (h(2 * q + 9) << 16);
+        float init[2], inv[2], negp[2];
+        for (int e = 0; e < 2; ++e) {
+            const int m = 1 + 8 * nt + 2 * q + e;   // C column 2q + e
+            init[e] = inv[e] = negp[e] = 0.0f;
+            if (m < N) {
+                const int pm = modulus(m);
+                uint32_t ws = 0;
+                for (int t = 0; t < DG; ++t) ws += res_weight(m, t, N, DG);
+                const uint32_t bias = (128u * res_weight(m, DG - 1, N, DG)) % (uint32_t)pm;
+                init[e] = -1024.0f * (float)ws - (float)bias;   // exact: below 2^23
+                inv[e] = c_mod_weights.inv[m];
+                negp[e] = -(float)pm;
+            }
+        }
+        L.init0 = init[0];
+        L.init1 = init[1];
+        L.inv = make_float4(inv[0], inv[0], inv[1], inv[1]);
+        L.negp = make_float4(negp[0], negp[0], negp[1], negp[1]);
+        tab[x] = L;
+    }
+}
+
+template <int DG>
+__device__ __forceinline__ void residue_warp(
+    const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
+    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+    const unsigned long long *__restrict__ rmax, __half *__restrict__ R, int N,
+    const ResLane *tab) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int64_t lchunks = row_contig ? k_pad / 4 : k_pad / 32;
+    const int64_t items = row_contig ? (rows_pad / 8) * lchunks : rows_pad * lchunks;
+    const int ntiles = (N - 1 + 7) / 8;
+    const uint32_t sel = (q & 1) ? 0x4342u : 0x4140u;   // halfword q&1 as two fp16 1024 + x
+    const float2 magic{12582912.0f, 12582912.0f}, nmagic{-12582912.0f, -12582912.0f};
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; item < items;
+         item += (int64_t)gridDim.x * (blockDim.x / 32)) {
+        // this lane's entry and the four entries (same row, consecutive l) it stores
+        const int64_t a = item / lchunks, c = item - a * lchunks;
+        const int64_t row = row_contig ? 8 * a + g : a;
+        const int64_t lbase = row_contig ? 4 * c : 32 * c + 4 * g;
+        const int64_t l = lbase + q;
+        double hi = 0.0, lo = 0.0;
+        int e = 0;
+        if (row < rows) {
+            e = scale_exponent(rmax[row]);
+            if (l < k) {
+                const int64_t off = row_contig ? (row + l * ld) : (l + row * ld);
+                hi = Xh[off];
+                lo = Xl[off];
+            }
+        }
+        const int shift = 8 * DG - e;
+        const unsigned __int128 Xb = (unsigned __int128)(scaled_round(hi, shift) +
+                                                         scaled_round(lo, shift)) +
+                                     ((unsigned __int128)1 << (8 * DG - 1));
+        const uint32_t w0 = (uint32_t)Xb, w1 = (uint32_t)(Xb >> 32), w2 = (uint32_t)(Xb >> 64),
+                       w3 = (uint32_t)(Xb >> 96);
+        // words q/2 and 2 + q/2 of the quad's four entries
+        uint32_t lw[4], hw[4];
+#pragma unroll
+        for (int E = 0; E < 4; ++E) {
+            const int src = (lane & ~3) | E;
+            const uint32_t x0 = __shfl_sync(0xFFFFFFFFu, w0, src);
+            const uint32_t x1 = __shfl_sync(0xFFFFFFFFu, w1, src);
+            const uint32_t x2 = __shfl_sync(0xFFFFFFFFu, w2, src);
+            const uint32_t x3 = __shfl_sync(0xFFFFFFFFu, w3, src);
+            lw[E] = (q >> 1) ? x1 : x0;
+            hw[E] = (q >> 1) ? x3 : x2;
+        }
+        // plane 0 (p = 256): the lowest byte of X, signed; lane q = 0 holds it for all four
+        if (q == 0) {
+            const __half2 h01 = __floats2half2_rn((float)(int8_t)(lw[0] & 0xFFu),
+                                                  (float)(int8_t)(lw[1] & 0xFFu));
+            const __half2 h23 = __floats2half2_rn((float)(int8_t)(lw[2] & 0xFFu),
+                                                  (float)(int8_t)(lw[3] & 0xFFu));
+            *reinterpret_cast<uint2 *>(R + row * k_pad + lbase) =
+                make_uint2(*reinterpret_cast<const uint32_t *>(&h01),
+                           *reinterpret_cast<const uint32_t *>(&h23));
+        }
+        // A fragments of tile t: row g = entry 2t, row g + 8 = entry 2t + 1
+        uint32_t A[2][4];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            A[t][0] = __byte_perm(lw[2 * t], 0x64646464u, sel);
+            A[t][1] = __byte_perm(lw[2 * t + 1], 0x64646464u, sel);
+            A[t][2] = __byte_perm(hw[2 * t], 0x64646464u, sel);
+            A[t][3] = __byte_perm(hw[2 * t + 1], 0x64646464u, sel);
+        }
+#pragma unroll
+        for (int nt = 0; nt < kResNT; ++nt) {
+            if (nt >= ntiles) break;
+            const ResLane L = tab[nt * 32 + lane];
+            const float c0[4] = {L.init0, L.init1, L.init0, L.init1};
+            float acc[2][4];
+            const uint2 bf = make_uint2(L.b0, L.b1);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) mma_16816(acc[t], A[t], bf, c0);
+            const float2 inv0{L.inv.x, L.inv.y}, inv1{L.inv.z, L.inv.w};
+            const float2 np0{L.negp.x, L.negp.y}, np1{L.negp.z, L.negp.w};
+#pragma unroll
+            for (int e2 = 0; e2 < 2; ++e2) {   // the lane's moduli 1 + 8nt + 2q + e2
+                const int m = 1 + 8 * nt + 2 * q + e2;
+                uint32_t packed[2];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const float2 s2{acc[t][e2], acc[t][2 + e2]};   // entries 2t, 2t + 1
+                    const float2 qn =
+                        __fadd2_rn(__ffma2_rn(s2, e2 ? inv1 : inv0, magic), nmagic);
+                    const float2 rr = __ffma2_rn(e2 ? np1 : np0, qn, s2);
+                    const __half2 hv = __float22half2_rn(rr);
+                    packed[t] = *reinterpret_cast<const uint32_t *>(&hv);
+                }
+                if (m < N)
+                    *reinterpret_cast<uint2 *>(R + ((int64_t)m * rows_pad + row) * k_pad + lbase) =
+                        make_uint2(packed[0], packed[1]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) residue_kernel(
+    const double *__restrict__ Xh, const double *__restrict__ Xl, int64_t ld, int row_contig,
+    int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
+    const unsigned long long *__restrict__ rmax, __half *__restrict__ R, const SplitPlan plan) {
+    __shared__ ResLane tab[kResNT * 32];
+    const PlanPick pk = plan_choice(plan);
+    if (pk.c < 0) return;
+    const int N = pk.count, DG = pk.width / 8;
+    res_setup(N, DG, tab);
+    __syncthreads();
+    switch (DG) {
+        case 14:
+            residue_warp<14>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N, tab);
+            break;
+        case 15:
+            residue_warp<15>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N, tab);
+            break;
+        default:
+            residue_warp<16>(Xh, Xl, ld, row_contig, rows, k, rows_pad, k_pad, rmax, R, N, tab);
             break;
     }
 }
@@ -565,32 +769,44 @@ CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
 }
 
 template <int NP>
-void launch_residues_np(const double *Xh, const double *Xl, int64_t ld, int rc, int64_t rows,
+void launch_residues_rows(const double *Xh, const double *Xl, int64_t ld, int rc, int64_t rows,
                         int64_t k, int64_t rows_pad, int64_t k_pad,
                         const unsigned long long *rmax, __half *R, const SplitPlan &plan,
                         cudaStream_t st) {
     dim3 grid((unsigned)ceil_div(rows_pad, 32), (unsigned)(k_pad / 16));
-    residue_kernel<NP><<<grid, 128, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R,
+    residue_rows_kernel<NP><<<grid, 128, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R,
                                              plan);
 }
 
-// Residues for up to Nmax moduli (the plan's widest candidate).
+// Residues for up to Nmax moduli (the plan's widest candidate): one warp
+// per 32 entries, blocks resident at once, looping.
 int launch_residues(int Nmax, const double *Xh, const double *Xl, int64_t ld, int rc,
                     int64_t rows, int64_t k, int64_t rows_pad, int64_t k_pad,
                     const unsigned long long *rmax, __half *R, const SplitPlan &plan,
                     cudaStream_t st) {
-    if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for residues");
-    switch (Nmax / 2) {
-#define MPDD_RES_CASE(NP)                                                                 \
-    case NP:                                                                              \
-        launch_residues_np<NP>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R, plan, st); \
+    if (rc) {   // rows contiguous: the FP32 kernel (full-sector stores along k)
+        if (k_pad / 16 > 65535) return fail(MP_DD_ERR_TOO_LARGE, "k too large for residues");
+        switch (Nmax / 2) {
+#define MPDD_RES_CASE(NP)                                                                      \
+    case NP:                                                                                   \
+        launch_residues_rows<NP>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad, rmax, R, plan, st); \
         break;
-        MPDD_RES_CASE(14) MPDD_RES_CASE(15) MPDD_RES_CASE(16) MPDD_RES_CASE(17)
-        MPDD_RES_CASE(18) MPDD_RES_CASE(19) MPDD_RES_CASE(20)
+            MPDD_RES_CASE(14) MPDD_RES_CASE(15) MPDD_RES_CASE(16) MPDD_RES_CASE(17)
+            MPDD_RES_CASE(18) MPDD_RES_CASE(19) MPDD_RES_CASE(20)
 #undef MPDD_RES_CASE
-        default:
-            return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [28, 40]", Nmax);
+            default:
+                return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [28, 40]", Nmax);
+        }
+        return check_launch("residue_rows_kernel");
     }
+    if (Nmax < 2 || Nmax > kMaxMod)
+        return fail(MP_DD_ERR_TOO_LARGE, "residue count %d outside [2, %d]", Nmax, kMaxMod);
+    const int64_t warps = rows_pad * k_pad / 32;
+    int64_t blocks = ceil_div(warps, 8);
+    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
+    if (blocks < 1) blocks = 1;
+    residue_kernel<<<(unsigned)blocks, 256, 0, st>>>(Xh, Xl, ld, rc, rows, k, rows_pad, k_pad,
+                                                     rmax, R, plan);
     return check_launch("residue_kernel");
 }
 
