@@ -1145,12 +1145,15 @@ def run_sliced_workload(args):
         step()
         band.append(mp.mp_dd_sliced_phase_ms())
     mp.mp_dd_sliced_timing(False)
+    # the products the certified call ran: its moduli count (CRT) or the
+    # digit pairs of its slice count (sliced form), from the call's report
+    rep = mp.mp_dd_split_report(ws)
     if crt:
         L = mp.mp_dd_crt_layout(size, size, size)
-        products = len(L["moduli"])
+        products = rep["count"]
     else:
         L = mp.mp_dd_sliced_layout(size, size, size, S)
-        products = S * (S + 1) // 2
+        products = rep["count"] * (rep["count"] + 1) // 2
     band_ms = sum(b[1] for b in band) / len(band)
     flops = 2.0 * L["m_pad"] * L["n_pad"] * L["k_pad"] * products
     peak, src = tensor_peak_tflops()
