@@ -148,14 +148,14 @@ int mp_dd_set_plain_staging(int mode);
 
 /* Scheduling of the split-precision band / residue products on 128 x 256
  * tiles (no counterpart in the manual; process-wide, for tuning and
- * testing).  A CTA pair is a cluster of two CTAs on vertically adjacent
- * tiles that share the op(B) panel, each loading one half and multicasting
- * it to both (a third fewer L2 reads per product); it needs an even number
- * of 128-row tiles.  mode 0 (the default): one CTA per tile; mode 1: pairs
- * wherever they apply (measured no faster: the kernel is bound by the
- * operand bytes each SM receives, which pairs do not change).  The products
- * are exact integers, so both modes give bitwise the same results.
- * Returns 0, or -1 for another mode. */
+ * testing).  A CTA pair is a cluster of two CTAs computing a 256 x 256 tile
+ * with the 2-SM tensor-core MMA: each CTA holds its 128 rows of op(A) and
+ * half of the op(B) panel, a third fewer operand bytes per SM; it needs an
+ * even number of 128-row tiles.  mode 0 (the default): pairs for the Rsyrk
+ * triangle (4 % faster at 8192), one CTA per tile for full products (where
+ * pairs measured 2.5 % slower); mode 1: pairs wherever they apply; mode 2:
+ * never.  The products are exact integers, so every mode gives bitwise the
+ * same results.  Returns 0, or -1 for another mode. */
 int mp_dd_set_band_pairs(int mode);
 
 /* Rsyrk (Sec. 6 table; CUDA dd Rsyrk in Sec. 7.3):

@@ -403,8 +403,8 @@ def mp_dd_set_plain_staging(mode: int) -> None:
 
 
 def mp_dd_set_band_pairs(mode: int) -> None:
-    """CTA pairs for 256-wide band products: 0 never (the default), 1
-    wherever they apply."""
+    """CTA pairs (2-SM MMA) for 256-wide band products: 0 for the Rsyrk
+    triangle (the default), 1 wherever they apply, 2 never."""
     _check(_LIB.mp_dd_set_band_pairs(int(mode)), "mp_dd_set_band_pairs")
 
 

@@ -776,7 +776,7 @@ int mp_dd_set_plain_staging(int mode) {
 
 int mp_dd_set_band_pairs(int mode) {
     clear_error();
-    if (mode < 0 || mode > 1) return fail(-1, "set_band_pairs: mode must be 0 or 1");
+    if (mode < 0 || mode > 2) return fail(-1, "set_band_pairs: mode must be 0, 1 or 2");
     set_band_pairs(mode);
     return 0;
 }

@@ -72,14 +72,16 @@ constexpr int kEpiCols = 64;                // accumulator columns per epilogue 
 
 // Two tile widths: 128 x 128 (6-stage ring of 32 KB, 8 epilogue warps) and
 // 128 x 256 (4 stages of 48 KB, 16 epilogue warps, all 512 TMEM columns);
-// the wider tile reads 25 % fewer operand bytes per flop.
-template <int TN>
+// the wider tile reads 25 % fewer operand bytes per flop.  PAIR: a CTA pair
+// on a 256 x 256 tile with the 2-SM MMA, each CTA holding its 128 rows of A
+// and 128 of the 256 rows of B: 32 KB per stage and SM, 6 stages.
+template <int TN, bool PAIR = false>
 struct BandCfg {
-    static constexpr int STAGES = TN == 256 ? 4 : 6;
+    static constexpr int STAGES = PAIR ? 6 : (TN == 256 ? 4 : 6);
     static constexpr int EPI_WARPS = TN / kEpiCols * 4;   // 4 lane quadrants
     static constexpr int THREADS = 32 * (2 + EPI_WARPS);  // producer, MMA, epilogue
     static constexpr int TMEM_COLS = 2 * TN;              // two fp32 accumulators
-    static constexpr uint32_t A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2;
+    static constexpr uint32_t A_BYTES = TM * TK * 2, B_BYTES = (PAIR ? TN / 2 : TN) * TK * 2;
     static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024 + 256;
 };
@@ -406,14 +408,18 @@ __device__ __forceinline__ void certificate_margin(const BandArgs &p,
 // MAG: the certificate's magnitude product (bf16 operands, fp32 sums, the
 // margin d_ij of every entry reduced to its minimum); otherwise the integer
 // band products with the band count taken from the call's plan.
-// PAIR: a cluster of two CTAs on vertically adjacent tiles with the same
-// columns.  Each CTA loads its own op(A) panel and one half of the shared
-// op(B) panel, delivered to both CTAs by a multicast copy (tmB's box is
-// TN / 2 rows), so a stage costs 32 KB of L2 reads per CTA instead of 48.
-// A stage is refilled only after both CTAs' MMAs have consumed it: every
-// MMA commit arrives on the "empty" barriers of both CTAs.
+// PAIR: a cluster of two CTAs on a 256 x 256 tile (vertically adjacent
+// 128-row halves, the same 256 columns) multiplied by the 2-SM MMA.  Each
+// CTA copies its own op(A) panel and one half of the op(B) panel (tmB's box
+// is TN / 2 rows) into its shared memory, with completion on the leader's
+// (rank 0) "full" barrier, which expects both CTAs' bytes.  The leader's MMA
+// thread issues the pair MMAs; its commits arrive on the "empty" and
+// "accumulator full" barriers of both CTAs.  Each CTA's epilogue drains its
+// own tensor memory and releases a buffer with one arrival per warp on the
+// leader's "accumulator empty" barrier.  Every tcgen05 operation of this
+// instantiation is of the pair form.
 template <int TN, bool MAG, bool PAIR = false>
-__global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
+__global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
     band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const BandArgs p) {
     int S = p.S;
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         if (pk.c < 0) return;
         S = pk.count;
     }
-    using Cfg = BandCfg<TN>;
+    using Cfg = BandCfg<TN, PAIR>;
     constexpr int STAGES = Cfg::STAGES;
     constexpr uint32_t kStageBytes = Cfg::STAGE_BYTES;
     constexpr int kTmemCols = Cfg::TMEM_COLS;
@@ -449,19 +455,25 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], PAIR ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 32 * Cfg::EPI_WARPS);
+            // PAIR: one arrival per epilogue warp of either CTA
+            mbar_init(&acce[b], PAIR ? 2 * Cfg::EPI_WARPS : 32 * Cfg::EPI_WARPS);
         }
         mbar_init(fin, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_holder, kTmemCols);
-        tmem_relinquish();
+        if (PAIR) {
+            tmem_alloc_pair(tmem_holder, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_holder, kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -494,20 +506,25 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                                 ok = false;
                                 break;
                             }
-                            mbar_arrive_expect_tx(&full[s], kStageBytes);
-                            tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, &full[s], kb * TK, ya);
-                            if (PAIR)
-                                tma_load_2d_multicast(
-                                    sB + s * Cfg::B_BYTES + rank * (Cfg::B_BYTES / 2), &tmB,
-                                    &full[s], kb * TK, yb + rank * (TN / 2), (uint16_t)3);
-                            else
+                            if (PAIR) {
+                                // both CTAs' copies complete on the leader's barrier,
+                                // which the leader arms for both
+                                const uint32_t fl = cluster_map(&full[s], 0);
+                                if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * kStageBytes);
+                                tma_load_2d_pair(sA + s * Cfg::A_BYTES, &tmA, fl, kb * TK, ya);
+                                tma_load_2d_pair(sB + s * Cfg::B_BYTES, &tmB, fl, kb * TK,
+                                                 yb + rank * (TN / 2));
+                            } else {
+                                mbar_arrive_expect_tx(&full[s], kStageBytes);
+                                tma_load_2d(sA + s * Cfg::A_BYTES, &tmA, &full[s], kb * TK, ya);
                                 tma_load_2d(sB + s * Cfg::B_BYTES, &tmB, &full[s], kb * TK, yb);
+                            }
                         }
                     }
             }
             if (PAIR && ok) {
-                // both MMAs' last arrivals on this CTA's barriers have landed
-                // before it may exit
+                // the leader's last commits on this CTA's barriers have
+                // landed before it may exit
                 const uint32_t first = it > STAGES ? it - STAGES : 0;
                 for (uint32_t j = first; j < it && ok; ++j)
                     ok = mbar_wait(&empty[j % STAGES], (j / STAGES) & 1, abort_flag);
@@ -525,9 +542,10 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = MAG ? idesc_bf16_f32(TM, TN) : idesc_f16_f32(TM, TN);
+        // ---------------- MMA issuer (PAIR: the leader's, for both CTAs)
+        if (lane == 0 && (!PAIR || rank == 0)) {
+            const uint32_t idesc = MAG ? idesc_bf16_f32(TM, TN)
+                                       : idesc_f16_f32(PAIR ? 2 * TM : TM, TN);
             uint32_t it = 0, chunk = 0;
             bool ok = true;
             for (int item = item0; item < num_items && ok; item += item_step) {
@@ -560,23 +578,37 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                             const uint32_t a0 = smem_u32(sA + s * Cfg::A_BYTES);
                             const uint32_t b0 = smem_u32(sB + s * Cfg::B_BYTES);
 #pragma unroll
-                            for (int kk = 0; kk < TK / 16; ++kk)
-                                mma_f16(d, desc_sw128_kmajor(a0 + kk * 32),
-                                        desc_sw128_kmajor(b0 + kk * 32), idesc,
-                                        (first && kk == 0) ? 0u : 1u);
-                            if (PAIR)
-                                mma_commit_multicast(&empty[s], (uint16_t)3);
-                            else
+                            for (int kk = 0; kk < TK / 16; ++kk) {
+                                if (PAIR)
+                                    mma_f16_pair(d, desc_sw128_kmajor(a0 + kk * 32),
+                                                 desc_sw128_kmajor(b0 + kk * 32), idesc,
+                                                 (first && kk == 0) ? 0u : 1u);
+                                else
+                                    mma_f16(d, desc_sw128_kmajor(a0 + kk * 32),
+                                            desc_sw128_kmajor(b0 + kk * 32), idesc,
+                                            (first && kk == 0) ? 0u : 1u);
+                            }
+                            if (PAIR) {
+                                mma_commit_pair(&empty[s], (uint16_t)3);
+                                if (last) {
+                                    mma_commit_pair(&accf[buf], (uint16_t)3);
+                                    ++chunk;
+                                }
+                            } else {
                                 mma_commit(&empty[s]);
-                            if (last) {
-                                mma_commit(&accf[buf]);
-                                ++chunk;
+                                if (last) {
+                                    mma_commit(&accf[buf]);
+                                    ++chunk;
+                                }
                             }
                         }
                 }
             }
             // every issued MMA has completed before the tensor memory is freed
-            mma_commit(fin);
+            if (PAIR)
+                mma_commit_pair(fin, (uint16_t)1);
+            else
+                mma_commit(fin);
             long long t0 = clock64();
             while (!mbar_try_wait(fin, 0) && clock64() - t0 < kWaitCycles) {
             }
@@ -622,7 +654,12 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
                         }
                     }
                     tc_fence_before();
-                    mbar_arrive(&acce[buf]);
+                    if (PAIR) {   // one arrival per warp on the leader's barrier
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cluster(cluster_map(&acce[buf], 0));
+                    } else {
+                        mbar_arrive(&acce[buf]);
+                    }
                 }
                 if (!ok) break;
                 if (MAG) {
@@ -652,7 +689,12 @@ __global__ void __launch_bounds__(BandCfg<TN>::THREADS, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+    if (PAIR) {
+        cluster_sync();   // both CTAs done with the pair's tensor memory
+        if (warp == 1) tmem_dealloc_pair(tmem, kTmemCols);
+    } else if (warp == 1) {
+        tmem_dealloc(tmem, kTmemCols);
+    }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, MP_DD_ERR_TIMEOUT);
     if (PAIR) cluster_sync();   // no CTA leaves while its peer may still signal it
 }
@@ -1161,11 +1203,10 @@ namespace {
 
 namespace {
 
-// 0: single CTAs (the default), 1: CTA pairs wherever they apply.  Pairs
-// halve the op(B) reads from L2 but measured no faster at 8192 (full
-// products within 1 %, the Rsyrk triangle 1.5 % slower than single CTAs on
-// 4-wide raster groups): the bytes each SM receives stay the same, and the
-// pair's MMAs wait on each other.
+// 0: CTA pairs (the 2-SM MMA) for the Rsyrk triangle, single CTAs for full
+// products; 1: pairs wherever they apply; 2: never.  At 8192 pairs take the
+// triangle's band phase from 13.0 to 12.5 ms and the full product's from
+// 20.5 to 21.0 ms.
 std::atomic<int> g_band_pairs{0};
 
 // Clusters of two band CTAs that fit on the GPU at once (0: none).
@@ -1173,7 +1214,7 @@ int pair_clusters() {
     static int count = -1;
     static std::once_flag once;
     std::call_once(once, [] {
-        using Cfg = BandCfg<256>;
+        using Cfg = BandCfg<256, true>;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2 * sm_count());
         cfg.blockDim = dim3(Cfg::THREADS);
@@ -1211,7 +1252,8 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
         cudaFuncSetAttribute(band_gemm_kernel<128, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
         cudaFuncSetAttribute(band_gemm_kernel<256, false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<256>::SMEM);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)BandCfg<256, true>::SMEM);
     });
     const int tiles = ba.tiles_m * ba.tiles_n;
     const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords (S: the most bands)
@@ -1219,13 +1261,14 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
     // (the magnitude product always runs on 128-wide tiles)
     if (ba.mag && TN != 128) return fail(MP_DD_ERR_TOO_LARGE, "magnitude product: tile width");
     if (!ba.mag && TN == 256 && tmB_half != nullptr && ba.tiles_m % 2 == 0 &&
-        g_band_pairs.load() == 1 && pair_clusters() > 0) {
+        (g_band_pairs.load() == 1 || (g_band_pairs.load() == 0 && ba.tri != 0)) &&
+        pair_clusters() > 0) {
         const int pair_items = items / 2;
         const int clusters = pair_items < pair_clusters() ? pair_items : pair_clusters();
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2 * clusters);
-        cfg.blockDim = dim3(BandCfg<256>::THREADS);
-        cfg.dynamicSmemBytes = BandCfg<256>::SMEM;
+        cfg.blockDim = dim3(BandCfg<256, true>::THREADS);
+        cfg.dynamicSmemBytes = BandCfg<256, true>::SMEM;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;

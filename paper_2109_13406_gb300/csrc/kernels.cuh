@@ -52,7 +52,7 @@ int plain_tile_r(const GemmArgs &p);
 void set_plain_staging(int mode);
 int plain_staging();
 // CTA pairs for the 256-wide split-precision band products (dd_sliced.cu):
-// 0 never (the default), 1 wherever they apply.
+// 0 for triangle products (the default), 1 wherever they apply, 2 never.
 void set_band_pairs(int mode);
 
 // FP64 issue-rate microbenchmark; *rate in FP64 instructions per second.

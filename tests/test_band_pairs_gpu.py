@@ -1,8 +1,8 @@
 """CTA pairs for the 256-wide band / residue products (GPU).
 
-The products are exact integers, so two CTAs sharing the op(B) panel by a
-multicast copy must give bitwise the same residue products and results as
-one CTA per tile: checked on the residue form (Rgemm, ragged edges, the
+The products are exact integers, so a CTA pair computing a 256 x 256 tile
+with the 2-SM MMA must give bitwise the same residue products and results
+as one CTA per 128 x 256 tile: checked on the residue form (Rgemm, ragged edges, the
 Rsyrk triangles) and the sliced form, plus one odd tile count that keeps
 single CTAs.  Results are also held against the oracle's exact tier.
 """
@@ -43,7 +43,7 @@ def test_crt_pairs_bitwise_equal_single(cuda_lib, shape):
     m, n, k = shape
     c = datagen.gemm_case(780 + k, "N", "T", m, n, k, pad=1)
     got1, p1 = crt_once(cuda_lib, c, 1)
-    got0, p0 = crt_once(cuda_lib, c, 0)
+    got0, p0 = crt_once(cuda_lib, c, 2)
     assert np.array_equal(p1, p0)
     assert np.array_equal(got1[0], got0[0]) and np.array_equal(got1[1], got0[1])
     rr, cc = sample_blocks(m, n, bs=16, count=6)
@@ -60,7 +60,7 @@ def test_rsyrk_crt_pairs_bitwise_equal_single(cuda_lib, uplo):
     C = datagen.dd_matrix(g, n, n, n)
     al, be = datagen.dd_scalar(g), datagen.dd_scalar(g)
     outs = []
-    for pairs in (1, 0):
+    for pairs in (1, 2):
         mp.mp_dd_set_band_pairs(pairs)
         try:
             dA, dC = dev(A), dev(C)
@@ -87,7 +87,7 @@ def test_sliced_pairs_bitwise_equal_single(cuda_lib):
     m, n, k = 4096, 2560, 128
     c = datagen.gemm_case(795, "N", "N", m, n, k)
     outs = []
-    for pairs in (1, 0):
+    for pairs in (1, 2):
         mp.mp_dd_set_band_pairs(pairs)
         try:
             A, B, C = dev(c.A), dev(c.B), dev(c.C)
@@ -105,6 +105,6 @@ def test_sliced_pairs_bitwise_equal_single(cuda_lib):
 
 
 def test_set_band_pairs_rejects_other_modes(cuda_lib):
-    assert cuda_lib.lib().mp_dd_set_band_pairs(2) == -1
+    assert cuda_lib.lib().mp_dd_set_band_pairs(3) == -1
     assert cuda_lib.lib().mp_dd_set_band_pairs(-1) == -1
     assert cuda_lib.lib().mp_dd_set_band_pairs(0) == 0
