@@ -726,7 +726,7 @@ int crt_candidates(int64_t k, int *widths, int *counts) {
 struct CrtLayout {
     int N;                                 // moduli the workspace holds (the widest candidate)
     int64_t m_pad, n_pad, k_pad;
-    size_t off_rowmax, off_colmax, off_ra, off_rb, off_res, off_ma, off_mb, total;
+    size_t off_rowmax, off_colmax, off_ra, off_rb, off_res, off_ma, off_mb, off_tri, total;
 };
 
 size_t align1k(size_t x) { return (x + 1023) / 1024 * 1024; }
@@ -764,6 +764,8 @@ CrtLayout crt_layout(int64_t m, int64_t n, int64_t k, bool sym = false) {
     L.off_ma = o; o = align1k(o + 2 * (size_t)L.m_pad * L.k_pad);
     L.off_mb = sym ? L.off_ma : o;
     if (!sym) o = align1k(o + 2 * (size_t)L.n_pad * L.k_pad);
+    L.off_tri = o;   // the band launches' triangle table (Rsyrk form)
+    if (sym) o = align1k(o + 4 * (size_t)kTriMax);
     L.total = o;
     return L;
 }
@@ -914,8 +916,9 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (!sym && (rc = launch_magnitude(p.bh, p.ldb, b_rc, p.n, p.k, L.n_pad, L.k_pad, cmax,
                                        w + L.off_mb, hdr, nullptr, st)))
         return rc;
+    int *tri_table = (p.tri && sym) ? reinterpret_cast<int *>(w + L.off_tri) : nullptr;
     if ((rc = launch_certificate(p, w + L.off_ma, w + L.off_mb, L.m_pad, L.n_pad, L.k_pad, TN,
-                                 rmax, cmax, hdr, st)))
+                                 rmax, cmax, hdr, st, tri_table)))
         return rc;
     if ((rc = launch_residues(L.N, p.ah, p.al, p.lda, a_rc, p.m, p.k, L.m_pad, L.k_pad, rmax,
                               RA, plan, st)))
@@ -944,6 +947,7 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     ba.status = &hdr->status;
     ba.diag = 1;
     ba.tri = p.tri;
+    ba.tri_cum = tri_table;
     ba.plan = plan;
     for (int i = 0; i < L.N; ++i) ba.moduli[i] = modulus(i);
     if ((rc = launch_band(tmA, tmB, ba, TN, st, &tmB_half))) return rc;

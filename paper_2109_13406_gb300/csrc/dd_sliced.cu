@@ -83,7 +83,10 @@ struct BandCfg {
     static constexpr int TMEM_COLS = 2 * TN;              // two fp32 accumulators
     static constexpr uint32_t A_BYTES = TM * TK * 2, B_BYTES = (PAIR ? TN / 2 : TN) * TK * 2;
     static constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+    // stages, 1 KB alignment slack, barriers; SMEM_TRI adds the triangle
+    // table (only launches that use it reserve it: the rest keep the L1)
     static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024 + 256;
+    static constexpr size_t SMEM_TRI = SMEM + 4 * kTriMax;
 };
 
 }  // namespace
@@ -303,7 +306,8 @@ __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, 
 // band range, so every role skips them alike.
 template <int TN, bool PAIR>
 __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, int num_tiles,
-                                            int rank, int &tm, int &tn, int &b0, int &b1) {
+                                            int rank, const int *tri_s, int &tm, int &tn,
+                                            int &b0, int &b1) {
     int tile = item;
     b0 = 0;
     b1 = S;
@@ -311,6 +315,23 @@ __device__ __forceinline__ void item_coords(const BandArgs &p, int S, int item, 
         b0 = item / num_tiles;
         b1 = b0 + 1;
         tile = item % num_tiles;
+    }
+    if (tri_s != nullptr) {
+        // tile-th tile inside the triangle: the last (group, row unit) whose
+        // cumulative count is at most tile, then the column within it
+        int lo = 0, hi = p.tri_rows;   // tri_s[lo] <= tile < tri_s[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (tri_s[mid] <= tile) lo = mid;
+            else hi = mid;
+        }
+        const int grp = lo / p.tri_units, u = lo - grp * p.tri_units;
+        const TriGeom g{p.tri, PAIR ? 2 * TM : TM, TN, p.tiles_n, kGroupTri};
+        int c_lo, c_hi;
+        tri_range(g, grp, u, c_lo, c_hi);
+        tn = c_lo + (tile - tri_s[lo]);
+        tm = PAIR ? 2 * u + rank : u;
+        return;
     }
     // a CTA pair takes two vertically adjacent tiles (one per CTA) and skips
     // a triangle item only when both tiles lie outside
@@ -418,7 +439,9 @@ __device__ __forceinline__ void certificate_margin(const BandArgs &p,
 // own tensor memory and releases a buffer with one arrival per warp on the
 // leader's "accumulator empty" barrier.  Every tcgen05 operation of this
 // instantiation is of the pair form.
-template <int TN, bool MAG, bool PAIR = false>
+// TRI: the work items are the tiles inside the triangle (p.tri_cum); the
+// other instantiations carry no code for it.
+template <int TN, bool MAG, bool PAIR = false, bool TRI = false>
 __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
     band_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                      const __grid_constant__ CUtensorMap tmB, const BandArgs p) {
@@ -446,6 +469,9 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
     uint64_t *fin = acce + 2;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(fin + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+    int *tri_s = TRI ? reinterpret_cast<int *>(smem + STAGES * kStageBytes + 256) : nullptr;
+    if (TRI)   // the triangle table, read by every role per item
+        for (int x = threadIdx.x; x <= p.tri_rows; x += blockDim.x) tri_s[x] = p.tri_cum[x];
 
     static_assert(!PAIR || (TN == 256 && !MAG), "CTA pairs: residue / digit products, 256 wide");
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -481,7 +507,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
     if (PAIR) cluster_sync();   // the peer's barriers exist before anything lands there
     const uint32_t tmem = *tmem_holder;
 
-    const int num_tiles = (PAIR ? p.tiles_m / 2 : p.tiles_m) * p.tiles_n;
+    const int num_tiles = TRI ? p.tri_tiles : (PAIR ? p.tiles_m / 2 : p.tiles_m) * p.tiles_n;
     const int KB = p.kb_count;
     const int num_items = p.diag ? num_tiles * S : num_tiles;
 
@@ -494,7 +520,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
             bool ok = true;
             for (int item = item0; item < num_items && ok; item += item_step) {
                 int tm, tn, b0, b1;
-                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
+                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tri_s, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b)
                     for (int t = p.diag ? b : 0; t <= b && ok; ++t) {
                         const int ya = (int)(t * p.m_pad) + tm * TM;
@@ -550,7 +576,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
             bool ok = true;
             for (int item = item0; item < num_items && ok; item += item_step) {
                 int tm, tn, b0, b1;
-                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
+                item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tri_s, tm, tn, b0, b1);
                 for (int b = b0; b < b1 && ok; ++b) {
                     const int steps = (p.diag ? 1 : b + 1) * KB;
                     int sidx = 0;
@@ -624,7 +650,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
         bool ok = true;
         for (int item = item0; item < num_items && ok; item += item_step) {
             int tm, tn, b0, b1;
-            item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tm, tn, b0, b1);
+            item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tri_s, tm, tn, b0, b1);
             for (int b = b0; b < b1 && ok; ++b) {
                 int32_t acc[kEpiCols];
 #pragma unroll
@@ -1053,7 +1079,8 @@ double ratio_lower(mp_dd beta, mp_dd alpha) {
 
 int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int64_t n_pad,
                        int64_t k_pad, int TN, const unsigned long long *rmax,
-                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st) {
+                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st,
+                       int *tri_table) {
     // 128-wide tiles whatever the product's own width (n_pad is a multiple
     // of 128 either way): the margin epilogue then has registers to spare
     (void)TN;
@@ -1095,6 +1122,7 @@ int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int
     // (|A||B|)_ij 2^-(e_i+f_j) with an eightfold margin on the additions.
     ba.c1 = (float)(1.0 - (double)(p.k + 1) * 0x1p-20);
     ba.dmin_out = &hdr->dmin;
+    ba.tri_cum = p.tri ? tri_table : nullptr;
     return launch_band(tmA, tmB, ba, TN, st);
 }
 
@@ -1203,6 +1231,67 @@ namespace {
 
 namespace {
 
+// The triangle table of launch_band: cum[x] = tiles inside the triangle
+// before (group, row unit) x in raster order, x = 0 .. rows (one block).
+__global__ void __launch_bounds__(256) tri_table_kernel(TriGeom g, int units, int rows,
+                                                        int *cum) {
+    __shared__ int part[256];
+    const int per = (rows + 255) / 256, x0 = threadIdx.x * per;
+    int s = 0;
+    for (int x = x0; x < x0 + per && x < rows; ++x) {
+        int lo, hi;
+        tri_range(g, x / units, x % units, lo, hi);
+        s += hi >= lo ? hi - lo + 1 : 0;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < 256; ++t) {
+            const int v = part[t];
+            part[t] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int x = x0; x < x0 + per && x < rows; ++x) {
+        cum[x] = run;
+        int lo, hi;
+        tri_range(g, x / units, x % units, lo, hi);
+        run += hi >= lo ? hi - lo + 1 : 0;
+    }
+    if (threadIdx.x == 255) cum[rows] = run;
+}
+
+// Geometry of the triangle table for a launch; 0 when the table does not
+// apply (no triangle, no table memory, or too many rows for shared memory).
+int tri_prepare(BandArgs &ba, int TN, bool pair, cudaStream_t st) {
+    if (!ba.tri || ba.tri_cum == nullptr) {
+        ba.tri_cum = nullptr;
+        return 0;
+    }
+    const TriGeom g{ba.tri, pair ? 2 * TM : TM, TN, ba.tiles_n, kGroupTri};
+    const int units = pair ? ba.tiles_m / 2 : ba.tiles_m;
+    const int groups = (ba.tiles_n + kGroupTri - 1) / kGroupTri;
+    const int rows = groups * units;
+    if (rows + 1 > kTriMax) {
+        ba.tri_cum = nullptr;
+        return 0;
+    }
+    int tiles = 0;
+    for (int x = 0; x < rows; ++x) {
+        int lo, hi;
+        tri_range(g, x / units, x % units, lo, hi);
+        tiles += hi >= lo ? hi - lo + 1 : 0;
+    }
+    ba.tri_rows = rows;
+    ba.tri_units = units;
+    ba.tri_tiles = tiles;
+    tri_table_kernel<<<1, 256, 0, st>>>(g, units, rows, ba.tri_cum);
+    return check_launch("tri_table_kernel");
+}
+
 // 0: CTA pairs (the 2-SM MMA) for the Rsyrk triangle, single CTAs for full
 // products; 1: pairs wherever they apply; 2: never.  At 8192 pairs take the
 // triangle's band phase from 13.0 to 12.5 ms and the full product's from
@@ -1245,30 +1334,37 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
                 cudaStream_t st, const CUtensorMap *tmB_half) {
     static std::once_flag attr_once;
     std::call_once(attr_once, [] {
-        cudaFuncSetAttribute(band_gemm_kernel<128, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
-        cudaFuncSetAttribute(band_gemm_kernel<256, false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<256>::SMEM);
-        cudaFuncSetAttribute(band_gemm_kernel<128, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BandCfg<128>::SMEM);
-        cudaFuncSetAttribute(band_gemm_kernel<256, false, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)BandCfg<256, true>::SMEM);
+        auto big = [](const void *f, size_t bytes) {
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        };
+        big((const void *)band_gemm_kernel<128, false>, BandCfg<128>::SMEM);
+        big((const void *)band_gemm_kernel<256, false>, BandCfg<256>::SMEM);
+        big((const void *)band_gemm_kernel<128, true>, BandCfg<128>::SMEM);
+        big((const void *)band_gemm_kernel<256, false, true>, BandCfg<256, true>::SMEM);
+        big((const void *)band_gemm_kernel<128, false, false, true>, BandCfg<128>::SMEM_TRI);
+        big((const void *)band_gemm_kernel<256, false, false, true>, BandCfg<256>::SMEM_TRI);
+        big((const void *)band_gemm_kernel<128, true, false, true>, BandCfg<128>::SMEM_TRI);
+        big((const void *)band_gemm_kernel<256, false, true, true>, BandCfg<256, true>::SMEM_TRI);
     });
-    const int tiles = ba.tiles_m * ba.tiles_n;
-    const int items = ba.diag ? tiles * ba.S : tiles;   // see item_coords (S: the most bands)
-    const int grid = items < sm_count() ? items : sm_count();
     // (the magnitude product always runs on 128-wide tiles)
     if (ba.mag && TN != 128) return fail(MP_DD_ERR_TOO_LARGE, "magnitude product: tile width");
-    if (!ba.mag && TN == 256 && tmB_half != nullptr && ba.tiles_m % 2 == 0 &&
-        (g_band_pairs.load() == 1 || (g_band_pairs.load() == 0 && ba.tri != 0)) &&
-        pair_clusters() > 0) {
-        const int pair_items = items / 2;
-        const int clusters = pair_items < pair_clusters() ? pair_items : pair_clusters();
+    const bool pair = !ba.mag && TN == 256 && tmB_half != nullptr && ba.tiles_m % 2 == 0 &&
+                      (g_band_pairs.load() == 1 || (g_band_pairs.load() == 0 && ba.tri != 0)) &&
+                      pair_clusters() > 0;
+    BandArgs b = ba;
+    int rc;
+    if ((rc = tri_prepare(b, TN, pair, st))) return rc;
+    // work items (see item_coords; S: the most bands the plan may choose)
+    const int units = pair ? b.tiles_m / 2 : b.tiles_m;
+    const int tiles = b.tri_cum != nullptr ? b.tri_tiles : units * b.tiles_n;
+    const int items = b.diag ? tiles * b.S : tiles;
+    const bool tt = b.tri_cum != nullptr;
+    if (pair) {
+        const int clusters = items < pair_clusters() ? items : pair_clusters();
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(2 * clusters);
+        cfg.gridDim = dim3(2 * (clusters > 0 ? clusters : 1));
         cfg.blockDim = dim3(BandCfg<256, true>::THREADS);
-        cfg.dynamicSmemBytes = BandCfg<256, true>::SMEM;
+        cfg.dynamicSmemBytes = tt ? BandCfg<256, true>::SMEM_TRI : BandCfg<256, true>::SMEM;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1278,19 +1374,28 @@ int launch_band(const CUtensorMap &tmA, const CUtensorMap &tmB, const BandArgs &
         cfg.attrs = at;
         cfg.numAttrs = 1;
         const cudaError_t e =
-            cudaLaunchKernelEx(&cfg, band_gemm_kernel<256, false, true>, tmA, *tmB_half, ba);
+            tt ? cudaLaunchKernelEx(&cfg, band_gemm_kernel<256, false, true, true>, tmA,
+                                    *tmB_half, b)
+               : cudaLaunchKernelEx(&cfg, band_gemm_kernel<256, false, true>, tmA, *tmB_half, b);
         if (e != cudaSuccess) return cuda_fail(e, "band_gemm_kernel (CTA pairs)");
         return check_launch("band_gemm_kernel");
     }
-    if (ba.mag)
-        band_gemm_kernel<128, true><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
-            tmA, tmB, ba);
-    else if (TN == 256)
-        band_gemm_kernel<256, false><<<grid, BandCfg<256>::THREADS, BandCfg<256>::SMEM, st>>>(
-            tmA, tmB, ba);
-    else
-        band_gemm_kernel<128, false><<<grid, BandCfg<128>::THREADS, BandCfg<128>::SMEM, st>>>(
-            tmA, tmB, ba);
+    const int grid = items < sm_count() ? (items > 0 ? items : 1) : sm_count();
+#define MPDD_BAND(TN_, MAG_, TRI_)                                                          \
+    band_gemm_kernel<TN_, MAG_, false, TRI_>                                                \
+        <<<grid, BandCfg<TN_>::THREADS, TRI_ ? BandCfg<TN_>::SMEM_TRI : BandCfg<TN_>::SMEM, \
+           st>>>(tmA, tmB, b)
+    if (b.mag) {
+        if (tt) MPDD_BAND(128, true, true);
+        else MPDD_BAND(128, true, false);
+    } else if (TN == 256) {
+        if (tt) MPDD_BAND(256, false, true);
+        else MPDD_BAND(256, false, false);
+    } else {
+        if (tt) MPDD_BAND(128, false, true);
+        else MPDD_BAND(128, false, false);
+    }
+#undef MPDD_BAND
     return check_launch("band_gemm_kernel");
 }
 

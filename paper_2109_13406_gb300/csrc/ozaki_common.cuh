@@ -105,7 +105,38 @@ struct BandArgs {
     float c1;                  // 1 - (k + 1) 2^-20 (exact in fp32): the sums' safety factor
     float ba_ratio32;          // ba_ratio rounded toward zero to fp32
     unsigned int *dmin_out;
+    // triangle mode: the work items are the tiles inside the triangle only,
+    // in raster order, through a table of cumulative tile counts per
+    // (raster group, row unit) (tri_rows + 1 entries in device memory,
+    // filled by launch_band); NULL: all tiles, the outside ones skipped
+    int *tri_cum;
+    int tri_rows, tri_units, tri_tiles;
 };
+
+// Tiles inside the triangle, enumerated as the band kernel's raster does: by
+// group of `group` tile columns, then by row unit (a tile, or a CTA pair's
+// two tiles: R rows), then by column.  For row unit u of group grp the
+// inside columns are [lo, hi] (empty when lo > hi), the tiles whose rows and
+// columns meet the triangle of C (tri = 1 upper, 2 lower).
+constexpr int kTriMax = 4096;   // largest table (entries) the kernel holds in shared memory
+struct TriGeom {
+    int tri, R, TN, tiles_n, group;
+};
+__host__ __device__ inline void tri_range(const TriGeom &g, int grp, int u, int &lo, int &hi) {
+    const int first = grp * g.group;
+    const int last = (first + g.group < g.tiles_n ? first + g.group : g.tiles_n) - 1;
+    const long long r0 = (long long)u * g.R;
+    if (g.tri == 1) {   // r0 <= c0 + TN - 1: columns from ceil((r0 - TN + 1) / TN)
+        const long long t0 = r0 - g.TN + 1;
+        const int tmin = t0 <= 0 ? 0 : (int)((t0 + g.TN - 1) / g.TN);
+        lo = tmin > first ? tmin : first;
+        hi = last;
+    } else {            // r0 + R - 1 >= c0: columns up to floor((r0 + R - 1) / TN)
+        const int tmax = (int)((r0 + g.R - 1) / g.TN);
+        lo = first;
+        hi = tmax < last ? tmax : last;
+    }
+}
 
 // Host launchers shared by the two forms (defined in dd_sliced.cu).
 // elem: 0 = fp16, 1 = bf16 elements.
@@ -134,7 +165,8 @@ int launch_magnitude(const double *X, int64_t ld, int row_contig, int64_t rows, 
 struct GemmArgs;
 int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int64_t n_pad,
                        int64_t k_pad, int TN, const unsigned long long *rmax,
-                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st);
+                       const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st,
+                       int *tri_table = nullptr);
 // The plain kernel behind the split-precision call: runs only when the
 // certificate fails (plan_choice < 0).
 int launch_plain_fallback(const GemmArgs &p, const SplitPlan &plan, cudaStream_t st);
