@@ -631,7 +631,11 @@ def run_default(args):
             "sections": sections,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 27 * args.steps,   # per step: 10 + 10 + 7 launches, see DESIGN
+            # per step 10 + 10 + 9 launches: each Rgemm runs maxima x2, magnitude
+            # planes x2, the magnitude product, residues x2, the products, the
+            # reconstruction and the gated plain kernel; the Rsyrk one operand's
+            # worth of those plus two triangle tables
+            "gpu_launches": 29 * args.steps,
             "clocks": clocks,
             "roofline": roofline,
             "summary": summary,
