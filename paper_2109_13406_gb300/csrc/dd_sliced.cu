@@ -68,17 +68,25 @@ __host__ __device__ constexpr int chunk_kb() { return MAG ? (1 << 30) : CHUNK_KB
 // matters more than operand reuse (13 % faster at 8192; 4 and 16 are 1.4 %
 // slower than 8 on full products).
 constexpr int kGroupFull = 8, kGroupTri = 4;
-constexpr int kEpiCols = 64;                // accumulator columns per epilogue thread
+// Accumulator columns per epilogue thread: 64 on the 128 x 128 tile (8
+// epilogue warps; the certificate's margin epilogue takes 64), 128 on the
+// 128 x 256 tile (8 epilogue warps, 10 in all, up to 168 registers).  On the
+// wide tile 8 warps of 128 columns drain faster alongside the MMAs than 16 of
+// 64: 1.4 % off the 8192 Rgemm band phase, 3.3 % off the Rsyrk triangle's.
+// (Loads of 32 columns at a time spill and measured slower.)
+constexpr int kEpiCols = 64;
+constexpr int kEpiColsWide = 128;
 
 // Two tile widths: 128 x 128 (6-stage ring of 32 KB, 8 epilogue warps) and
-// 128 x 256 (4 stages of 48 KB, 16 epilogue warps, all 512 TMEM columns);
+// 128 x 256 (4 stages of 48 KB, 8 epilogue warps, all 512 TMEM columns);
 // the wider tile reads 25 % fewer operand bytes per flop.  PAIR: a CTA pair
 // on a 256 x 256 tile with the 2-SM MMA, each CTA holding its 128 rows of A
 // and 128 of the 256 rows of B: 32 KB per stage and SM, 6 stages.
 template <int TN, bool PAIR = false>
 struct BandCfg {
     static constexpr int STAGES = PAIR ? 6 : (TN == 256 ? 4 : 6);
-    static constexpr int EPI_WARPS = TN / kEpiCols * 4;   // 4 lane quadrants
+    static constexpr int EPI_COLS = TN == 256 ? kEpiColsWide : kEpiCols;
+    static constexpr int EPI_WARPS = TN / EPI_COLS * 4;   // 4 lane quadrants
     static constexpr int THREADS = 32 * (2 + EPI_WARPS);  // producer, MMA, epilogue
     static constexpr int TMEM_COLS = 2 * TN;              // two fp32 accumulators
     static constexpr uint32_t A_BYTES = TM * TK * 2, B_BYTES = (PAIR ? TN / 2 : TN) * TK * 2;
@@ -643,7 +651,9 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
     } else {
         // ---------------- epilogue: drain chunks into int32 band sums
         const int q = warp % 4;                 // tensor-memory lane quadrant
-        const int col0 = ((warp - 2) / 4) * kEpiCols;  // first accumulator column
+        constexpr int EC = Cfg::EPI_COLS;             // accumulator columns of this thread
+        static_assert(!MAG || EC == kEpiCols, "the margin epilogue takes 64 columns");
+        const int col0 = ((warp - 2) / 4) * EC;       // first accumulator column
         const int row = q * 32 + lane;          // row of the tile this thread owns
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
         uint32_t chunk = 0;
@@ -652,9 +662,9 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
             int tm, tn, b0, b1;
             item_coords<TN, PAIR>(p, S, item, num_tiles, rank, tri_s, tm, tn, b0, b1);
             for (int b = b0; b < b1 && ok; ++b) {
-                int32_t acc[kEpiCols];
+                int32_t acc[EC];
 #pragma unroll
-                for (int j = 0; j < kEpiCols; ++j) acc[j] = 0;
+                for (int j = 0; j < EC; ++j) acc[j] = 0;
                 const int steps = (p.diag ? 1 : b + 1) * KB;
                 const int nchunks = (steps + chunk_kb<MAG>() - 1) / chunk_kb<MAG>();
                 for (int c = 0; c < nchunks; ++c, ++chunk) {
@@ -665,7 +675,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int cc = 0; cc < kEpiCols / 16; ++cc) {
+                    for (int cc = 0; cc < EC / 16; ++cc) {
                         uint32_t r[16];
                         tmem_ld_32x32b_x16(tmem + lane_base + buf * TN + col0 + cc * 16, r);
                         tmem_ld_wait();
@@ -688,7 +698,7 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
                     }
                 }
                 if (!ok) break;
-                if (MAG) {
+                if constexpr (MAG) {
                     certificate_margin(p, acc, (int64_t)tm * TM + row,
                                        (int64_t)tn * TN + col0);
                     continue;
@@ -699,14 +709,14 @@ __global__ void __launch_bounds__(BandCfg<TN, PAIR>::THREADS, 1)
                     const int pm = p.moduli[b];
                     uint8_t *dst = p.R + off;
 #pragma unroll
-                    for (int j = 0; j < kEpiCols; ++j) {
+                    for (int j = 0; j < EC; ++j) {
                         int r = acc[j] % pm;
                         dst[(int64_t)j * p.m_pad] = (uint8_t)(r < 0 ? r + pm : r);
                     }
                 } else {
                     int32_t *dst = p.P + off;
 #pragma unroll
-                    for (int j = 0; j < kEpiCols; ++j) dst[(int64_t)j * p.m_pad] = acc[j];
+                    for (int j = 0; j < EC; ++j) dst[(int64_t)j * p.m_pad] = acc[j];
                 }
             }
         }
