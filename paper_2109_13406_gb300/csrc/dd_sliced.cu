@@ -73,7 +73,9 @@ constexpr int kGroupFull = 8, kGroupTri = 4;
 // 128 x 256 tile (8 epilogue warps, 10 in all, up to 168 registers).  On the
 // wide tile 8 warps of 128 columns drain faster alongside the MMAs than 16 of
 // 64: 1.4 % off the 8192 Rgemm band phase, 3.3 % off the Rsyrk triangle's.
-// (Loads of 32 columns at a time spill and measured slower.)
+// (Loads of 32 columns at a time spill and measured slower; so did sums
+// reduced mod p per run and packed two columns to a word, in 4 or 8 warps:
+// the extra arithmetic per drained value slows the MMAs.)
 constexpr int kEpiCols = 64;
 constexpr int kEpiColsWide = 128;
 
