@@ -1120,9 +1120,11 @@ int launch_certificate(const GemmArgs &p, void *MA, void *MB, int64_t m_pad, int
                        int64_t k_pad, int TN, const unsigned long long *rmax,
                        const unsigned long long *cmax, SplitHeader *hdr, cudaStream_t st,
                        int *tri_table) {
-    // the product's own tile width (n_pad is a multiple of it): on 128 x 256
-    // tiles the 8192 certificate phase runs ~1.5 % faster than on 128 x 128
-    if (TN != 256) TN = 128;
+    // the product's own tile width (n_pad is a multiple of it) when that
+    // leaves at least 1024 tiles (~7 per SM): at 8192 the 128 x 256 tiles
+    // take the magnitude product from 1.23 to 1.09 ms, at 4096 their 512
+    // tiles (3.4 per SM) took 254 us against 189 us on 128 x 128 tiles
+    if (TN != 256 || (m_pad / TM) * (n_pad / 256) < 1024) TN = 128;
     int rc;
     CUtensorMap tmA, tmB;
     if ((rc = make_tmap(&tmA, MA, m_pad, k_pad, TM, 1))) return rc;
