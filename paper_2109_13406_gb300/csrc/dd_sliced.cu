@@ -68,9 +68,9 @@ __host__ __device__ constexpr int chunk_kb() { return MAG ? (1 << 30) : CHUNK_KB
 // matters more than operand reuse (13 % faster at 8192; 4 and 16 are 1.4 %
 // slower than 8 on full products).
 constexpr int kGroupFull = 8, kGroupTri = 4;
-// Accumulator columns per epilogue thread: 64 on the 128 x 128 tile (8
-// epilogue warps; the certificate's margin epilogue takes 64), 128 on the
-// 128 x 256 tile (8 epilogue warps, 10 in all, up to 168 registers).  On the
+// Accumulator columns per epilogue thread: 64 on the 128 x 128 tile, 128 on
+// the 128 x 256 tile; 8 epilogue warps either way (10 in all, up to 168
+// registers), for the residue and magnitude products alike.  On the
 // wide tile 8 warps of 128 columns drain faster alongside the MMAs than 16 of
 // 64: 1.4 % off the 8192 Rgemm band phase, 3.3 % off the Rsyrk triangle's.
 // (Loads of 32 columns at a time spill and measured slower; so did sums
