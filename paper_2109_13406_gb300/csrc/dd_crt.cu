@@ -646,6 +646,25 @@ __global__ void __launch_bounds__(256) crt_kernel(const __grid_constant__ CrtArg
 
 // ------------------------------------------------------------------ host
 
+// 256-thread blocks of the three crt_kernel instantiations resident per SM
+// (occupancy query, once per instantiation; 1 if the query fails).
+int crt_resident_blocks(int which) {
+    static int cached[3] = {0, 0, 0};
+    static std::once_flag once[3];
+    std::call_once(once[which], [which] {
+        int b = 0;
+        const void *f = which == 0 ? (const void *)crt_kernel<8, 9, 10>
+                        : which == 1 ? (const void *)crt_kernel<9, 9, 10>
+                                     : (const void *)crt_kernel<9, 10, 10>;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b = 0;
+        }
+        cached[which] = b > 0 ? b : 1;
+    });
+    return cached[which];
+}
+
 // Little-endian multiword helpers (host).
 using Big = std::vector<uint32_t>;
 
@@ -973,20 +992,27 @@ int run_crt(const GemmArgs &p, void *ws, size_t ws_bytes, cudaStream_t st) {
     for (int c = 0; c < ncand; ++c)
         if ((rc = crt_tables(counts[c], ca.tab[c], &nw[c]))) return rc;
     for (int c = ncand; c < kMaxCand; ++c) nw[c] = nw[ncand - 1];   // (never chosen)
-    // one thread per entry pair; blocks resident at once, looping
-    const int64_t pairs = ceil_div(p.m, 2) * p.n;
-    int64_t blocks = ceil_div(pairs, 256);
-    if (blocks > (int64_t)sm_count() * 8) blocks = (int64_t)sm_count() * 8;
-    if (blocks < 1) blocks = 1;
     // the word counts that occur for k < 2^17: 8 at 112 bits (9 for the
     // largest k), 9 at 120 bits, 9 or 10 at 128 bits; a kernel with more
     // words than needed gives the same result (the weights are zero-padded)
     if (nw[0] > 9 || nw[1] > 10 || nw[2] > 10)
         return fail(MP_DD_ERR_TOO_LARGE, "CRT word counts %d/%d/%d beyond the kernel's", nw[0],
                     nw[1], nw[2]);
+    // one thread per entry pair, looping.  Full products: as many blocks as
+    // are resident at once (three per SM at 80 registers; eight per SM left
+    // the last two-thirds wave with a third of the slots idle: 3.65-3.68
+    // against 3.70-3.73 ms at 8192).  Triangles: eight per SM, which the
+    // block scheduler balances over the uneven work of the skipped entries
+    // (resident blocks only: 2.61 against 2.41-2.45 ms).
+    const int64_t pairs = ceil_div(p.m, 2) * p.n;
+    const int which = nw[0] <= 8 && nw[1] <= 9 ? 0 : (nw[1] <= 9 ? 1 : 2);
+    int64_t blocks = ceil_div(pairs, 256);
+    const int64_t cap = (int64_t)sm_count() * (p.tri ? 8 : crt_resident_blocks(which));
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
     const unsigned nb = (unsigned)blocks;
-    if (nw[0] <= 8 && nw[1] <= 9) crt_kernel<8, 9, 10><<<nb, 256, 0, st>>>(ca);
-    else if (nw[1] <= 9) crt_kernel<9, 9, 10><<<nb, 256, 0, st>>>(ca);
+    if (which == 0) crt_kernel<8, 9, 10><<<nb, 256, 0, st>>>(ca);
+    else if (which == 1) crt_kernel<9, 9, 10><<<nb, 256, 0, st>>>(ca);
     else crt_kernel<9, 10, 10><<<nb, 256, 0, st>>>(ca);
     if ((rc = check_launch("crt_kernel"))) return rc;
     rc = launch_plain_fallback(p, plan, st);
